@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Throughput of the transposition-free tensor contraction on GB300.
+
+Default workload: the FP64 coupled-cluster-style contraction
+    C[a,b,i,j] = 0.5 * sum_{c,d} A[c,a,d,b] * B[i,c,j,d] + 1.0 * C[a,b,i,j]
+with a, b, c, d = 96 and i, j = 24 in general column-major layout (a 9216 x 576
+x 9216 matrix product in disguise, 9.78e10 flops per step).  One step = one
+tc_contract call (scatter-vector build + FP64 mainloop with fused epilogue).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (the contraction needs no exchange between
+GPUs); `value` sums the work of all ranks over the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import paper_1607_00291_gb300 as tc  # noqa: E402
+from paper_1607_00291_gb300 import _lib as L  # noqa: E402
+from paper_1607_00291_gb300 import workloads as W  # noqa: E402
+
+METRIC = "contraction TFLOP/s and % of tensor-pipe peak per precision, at stated error"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cc4x4_f64", choices=sorted(W.SPECS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- process group ----------------------------------------------------------------
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks ------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- peaks ---------------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def fp64_peak_tflops() -> float:
+    """FP64 denominator: cuBLAS DGEMM 4096^3 (best of 3) on this GPU, measured
+    here outside the timed region (the pool's peak file carries no FP64 figure)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source
+    is unchanged since the counters were taken; else None."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except OSError:
+        return None
+    e = t.get(f"{kernel}:{workload}")
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1607_00291_gb300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return e["dram_bytes_per_launch"] if h == e["source_sha256_16"] else None
+
+
+# ---- workload -------------------------------------------------------------------------
+
+def workload_config(spec, extra=None):
+    pl = tc.plan_describe(_cm(spec, spec.labA), spec.labA, _cm(spec, spec.labB), spec.labB, _cm(spec, spec.labC), spec.labC)
+    desc = (f"{spec.name}: {spec.labC} <- {spec.labA}.{spec.labB}, extents "
+            + ",".join(f"{k}={v}" for k, v in sorted(spec.ext.items()))
+            + f", column-major, alpha={spec.alpha}, beta={spec.beta}, mode={spec.mode}")
+    cfg = {"workload": desc, "m": pl["m"], "n": pl["n"], "k": pl["k"], "mode": spec.mode}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _cm(spec, lab):
+    acc, st = 1, []
+    for x in lab:
+        st.append(acc)
+        acc *= spec.ext[x]
+    return tuple(spec.ext[x] for x in lab), tuple(st)
+
+
+def to_device(t, dtype):
+    return torch.empty_strided(t.shape, t.stride(), dtype=dtype, device="cuda").copy_(t.to(dtype))
+
+
+def host_bytes(spec):
+    es = torch.tensor([], dtype=spec.dtype).element_size()
+    n = lambda lab: int(np.prod(spec.shape(lab)))
+    return es * n(spec.labA), es * n(spec.labB), es * n(spec.labC)
+
+
+# ---- CPU oracle baseline -----------------------------------------------------------------
+
+def oracle_sample(spec, host, seconds: float, out_count=None):
+    """Time the CPU oracle on the first S output elements of the workload, S
+    chosen to take about `seconds`.  Returns (flops, seconds, S, cores, C, mag)."""
+    import oracle
+    a, b = host["A"].numpy(), host["B"].numpy()
+    k = 1
+    for x in set(spec.labA) & set(spec.labB):
+        k *= spec.ext[x]
+    cores = oracle.num_threads()
+    c = np.array(host["C"].numpy(), copy=True)
+    probe = min(max(cores * 8, 64), c.size)
+    t0 = time.perf_counter()
+    oracle.contract_(spec.alpha, a, spec.labA, b, spec.labB, spec.beta, c, spec.labC, mag=False,
+                     begin=0, end=probe)
+    dt = time.perf_counter() - t0
+    S = out_count or int(min(c.size, max(probe, probe * seconds / max(dt, 1e-6))))
+    c = np.array(host["C"].numpy(), copy=True)
+    t0 = time.perf_counter()
+    mag = oracle.contract_(spec.alpha, a, spec.labA, b, spec.labB, spec.beta, c, spec.labC,
+                           begin=0, end=S)
+    dt = time.perf_counter() - t0
+    return 2.0 * k * S, dt, S, cores, c, mag
+
+
+# ---- our arm ---------------------------------------------------------------------------------
+
+def run_ours(args, ws, rank, local):
+    spec = W.SPECS[args.workload]
+    warm = max(3, args.warmup)
+    K = max(1, args.steps)
+    seed = 1000 + list(W.SPECS).index(spec.name)
+    host = W.make_inputs(spec, seed=seed)
+    dt = spec.dtype
+    dA, dB, dC = (to_device(host[x], dt) for x in "ABC")
+    C0 = dC.clone()
+    wsz = tc.workspace_size(dA, spec.labA, dB, spec.labB, dC, spec.labC, mode=spec.mode)
+    work = torch.empty(max(1, wsz), dtype=torch.uint8, device="cuda")
+    flops = spec.flops()
+    lib = L.lib()
+
+    def step():
+        tc.contract(dA, spec.labA, dB, spec.labB, dC, spec.labC, alpha=spec.alpha, beta=spec.beta,
+                    mode=spec.mode, workspace=work)
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+
+    # device-resident timed region
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.tc_launch_count()
+    e0.record()
+    for i in range(K):
+        lib.tc_set_mainloop_events(L.c_vp(kev[i][0].cuda_event), L.c_vp(kev[i][1].cuda_event))
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = lib.tc_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(ws)
+    ms = e0.elapsed_time(e1) / K
+    kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    ms_max = max_over_ranks(ms, ws)
+    kms_max = max_over_ranks(kms, ws)
+    err_code = tc.device_error()
+
+    # end-to-end through the public API with host buffers
+    # pinned host copies keep the column-major strides of the host views
+    hA = torch.empty_strided(host["A"].shape, host["A"].stride(), dtype=dt).pin_memory().copy_(host["A"])
+    hB = torch.empty_strided(host["B"].shape, host["B"].stride(), dtype=dt).pin_memory().copy_(host["B"])
+    hC = torch.empty_strided(host["C"].shape, host["C"].stride(), dtype=dt).pin_memory().copy_(host["C"])
+    hOut = torch.empty_strided(hC.shape, hC.stride(), dtype=dt).pin_memory()
+    bi = sum(host_bytes(spec))
+    bo = host_bytes(spec)[2]
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        step()
+        hOut.copy_(dC, non_blocking=True)
+
+    for _ in range(warm):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(K):
+        e2e_step()
+    f1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / K, ws)
+
+    peak = fp64_peak_tflops() if spec.mode == "f64" else None
+    if spec.mode == "f64":
+        peak_v, peak_src = peak, "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
+        bound, unit, ach = "tensor", "TFLOP/s", flops / (kms_max * 1e-3) / 1e12
+        kname = "k_f64"
+    else:
+        mp = measured_peaks()
+        peak_v = mp.get("bf16_tflops", 1900.0)
+        peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
+        bound, unit, ach = "tensor", "TFLOP/s", 3 * flops / (kms_max * 1e-3) / 1e12
+        kname = "k_bf16x3"
+    value = ws * flops / (ms_max * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": ws, "steps": K,
+        "warmup": warm, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if spec.mode == "f64" else "f32 data, bf16x3 products, f32 accumulate",
+        "data": "synthetic (seeded uniform[-1,1], column-major; shapes of the paper's CC-style contractions)",
+        "config": workload_config(spec, {
+            "l2": f"inputs larger than L2 (A = {host_bytes(spec)[0] / 1e6:.1f} MB > {L2_BYTES / 1e6:.0f} MB)",
+            "parallelism": f"replicas x{ws}"}),
+        "clocks": clk,
+        "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": bound, "kernel": kname, "achieved": round(ach, 5), "peak": round(peak_v, 5),
+                     "unit": unit, "frac": round(ach / peak_v, 4), "peak_source": peak_src,
+                     "kernel_ms": round(kms_max, 4),
+                     "traffic": traffic_for(kname, spec.name),
+                     "algorithmic": f"{flops:.4g} flops per launch"
+                                    + (" (x3 bf16 products)" if spec.mode != "f64" else "")},
+        "device_error": err_code,
+    }
+
+    # CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        dC.copy_(C0)
+        step()
+        torch.cuda.synchronize()
+        got = dC.cpu().to(torch.float64).numpy()
+        fl, sec, S, cores, cref, mag = oracle_sample(spec, host, seconds=12.0)
+        sel = np.arange(S)
+        g = got.ravel(order="F")[sel]
+        r = cref.ravel(order="F")[sel]
+        m = mag.ravel(order="F")[sel]
+        err = float(np.max(np.abs(g - r) / np.maximum(m, 1e-300)))
+        line["cpu_baseline"] = {"value": round(fl / sec / 1e12, 8), "unit": "TFLOP/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {S} of {got.size} output elements (all k terms each), "
+                                          f"{sec:.1f} s on {cores} host threads",
+                                "max_normalised_err_gpu_vs_oracle": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---- reference arm: the CPU oracle as it stands ------------------------------------------------
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    spec = W.SPECS[args.workload]
+    seed = 1000 + list(W.SPECS).index(spec.name)
+    host = W.make_inputs(spec, seed=seed)
+    warm, K = max(3, args.warmup), max(1, args.steps)
+    per_step = max(0.5, min(4.0, 90.0 / (warm + K)))
+    fl, sec, S, cores, _, _ = oracle_sample(spec, host, seconds=per_step)
+    for _ in range(warm - 1):
+        oracle_sample(spec, host, seconds=per_step, out_count=S)
+    times = []
+    for _ in range(K):
+        fl, sec, _, _, _, _ = oracle_sample(spec, host, seconds=per_step, out_count=S)
+        times.append(sec)
+    t = float(np.mean(times))
+    v = fl / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": K, "warmup": warm, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(spec, {"sample": f"first {S} output elements per step"}),
+            "cpu_baseline": {"value": round(v, 8), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {S} output elements of {spec.name} per step"},
+            "e2e": {"value": round(v, 8), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py --impl ours needs a GPU")
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * tc.h -- C ABI of the transposition-free tensor contraction library (libtc).
+ *
+ * The operation (Section 4, eq. (gen-contraction); alpha/beta as in Section 3):
+ *
+ *   C[pi_C(I J)] := alpha * sum_P A[pi_A(I P)] * B[pi_B(P J)] + beta * C[pi_C(I J)]
+ *
+ * The I bundle holds the labels shared by A and C, J those shared by B and C,
+ * P those shared by A and B (Section 4).  The contraction runs as a matrix
+ * multiplication C_{IJ} = A_{IP} B_{PJ} directly on the tensors' own layouts
+ * through scatter and block-scatter vectors (Sections 6.1-6.2); no operand is
+ * transposed or copied.
+ *
+ * Conventions for every entry point:
+ *  - Strides and lengths are in ELEMENTS.  A data pointer addresses the element
+ *    whose indices are all zero.  A and B may have any int64 strides (negative
+ *    or zero included); C must not overlap itself.
+ *  - Labels are single bytes, one per dimension, unique within a tensor; every
+ *    label must appear in exactly two of A, B, C, with one extent.
+ *  - All data pointers are DEVICE pointers owned by the caller.  The library
+ *    keeps no pointer after a call returns, except that a tc_plan keeps copies
+ *    of its problem descriptors (and a device buffer of its own, see below).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued asynchronously; a return of TC_OK means the launches were issued.
+ *  - Errors are returned as negative codes (never thrown, never aborting);
+ *    device-side faults detected by the kernels (bounded waits that expired,
+ *    offsets outside an operand) are reported by tc_get_device_error.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TC_MAX_RANK 16
+
+/* Element type of A, B and C (all three share it). */
+typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
+
+/* Arithmetic:
+ *  TC_MODE_F64    -- products and sums in FP64 (F32 data is widened on load);
+ *  TC_MODE_BF16X3 -- F32 data only: each operand split as x = hi + lo with
+ *                    hi = RN_bf16(x), lo = RN_bf16(x - hi); hi*hi + hi*lo + lo*hi
+ *                    on the tensor cores with FP32 accumulation, split-K
+ *                    partials reduced in FP64. */
+typedef enum { TC_MODE_F64 = 0, TC_MODE_BF16X3 = 1 } tc_mode;
+
+enum {
+  TC_OK = 0,
+  TC_ERR_ARG = -1,            /* null pointer, rank > TC_MAX_RANK, negative length, bad enum */
+  TC_ERR_LABEL = -2,          /* label repeated in a tensor, or not in exactly two tensors */
+  TC_ERR_EXTENT = -3,         /* one label with two different lengths */
+  TC_ERR_OVERLAP = -4,        /* C overlaps itself */
+  TC_ERR_WORKSPACE = -5,      /* workspace missing, too small or misaligned */
+  TC_ERR_CUDA = -6,           /* a CUDA runtime call failed */
+  TC_ERR_DEVICE_TIMEOUT = -7, /* a kernel's bounded wait expired (device error word) */
+  TC_ERR_UNSUPPORTED = -8,    /* combination not provided (e.g. BF16X3 on F64 data) */
+  TC_ERR_DEVICE_BOUNDS = -9   /* a kernel computed an offset outside an operand */
+};
+
+/* One tensor operand: `rank` dimensions with lengths `len[d]` >= 0, strides
+ * `stride[d]` (elements) and labels `labels[d]` (rank bytes, not necessarily
+ * NUL-terminated).  rank 0 is a scalar.  All arrays are host memory, read only
+ * during the call. */
+typedef struct {
+  int32_t rank;
+  const int64_t* len;
+  const int64_t* stride;
+  const char* labels;
+  void* data;
+} tc_tensor;
+
+/* One contraction of a batch. */
+typedef struct {
+  double alpha, beta;
+  tc_tensor A, B, C;
+} tc_problem;
+
+/* Host-side description of how a contraction is laid out as a matrix
+ * multiplication (Section 7.3: length-one dims dropped, sequentially contiguous
+ * dims folded, I and J sorted by stride in C, A<->B swapped when C's unit
+ * stride is in J, P sorted by stride in A).  After a swap, "A" and "B" below
+ * name the operands in their matrix roles (A is the caller's B). */
+typedef struct {
+  int32_t swapped;                 /* 1 if the caller's A and B were exchanged */
+  int32_t nI, nJ, nP;              /* folded dimensions per bundle */
+  int64_t m, n, k;                 /* products of the bundle lengths */
+  int64_t I_len[TC_MAX_RANK], I_sA[TC_MAX_RANK], I_sC[TC_MAX_RANK];
+  int64_t J_len[TC_MAX_RANK], J_sB[TC_MAX_RANK], J_sC[TC_MAX_RANK];
+  int64_t P_len[TC_MAX_RANK], P_sA[TC_MAX_RANK], P_sB[TC_MAX_RANK];
+  /* For each folded dim, the caller's labels it covers (NUL-terminated). */
+  char I_labels[TC_MAX_RANK][TC_MAX_RANK + 1];
+  char J_labels[TC_MAX_RANK][TC_MAX_RANK + 1];
+  char P_labels[TC_MAX_RANK][TC_MAX_RANK + 1];
+  /* Access plan (Section 7.3, stride-1 preference): 1 if the operand's
+   * smallest |stride| lies along K (A, B) or along M (C). */
+  int32_t a_k_contig, b_k_contig, c_m_contig;
+} tc_plan_info;
+
+/* Opaque batched plan. */
+typedef struct tc_plan tc_plan;
+
+/* ---- planning (host only, no GPU needed) -------------------------------- */
+
+/* Validate and lay out a contraction (Sections 4 and 7.3) without launching
+ * anything.  Returns TC_OK and fills *info, or an error code. */
+TC_API int tc_plan_describe(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C,
+                     tc_plan_info* info);
+
+/* Device workspace in bytes that tc_contract needs for this problem: the
+ * scatter and block-scatter vectors, O(m + n + k) (Sections 6.1-6.3), plus
+ * split-K or stream-K partial tiles where the tile scheduler uses them.  Never
+ * an operand-sized copy.  Alignment: 256 bytes. */
+TC_API int tc_workspace_size(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                      const tc_tensor* C, size_t* bytes);
+
+/* ---- the contraction -------------------------------------------------------- */
+
+/* C := alpha * A.B + beta * C, in place on the caller's layouts (Section 4,
+ * Section 6.2's block-scatter-matrix algorithm mapped onto GPU tiles).
+ * beta == 0: C is only written (NaN in C does not propagate); alpha == 0 or an
+ * empty contracted range: C := beta * C.  `workspace` must hold at least
+ * tc_workspace_size bytes, 256-byte aligned (may be NULL if that size is 0).
+ * Asynchronous on `stream`. */
+TC_API int tc_contract(tc_dtype dtype, tc_mode mode, double alpha, const tc_tensor* A,
+                const tc_tensor* B, double beta, const tc_tensor* C, void* workspace,
+                size_t ws_bytes, void* stream);
+
+/* ---- batches ------------------------------------------------------------------ */
+
+/* Workspace for tc_contract_batched over the same problems. */
+TC_API int tc_batched_workspace_size(tc_dtype dtype, tc_mode mode, int32_t count,
+                              const tc_problem* probs, size_t* bytes);
+
+/* Run `count` independent contractions of possibly different ranks, extents,
+ * strides and labels in one persistent launch (plus one launch building all
+ * scatter vectors and, in BF16X3 mode, one FP64 reduction launch).  Equivalent
+ * to calling tc_contract on each problem.  Problems must not write overlapping
+ * C elements.  Creates and destroys a temporary plan (allocates and frees a
+ * small device descriptor buffer; synchronises `stream` before freeing it). */
+TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/* Plan form for repeated batches: tc_plan_create validates and plans every
+ * problem, chooses tiles (from the autotune table), and copies the
+ * descriptors into a device buffer that the plan owns (cudaMalloc at create,
+ * cudaFree at destroy).  tc_plan_execute only launches kernels, with no host
+ * synchronisation and no allocation, so it can be captured in a CUDA graph. */
+TC_API int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                   tc_plan** out);
+TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);
+TC_API int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream);
+TC_API void tc_plan_destroy(tc_plan* plan);
+
+/* ---- scatter vectors (K1 on its own; used by the tests) ------------------------ */
+
+/* Number of int64 entries tc_build_scatter writes for this problem and block
+ * size b: 2(m + n + k) scatter entries followed by the six block-scatter
+ * vectors. */
+TC_API int tc_scatter_count(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,
+                     int64_t* count);
+
+/* Build on the device, into `out` (device, count int64), the scatter vectors of
+ * Section 6.1 for the planned bundles and the block-scatter vectors of
+ * Section 6.2 with blocking parameter b, in this order:
+ *   rscat(A)[m] cscat(A)[k] rscat(B)[k] cscat(B)[n] rscat(C)[m] cscat(C)[n]
+ *   rbs(A)[ceil(m/b)] cbs(A)[ceil(k/b)] rbs(B)[ceil(k/b)] cbs(B)[ceil(n/b)]
+ *   rbs(C)[ceil(m/b)] cbs(C)[ceil(n/b)]
+ * where A and B are the matrix-role operands of tc_plan_describe.  A block
+ * entry is its constant stride s > 0, or 0 when the block's stride varies; a
+ * one-element block has stride 1. */
+TC_API int tc_build_scatter(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,
+                     int64_t* out, int64_t count, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------------------ */
+
+/* Synchronise `stream`, read and clear the library's device error word.
+ * *code is TC_OK, TC_ERR_DEVICE_TIMEOUT or TC_ERR_DEVICE_BOUNDS. */
+TC_API int tc_get_device_error(void* stream, int32_t* code);
+
+/* Instrumentation: record the caller's CUDA events `before` and `after`
+ * (cudaEvent_t handles, or NULL to stop) on the launching stream immediately
+ * before and after the mainloop kernel of the next contraction issued from
+ * this host thread (tc_contract or tc_plan_execute); the pair is used once and
+ * then cleared.  Lets a caller time the dominant kernel alone. */
+TC_API int tc_set_mainloop_events(void* before, void* after);
+
+/* Number of kernels libtc has launched in this process so far. */
+TC_API uint64_t tc_launch_count(void);
+
+/* Static string for a status code. */
+TC_API const char* tc_status_string(int status);
+
+/* Library version (major*10000 + minor*100 + patch). */
+TC_API int tc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

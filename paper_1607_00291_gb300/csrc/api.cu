@@ -1,0 +1,285 @@
+// libtc C ABI: argument checks, planning, workspace carving and launches.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+
+namespace tc {
+int aliases(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, size_t es);
+
+std::atomic<uint64_t> g_launches{0};
+thread_local cudaEvent_t t_ev_before = nullptr, t_ev_after = nullptr;
+
+void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+void mainloop_event_before(cudaStream_t s) {
+  if (t_ev_before) cudaEventRecord(t_ev_before, s);
+}
+void mainloop_event_after(cudaStream_t s) {
+  if (t_ev_after) cudaEventRecord(t_ev_after, s);
+  t_ev_before = t_ev_after = nullptr;
+}
+}  // namespace tc
+
+namespace {
+
+using namespace tc;
+
+__device__ int32_t g_tc_error;  // device error word (kDevTimeout / kDevBounds), 0 = none
+
+std::mutex g_mu;
+int32_t* g_err_ptr[64] = {};
+
+// Address of the device error word on the current device (set up once per device).
+int32_t* err_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_err_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) return nullptr;
+    g_err_ptr[dev] = static_cast<int32_t*>(p);
+  }
+  return g_err_ptr[dev];
+}
+
+size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : 4; }
+
+int check_modes(tc_dtype dt, tc_mode mode) {
+  if (dt != TC_F64 && dt != TC_F32) return TC_ERR_ARG;
+  if (mode != TC_MODE_F64 && mode != TC_MODE_BF16X3) return TC_ERR_ARG;
+  if (mode == TC_MODE_BF16X3) return TC_ERR_UNSUPPORTED;  // provided by the tcgen05 path
+  return TC_OK;
+}
+
+struct WsLayout {
+  size_t scatter_off, scatter_bytes;
+  size_t total;
+};
+
+WsLayout ws_layout(const Planned& p) {
+  WsLayout w;
+  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
+  w.scatter_off = 0;
+  w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
+  w.total = w.scatter_bytes;
+  return w;
+}
+
+int plan_checked(tc_dtype dt, const tc_tensor* A, const tc_tensor* B, const tc_tensor* C,
+                 Planned* p) {
+  int rc = plan_problem(A, B, C, p);
+  if (rc != TC_OK) return rc;
+  if (tc::aliases(A, B, C, elem_size(dt))) return TC_ERR_OVERLAP;
+  return TC_OK;
+}
+
+int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Planned& p,
+                void* ws, size_t ws_bytes, cudaStream_t s) {
+  const Layout& L = p.L;
+  if (L.m == 0 || L.n == 0) return TC_OK;
+  const WsLayout w = ws_layout(p);
+  if (ws_bytes < w.total || (w.total > 0 && ws == nullptr) ||
+      (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return TC_ERR_WORKSPACE;
+  int64_t* scat = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + w.scatter_off);
+  const ScatterOffsets o = scatter_offsets(L, kBsBlock);
+  if (launch_build_scatter(L, kBsBlock, scat, s) != cudaSuccess) return TC_ERR_CUDA;
+  const ScatterPtrs sp = scatter_ptrs(scat, o);
+  if (L.k == 0 || alpha == 0.0)
+    return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  (void)mode;
+  F64Launch f;
+  f.dtype = dt;
+  f.a = p.a;
+  f.b = p.b;
+  f.c = p.c;
+  f.sp = sp;
+  f.m = L.m;
+  f.n = L.n;
+  f.k = L.k;
+  f.alpha = alpha;
+  f.beta = beta;
+  f.a_k_contig = p.info.a_k_contig;
+  f.b_k_contig = p.info.b_k_contig;
+  f.err = err_word();
+  return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+}  // namespace
+
+struct tc_plan {
+  tc_dtype dtype;
+  tc_mode mode;
+  std::vector<tc_problem> probs;
+  std::vector<Planned> planned;
+  std::vector<size_t> ws_off;
+  size_t ws_total;
+};
+
+extern "C" {
+
+int tc_version(void) { return 100; }
+
+const char* tc_status_string(int status) {
+  switch (status) {
+    case TC_OK: return "ok";
+    case TC_ERR_ARG: return "invalid argument";
+    case TC_ERR_LABEL: return "invalid labels (each label must appear in exactly two tensors)";
+    case TC_ERR_EXTENT: return "mismatched extents for a shared label";
+    case TC_ERR_OVERLAP: return "C overlaps itself or aliases A/B";
+    case TC_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case TC_ERR_CUDA: return "CUDA runtime error";
+    case TC_ERR_DEVICE_TIMEOUT: return "device-side bounded wait expired";
+    case TC_ERR_UNSUPPORTED: return "unsupported dtype/mode combination";
+    case TC_ERR_DEVICE_BOUNDS: return "device-side offset outside an operand";
+    default: return "unknown status";
+  }
+}
+
+int tc_plan_describe(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C,
+                     tc_plan_info* info) {
+  if (!info) return TC_ERR_ARG;
+  Planned p;
+  int rc = plan_problem(A, B, C, &p);
+  if (rc != TC_OK) return rc;
+  *info = p.info;
+  return TC_OK;
+}
+
+int tc_workspace_size(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                      const tc_tensor* C, size_t* bytes) {
+  if (!bytes) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  Planned p;
+  if ((rc = plan_problem(A, B, C, &p)) != TC_OK) return rc;
+  *bytes = (p.L.m == 0 || p.L.n == 0) ? 0 : ws_layout(p).total;
+  return TC_OK;
+}
+
+int tc_contract(tc_dtype dtype, tc_mode mode, double alpha, const tc_tensor* A,
+                const tc_tensor* B, double beta, const tc_tensor* C, void* workspace,
+                size_t ws_bytes, void* stream) {
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  Planned p;
+  if ((rc = plan_checked(dtype, A, B, C, &p)) != TC_OK) return rc;
+  return run_planned(dtype, mode, alpha, beta, p, workspace, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                   tc_plan** out) {
+  if (!out || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  tc_plan* pl = new tc_plan;
+  pl->dtype = dtype;
+  pl->mode = mode;
+  pl->ws_total = 0;
+  pl->planned.resize(count);
+  for (int32_t i = 0; i < count; ++i) {
+    rc = plan_checked(dtype, &probs[i].A, &probs[i].B, &probs[i].C, &pl->planned[i]);
+    if (rc != TC_OK) {
+      delete pl;
+      return rc;
+    }
+    pl->ws_off.push_back(pl->ws_total);
+    const Planned& p = pl->planned[i];
+    if (p.L.m != 0 && p.L.n != 0) pl->ws_total += ws_layout(p).total;
+    pl->probs.push_back(probs[i]);
+  }
+  *out = pl;
+  return TC_OK;
+}
+
+int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return TC_ERR_ARG;
+  *bytes = plan->ws_total;
+  return TC_OK;
+}
+
+int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+  if (!plan) return TC_ERR_ARG;
+  if (ws_bytes < plan->ws_total || (plan->ws_total > 0 && !workspace)) return TC_ERR_WORKSPACE;
+  for (size_t i = 0; i < plan->planned.size(); ++i) {
+    const Planned& p = plan->planned[i];
+    if (p.L.m == 0 || p.L.n == 0) continue;
+    int rc = run_planned(plan->dtype, plan->mode, plan->probs[i].alpha, plan->probs[i].beta, p,
+                         static_cast<char*>(workspace) + plan->ws_off[i],
+                         ws_layout(p).total, static_cast<cudaStream_t>(stream));
+    if (rc != TC_OK) return rc;
+  }
+  return TC_OK;
+}
+
+void tc_plan_destroy(tc_plan* plan) { delete plan; }
+
+int tc_batched_workspace_size(tc_dtype dtype, tc_mode mode, int32_t count,
+                              const tc_problem* probs, size_t* bytes) {
+  if (!bytes) return TC_ERR_ARG;
+  tc_plan* pl = nullptr;
+  int rc = tc_plan_create(dtype, mode, count, probs, &pl);
+  if (rc != TC_OK) return rc;
+  *bytes = pl->ws_total;
+  tc_plan_destroy(pl);
+  return TC_OK;
+}
+
+int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                        void* workspace, size_t ws_bytes, void* stream) {
+  tc_plan* pl = nullptr;
+  int rc = tc_plan_create(dtype, mode, count, probs, &pl);
+  if (rc != TC_OK) return rc;
+  rc = tc_plan_execute(pl, workspace, ws_bytes, stream);
+  tc_plan_destroy(pl);
+  return rc;
+}
+
+int tc_scatter_count(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,
+                     int64_t* count) {
+  if (!count || b <= 0) return TC_ERR_ARG;
+  Planned p;
+  int rc = plan_problem(A, B, C, &p);
+  if (rc != TC_OK) return rc;
+  *count = scatter_offsets(p.L, b).total;
+  return TC_OK;
+}
+
+int tc_build_scatter(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,
+                     int64_t* out, int64_t count, void* stream) {
+  if (b <= 0) return TC_ERR_ARG;
+  Planned p;
+  int rc = plan_problem(A, B, C, &p);
+  if (rc != TC_OK) return rc;
+  const ScatterOffsets o = scatter_offsets(p.L, b);
+  if (count < o.total || (o.total > 0 && !out)) return TC_ERR_WORKSPACE;
+  return launch_build_scatter(p.L, b, out, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? TC_OK
+             : TC_ERR_CUDA;
+}
+
+int tc_set_mainloop_events(void* before, void* after) {
+  tc::t_ev_before = static_cast<cudaEvent_t>(before);
+  tc::t_ev_after = static_cast<cudaEvent_t>(after);
+  return TC_OK;
+}
+
+uint64_t tc_launch_count(void) { return tc::g_launches.load(); }
+
+int tc_get_device_error(void* stream, int32_t* code) {
+  if (!code) return TC_ERR_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return TC_ERR_CUDA;
+  int32_t* w = err_word();
+  if (!w) return TC_ERR_CUDA;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return TC_ERR_CUDA;
+  const int32_t zero = 0;
+  if (cudaMemcpy(w, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return TC_ERR_CUDA;
+  *code = v == kDevOk ? TC_OK : v == kDevTimeout ? TC_ERR_DEVICE_TIMEOUT : TC_ERR_DEVICE_BOUNDS;
+  return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// K2 + K5: FP64 mainloop over the block-scatter-matrix view, with the scattered
+// alpha/beta epilogue fused in.
+//
+// The matrix product C_{IJ} = A_{IP} B_{PJ} of Section 4 is tiled into
+// BM x BN output tiles (Section 6.1: partitioning a scatter-matrix is slicing
+// its scatter vectors).  Each CTA gathers its A and B panels straight from the
+// tensors through rscat/cscat (Section 6.1's packing kernel, here a register-
+// staged global->shared gather, coalesced along each operand's own unit-stride
+// index), multiplies them on the FP64 tensor pipe (DMMA, mma.sync m8n8k4 f64),
+// and updates C through rscat(C) + cscat(C) (Section 6.1's scattered
+// micro-tile update), reading C only when beta != 0.
+//
+// GB300 has no tcgen05 kind for FP64, and its FP64 rate (DMMA ~= DFMA) is low
+// enough that a register-blocked warp-level DMMA tile keeps the pipe saturated;
+// global traffic is far below HBM bandwidth at every tile size used here.
+#include "kernels.h"
+
+namespace tc {
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 16, NT = 256;
+constexpr int LDA = BM + 8, LDB = BN + 8;  // row pitch (doubles); rows land 64 B apart in banks
+constexpr int A_PER_T = BM * BK / NT;
+constexpr int B_PER_T = BN * BK / NT;
+constexpr size_t kSmem = (size_t)(2 * BK * LDA + 2 * BK * LDB) * sizeof(double) +
+                         (size_t)(2 * BM + 2 * BN) * sizeof(int64_t);
+
+__device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d[0]), "+d"(d[1])
+               : "d"(a), "d"(b));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 1)
+    k_f64(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ c, const ScatterPtrs sp,
+          const int64_t M, const int64_t N, const int64_t K, const double alpha, const double beta,
+          const int a_kc, const int b_kc, const int64_t tiles_n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* As = reinterpret_cast<double*>(smem);  // [2][BK][LDA]
+  double* Bs = As + 2 * BK * LDA;                // [2][BK][LDB]
+  int64_t* sRA = reinterpret_cast<int64_t*>(Bs + 2 * BK * LDB);
+  int64_t* sRC = sRA + BM;
+  int64_t* sCB = sRC + BM;
+  int64_t* sCC = sCB + BN;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tig = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int64_t tile = blockIdx.x;
+  const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+
+  for (int i = tid; i < BM; i += NT) {
+    const int64_t gm = m0 + i;
+    sRA[i] = gm < M ? sp.rA[gm] : 0;
+    sRC[i] = gm < M ? sp.rC[gm] : 0;
+  }
+  for (int i = tid; i < BN; i += NT) {
+    const int64_t gn = n0 + i;
+    sCB[i] = gn < N ? sp.cB[gn] : 0;
+    sCC[i] = gn < N ? sp.cC[gn] : 0;
+  }
+  __syncthreads();
+
+  double acc[4][4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+  double ra[A_PER_T], rb[B_PER_T];
+  const int64_t KT = (K + BK - 1) / BK;
+
+  // element e of a panel -> (row, k) with consecutive threads along the
+  // operand's unit-stride index
+  auto a_coord = [&](int e, int& mm, int& kk) {
+    if (a_kc) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+  };
+  auto b_coord = [&](int e, int& nn, int& kk) {
+    if (b_kc) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+  };
+  auto load = [&](int64_t kt) {
+    const int64_t k0 = kt * BK;
+#pragma unroll
+    for (int i = 0; i < A_PER_T; ++i) {
+      int mm, kk;
+      a_coord(tid + i * NT, mm, kk);
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      ra[i] = (gm < M && gk < K) ? (double)a[sRA[mm] + sp.cA[gk]] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER_T; ++i) {
+      int nn, kk;
+      b_coord(tid + i * NT, nn, kk);
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      rb[i] = (gn < N && gk < K) ? (double)b[sp.rB[gk] + sCB[nn]] : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < A_PER_T; ++i) {
+      int mm, kk;
+      a_coord(tid + i * NT, mm, kk);
+      As[(buf * BK + kk) * LDA + mm] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER_T; ++i) {
+      int nn, kk;
+      b_coord(tid + i * NT, nn, kk);
+      Bs[(buf * BK + kk) * LDB + nn] = rb[i];
+    }
+  };
+
+  if (KT > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t kt = 0; kt < KT; ++kt) {
+    const int buf = (int)(kt & 1);
+    if (kt + 1 < KT) load(kt + 1);
+    const double* Ab = As + buf * BK * LDA + wm * 32 + g;
+    const double* Bb = Bs + buf * BK * LDB + wn * 32 + g;
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) af[i] = Ab[(kk + tig) * LDA + i * 8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bf[j] = Bb[(kk + tig) * LDB + j * 8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+    }
+    if (kt + 1 < KT) store(buf ^ 1);
+    __syncthreads();
+  }
+
+  // K5: scattered epilogue, C[rscat + cscat] = alpha * acc + beta * C
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
+        if (m0 + mm < M && n0 + nn < N) {
+          T* p = c + sRC[mm] + sCC[nn];
+          double v = alpha * acc[i][j][q];
+          if (beta != 0.0) v += beta * (double)*p;
+          *p = (T)v;
+        }
+      }
+}
+
+template <typename T>
+cudaError_t launch_t(const F64Launch& p, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_f64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int64_t tm = (p.m + BM - 1) / BM, tn = (p.n + BN - 1) / BN;
+  const int64_t tiles = tm * tn;
+  if (tiles == 0) return cudaSuccess;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  mainloop_event_before(s);
+  k_f64<T><<<(unsigned)tiles, NT, kSmem, s>>>((const T*)p.a, (const T*)p.b, (T*)p.c, p.sp, p.m,
+                                               p.n, p.k, p.alpha, p.beta, p.a_k_contig,
+                                               p.b_k_contig, tn);
+  note_launch();
+  mainloop_event_after(s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_f64(const F64Launch& p, cudaStream_t s) {
+  return p.dtype == TC_F64 ? launch_t<double>(p, s) : launch_t<float>(p, s);
+}
+
+}  // namespace tc

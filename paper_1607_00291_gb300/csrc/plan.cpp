@@ -1,0 +1,270 @@
+// Host planner: validation, index bundling and the dimension heuristic.
+//
+// Section 4 defines the bundles: labels of A and C form I, of B and C form J,
+// of A and B form P; each label lies in exactly two tensors with one length.
+// Section 7.3 gives the purely logical reordering applied here, in order:
+//   1. drop dims of length one;
+//   2. fold dims that are sequentially contiguous in every tensor of the bundle
+//      (x, y fold when s_y(T) == s_x(T) * n_x for both tensors T);
+//   3. sort I and J by increasing |stride| in C (stable in C's label order);
+//   4. if the first J dim has stride 1 in C, exchange A and B (and I and J),
+//      i.e. compute C^T = B^T A^T so that C's unit stride runs along M;
+//   5. sort P by increasing |stride| in A (stable in the original A's order).
+// No data moves; the result only fixes the iteration order of the kernels.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "tc_internal.h"
+
+namespace tc {
+namespace {
+
+struct LDim {
+  int64_t len;
+  int64_t s0, s1;
+  char labels[kMaxRank + 1];
+  int nlab;
+};
+
+int find(const tc_tensor* T, char x) {
+  for (int d = 0; d < T->rank; ++d)
+    if (T->labels[d] == x) return d;
+  return -1;
+}
+
+int check_tensor(const tc_tensor* T) {
+  if (!T) return TC_ERR_ARG;
+  if (T->rank < 0 || T->rank > kMaxRank) return TC_ERR_ARG;
+  if (T->rank > 0 && (!T->len || !T->stride || !T->labels)) return TC_ERR_ARG;
+  for (int d = 0; d < T->rank; ++d)
+    if (T->len[d] < 0) return TC_ERR_ARG;
+  for (int d = 0; d < T->rank; ++d)
+    for (int e = d + 1; e < T->rank; ++e)
+      if (T->labels[d] == T->labels[e]) return TC_ERR_LABEL;
+  return TC_OK;
+}
+
+int64_t numel(const tc_tensor* T) {
+  int64_t n = 1;
+  for (int d = 0; d < T->rank; ++d) n *= T->len[d];
+  return n;
+}
+
+// C must not overlap itself.  Sufficient test: with its dims of length > 1
+// sorted by |stride|, every |stride| exceeds the largest offset reachable with
+// the dims before it.
+bool self_overlaps(const tc_tensor* C) {
+  if (numel(C) == 0) return false;
+  int64_t ls[kMaxRank][2];
+  int n = 0;
+  for (int d = 0; d < C->rank; ++d)
+    if (C->len[d] > 1) {
+      ls[n][0] = std::llabs(C->stride[d]);
+      ls[n][1] = C->len[d];
+      ++n;
+    }
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && ls[j][0] < ls[j - 1][0]; --j) std::swap(ls[j], ls[j - 1]);
+  // span = 1 + largest offset reachable with the dims so far
+  int64_t span = 1;
+  for (int i = 0; i < n; ++i) {
+    if (ls[i][0] < span) return true;
+    span += (ls[i][1] - 1) * ls[i][0];
+  }
+  return false;
+}
+
+// Byte range [lo, hi] touched by a tensor (empty tensors touch nothing).
+bool byte_range(const tc_tensor* T, size_t es, intptr_t* lo, intptr_t* hi) {
+  if (numel(T) == 0) return false;
+  int64_t mn = 0, mx = 0;
+  for (int d = 0; d < T->rank; ++d) {
+    int64_t ext = (T->len[d] - 1) * T->stride[d];
+    if (ext < 0) mn += ext; else mx += ext;
+  }
+  *lo = reinterpret_cast<intptr_t>(T->data) + mn * (int64_t)es;
+  *hi = reinterpret_cast<intptr_t>(T->data) + mx * (int64_t)es + (intptr_t)es - 1;
+  return true;
+}
+
+void fold(LDim* d, int& n) {
+  bool merged = true;
+  while (merged) {
+    merged = false;
+    for (int i = 0; i < n && !merged; ++i)
+      for (int j = 0; j < n && !merged; ++j) {
+        if (i == j) continue;
+        if (d[j].s0 == d[i].s0 * d[i].len && d[j].s1 == d[i].s1 * d[i].len) {
+          LDim x = d[i];
+          x.len = d[i].len * d[j].len;
+          for (int q = 0; q < d[j].nlab; ++q) x.labels[x.nlab++] = d[j].labels[q];
+          x.labels[x.nlab] = 0;
+          d[i] = x;
+          for (int q = j; q + 1 < n; ++q) d[q] = d[q + 1];
+          --n;
+          merged = true;
+        }
+      }
+  }
+}
+
+template <typename Key>
+void stable_sort(LDim* d, int n, Key key) {
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && key(d[j]) < key(d[j - 1]); --j) std::swap(d[j], d[j - 1]);
+}
+
+}  // namespace
+
+int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Planned* out) {
+  int rc;
+  if ((rc = check_tensor(A)) || (rc = check_tensor(B)) || (rc = check_tensor(C))) return rc;
+  std::memset(out, 0, sizeof(*out));
+
+  LDim I[kMaxRank], J[kMaxRank], P[kMaxRank];
+  int nI = 0, nJ = 0, nP = 0;
+  // a1: classify (Section 4)
+  for (int d = 0; d < C->rank; ++d) {
+    int ia = find(A, C->labels[d]), ib = find(B, C->labels[d]);
+    if ((ia < 0) == (ib < 0)) return TC_ERR_LABEL;
+    LDim x;
+    x.len = C->len[d];
+    x.s1 = C->stride[d];
+    x.labels[0] = C->labels[d];
+    x.labels[1] = 0;
+    x.nlab = 1;
+    if (ia >= 0) {
+      if (A->len[ia] != C->len[d]) return TC_ERR_EXTENT;
+      x.s0 = A->stride[ia];
+      I[nI++] = x;
+    } else {
+      if (B->len[ib] != C->len[d]) return TC_ERR_EXTENT;
+      x.s0 = B->stride[ib];
+      J[nJ++] = x;
+    }
+  }
+  for (int d = 0; d < A->rank; ++d) {
+    if (find(C, A->labels[d]) >= 0) continue;
+    int ib = find(B, A->labels[d]);
+    if (ib < 0) return TC_ERR_LABEL;
+    if (B->len[ib] != A->len[d]) return TC_ERR_EXTENT;
+    LDim x;
+    x.len = A->len[d];
+    x.s0 = A->stride[d];
+    x.s1 = B->stride[ib];
+    x.labels[0] = A->labels[d];
+    x.labels[1] = 0;
+    x.nlab = 1;
+    P[nP++] = x;
+  }
+  for (int d = 0; d < B->rank; ++d)
+    if (find(C, B->labels[d]) < 0 && find(A, B->labels[d]) < 0) return TC_ERR_LABEL;
+  if (self_overlaps(C)) return TC_ERR_OVERLAP;
+
+  // a2 step 1: drop length-one dims
+  auto drop1 = [](LDim* d, int& n) {
+    int w = 0;
+    for (int i = 0; i < n; ++i)
+      if (d[i].len != 1) d[w++] = d[i];
+    n = w;
+  };
+  drop1(I, nI);
+  drop1(J, nJ);
+  drop1(P, nP);
+  // step 2: fold sequentially contiguous dims
+  fold(I, nI);
+  fold(J, nJ);
+  fold(P, nP);
+  // step 3: sort I and J by |stride| in C
+  stable_sort(I, nI, [](const LDim& x) { return std::llabs(x.s1); });
+  stable_sort(J, nJ, [](const LDim& x) { return std::llabs(x.s1); });
+  // step 4: swap when C's unit stride lies in J
+  bool swapped = false;
+  if (nJ > 0 && J[0].s1 == 1) {
+    swapped = true;
+    LDim t[kMaxRank];
+    int nt = nI;
+    std::memcpy(t, I, sizeof(LDim) * nI);
+    std::memcpy(I, J, sizeof(LDim) * nJ);
+    nI = nJ;
+    std::memcpy(J, t, sizeof(LDim) * nt);
+    nJ = nt;
+    for (int i = 0; i < nP; ++i) std::swap(P[i].s0, P[i].s1);
+  }
+  // step 5: sort P by |stride| in A
+  stable_sort(P, nP, [](const LDim& x) { return std::llabs(x.s0); });
+
+  Layout& L = out->L;
+  tc_plan_info& info = out->info;
+  auto put = [](Bundle& b, const LDim* d, int n, int64_t* len, int64_t* s0, int64_t* s1,
+                char (*labs)[kMaxRank + 1]) {
+    b.nd = n;
+    int64_t prod = 1;
+    for (int i = 0; i < n; ++i) {
+      b.len[i] = len[i] = d[i].len;
+      b.s0[i] = s0[i] = d[i].s0;
+      b.s1[i] = s1[i] = d[i].s1;
+      std::memcpy(labs[i], d[i].labels, kMaxRank + 1);
+      prod *= d[i].len;
+    }
+    return prod;
+  };
+  L.m = put(L.I, I, nI, info.I_len, info.I_sA, info.I_sC, info.I_labels);
+  L.n = put(L.J, J, nJ, info.J_len, info.J_sB, info.J_sC, info.J_labels);
+  L.k = put(L.P, P, nP, info.P_len, info.P_sA, info.P_sB, info.P_labels);
+  // a length-0 dim was kept by step 1, so a product of 0 means an empty range
+  info.swapped = swapped;
+  info.nI = nI;
+  info.nJ = nJ;
+  info.nP = nP;
+  info.m = L.m;
+  info.n = L.n;
+  info.k = L.k;
+
+  // a3: stride-1 preference per operand
+  auto minabs = [](const int64_t* s, int n) {
+    int64_t v = INT64_MAX;
+    for (int i = 0; i < n; ++i) v = std::min<int64_t>(v, std::llabs(s[i]));
+    return v;
+  };
+  info.a_k_contig = nP > 0 && (nI == 0 || minabs(L.P.s0, nP) < minabs(L.I.s0, nI));
+  info.b_k_contig = nP > 0 && (nJ == 0 || minabs(L.P.s1, nP) < minabs(L.J.s0, nJ));
+  info.c_m_contig = nJ == 0 || (nI > 0 && minabs(L.I.s1, nI) <= minabs(L.J.s1, nJ));
+
+  out->a = swapped ? B->data : A->data;
+  out->b = swapped ? A->data : B->data;
+  out->c = C->data;
+  return TC_OK;
+}
+
+ScatterOffsets scatter_offsets(const Layout& L, int32_t b) {
+  ScatterOffsets o;
+  auto nb = [b](int64_t l) { return (l + b - 1) / b; };
+  int64_t p = 0;
+  o.rA = p; p += L.m;
+  o.cA = p; p += L.k;
+  o.rB = p; p += L.k;
+  o.cB = p; p += L.n;
+  o.rC = p; p += L.m;
+  o.cC = p; p += L.n;
+  o.rbsA = p; p += nb(L.m);
+  o.cbsA = p; p += nb(L.k);
+  o.rbsB = p; p += nb(L.k);
+  o.cbsB = p; p += nb(L.n);
+  o.rbsC = p; p += nb(L.m);
+  o.cbsC = p; p += nb(L.n);
+  o.total = p;
+  return o;
+}
+
+// Exposed for the API layer.
+int aliases(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, size_t es) {
+  intptr_t clo, chi, lo, hi;
+  if (!byte_range(C, es, &clo, &chi)) return 0;
+  if (byte_range(A, es, &lo, &hi) && !(hi < clo || chi < lo)) return 1;
+  if (byte_range(B, es, &lo, &hi) && !(hi < clo || chi < lo)) return 1;
+  return 0;
+}
+
+}  // namespace tc

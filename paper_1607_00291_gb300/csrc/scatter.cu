@@ -1,0 +1,139 @@
+// K1: device construction of the scatter and block-scatter vectors.
+//
+// Section 6.1: for a bundle with dims (n_0, s_0), (n_1, s_1), ... the scatter
+// vector maps the linearised index x (dim 0 fastest) to the tensor offset
+// scat[x] = sum_d u_d(x) s_d.  A matrix view C_{IJ} of a tensor then has
+// loc(C_{IJ}) = rscat_I(C) + cscat_J(C); A uses rscat over I and cscat over P,
+// B rscat over P and cscat over J.
+// Section 6.2: the block-scatter vector with blocking parameter b holds, per
+// block of b consecutive entries, the common difference s > 0 of the entries
+// when there is one and 0 otherwise (one-element blocks get 1).
+//
+// GPU form: one thread per output entry; each block-scatter entry recomputes
+// the scatter values of its own block, so the kernel needs no second pass.
+#include "kernels.h"
+
+namespace tc {
+namespace {
+
+__device__ __forceinline__ int64_t scat_at(const int64_t* len, const int64_t* s, int nd,
+                                           int64_t x) {
+  int64_t v = 0;
+  for (int d = 0; d < nd; ++d) {
+    int64_t q = x / len[d];
+    v += (x - q * len[d]) * s[d];
+    x = q;
+  }
+  return v;
+}
+
+struct Section {
+  const int64_t* len;
+  const int64_t* s;
+  int nd;
+  int64_t l;
+};
+
+__device__ __forceinline__ Section section(const Layout& L, int which) {
+  // 0 rA: I/A   1 cA: P/A   2 rB: P/B   3 cB: J/B   4 rC: I/C   5 cC: J/C
+  switch (which) {
+    case 0: return {L.I.len, L.I.s0, L.I.nd, L.m};
+    case 1: return {L.P.len, L.P.s0, L.P.nd, L.k};
+    case 2: return {L.P.len, L.P.s1, L.P.nd, L.k};
+    case 3: return {L.J.len, L.J.s0, L.J.nd, L.n};
+    case 4: return {L.I.len, L.I.s1, L.I.nd, L.m};
+    default: return {L.J.len, L.J.s1, L.J.nd, L.n};
+  }
+}
+
+__global__ void k_build_scatter(const Layout L, const int32_t b, const ScatterOffsets o,
+                                int64_t* __restrict__ out) {
+  const int64_t starts[12] = {o.rA, o.cA, o.rB, o.cB, o.rC, o.cC,
+                              o.rbsA, o.cbsA, o.rbsB, o.cbsB, o.rbsC, o.cbsC};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < o.total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int sec = 0;
+    while (sec < 11 && t >= starts[sec + 1]) ++sec;
+    const int64_t x = t - starts[sec];
+    if (sec < 6) {
+      Section S = section(L, sec);
+      out[t] = scat_at(S.len, S.s, S.nd, x);
+    } else {
+      Section S = section(L, sec - 6);
+      const int64_t lo = x * b;
+      const int64_t hi = lo + b < S.l ? lo + b : S.l;
+      int64_t v;
+      if (hi - lo <= 1) {
+        v = 1;
+      } else {
+        int64_t prev = scat_at(S.len, S.s, S.nd, lo);
+        int64_t cur = scat_at(S.len, S.s, S.nd, lo + 1);
+        const int64_t st = cur - prev;
+        bool ok = st > 0;
+        for (int64_t j = lo + 2; j < hi && ok; ++j) {
+          prev = cur;
+          cur = scat_at(S.len, S.s, S.nd, j);
+          ok = (cur - prev) == st;
+        }
+        v = ok ? st : 0;
+      }
+      out[t] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale_c(T* __restrict__ c, const int64_t* __restrict__ rC,
+                          const int64_t* __restrict__ cC, int64_t m, int64_t n, double beta) {
+  const int64_t total = m * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % m, j = t / m;
+    T* p = c + rC[i] + cC[j];
+    *p = beta == 0.0 ? T(0) : T(beta * (double)*p);
+  }
+}
+
+}  // namespace
+
+ScatterPtrs scatter_ptrs(const int64_t* base, const ScatterOffsets& o) {
+  ScatterPtrs p;
+  p.rA = base + o.rA;
+  p.cA = base + o.cA;
+  p.rB = base + o.rB;
+  p.cB = base + o.cB;
+  p.rC = base + o.rC;
+  p.cC = base + o.cC;
+  p.rbsA = base + o.rbsA;
+  p.cbsA = base + o.cbsA;
+  p.rbsB = base + o.rbsB;
+  p.cbsB = base + o.cbsB;
+  p.rbsC = base + o.rbsC;
+  p.cbsC = base + o.cbsC;
+  return p;
+}
+
+cudaError_t launch_build_scatter(const Layout& L, int32_t b, int64_t* out, cudaStream_t s) {
+  const ScatterOffsets o = scatter_offsets(L, b);
+  if (o.total == 0) return cudaSuccess;
+  int64_t blocks = (o.total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_build_scatter<<<(int)blocks, 256, 0, s>>>(L, b, o, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_c(tc_dtype dt, void* c, const ScatterPtrs& sp, int64_t m, int64_t n,
+                           double beta, cudaStream_t s) {
+  if (beta == 1.0 || m == 0 || n == 0) return cudaSuccess;
+  int64_t blocks = (m * n + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  if (dt == TC_F64)
+    k_scale_c<double><<<(int)blocks, 256, 0, s>>>((double*)c, sp.rC, sp.cC, m, n, beta);
+  else
+    k_scale_c<float><<<(int)blocks, 256, 0, s>>>((float*)c, sp.rC, sp.cC, m, n, beta);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace tc

@@ -1,0 +1,63 @@
+// Internal types shared by the planner and the kernels of libtc.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr int kMaxRank = TC_MAX_RANK;
+
+// One index bundle after normalisation: lengths and the strides of the bundle
+// dims in the two tensors that hold it (I: A, C; J: B, C; P: A, B).  The
+// bundle's linearised index runs colexicographically over the dims (dim 0
+// fastest), which is the matrix index of Section 6.1.
+struct Bundle {
+  int32_t nd;
+  int64_t len[kMaxRank];
+  int64_t s0[kMaxRank];
+  int64_t s1[kMaxRank];
+};
+
+// The matrix view of one contraction: C_{IJ} (m x n) = A_{IP} (m x k) B_{PJ} (k x n).
+struct Layout {
+  int64_t m, n, k;
+  Bundle I;  // s0 = stride in A, s1 = stride in C
+  Bundle J;  // s0 = stride in B, s1 = stride in C
+  Bundle P;  // s0 = stride in A, s1 = stride in B
+};
+
+// A planned contraction (host side).  a/b are the operands in their matrix
+// roles, i.e. already exchanged when info.swapped.
+struct Planned {
+  Layout L;
+  tc_plan_info info;
+  const void* a;
+  const void* b;
+  void* c;
+};
+
+// Validation + Section 7.3 normalisation.  Returns TC_OK or an error code.
+int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Planned* out);
+
+// Scatter-vector section offsets inside a workspace (int64 entries).
+struct ScatterOffsets {
+  int64_t rA, cA, rB, cB, rC, cC;        // scatter vectors
+  int64_t rbsA, cbsA, rbsB, cbsB, rbsC, cbsC;  // block-scatter vectors
+  int64_t total;                           // entries
+};
+ScatterOffsets scatter_offsets(const Layout& L, int32_t b);
+
+// Block size of the block-scatter vectors the mainloops consult.
+constexpr int32_t kBsBlock = 4;
+
+// Device error word codes (shared by all kernels).
+constexpr int32_t kDevOk = 0;
+constexpr int32_t kDevTimeout = 1;
+constexpr int32_t kDevBounds = 2;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace tc

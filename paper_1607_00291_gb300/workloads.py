@@ -1,0 +1,174 @@
+"""Seeded synthetic workloads (shapes, layouts, value distributions).
+
+This module holds no arithmetic of the method: it only defines the contraction
+shapes the benchmarks and tests use and draws their inputs from seeded
+generators, in FP64 on the host.  The same host arrays feed both the CUDA path
+and the CPU oracle.
+
+Layout convention: "column-major" means general column-major order (Section 5):
+the first index has stride 1 and each further stride is the product of the
+lengths before it.
+"""
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+import torch
+
+
+@dataclass
+class Spec:
+    name: str
+    labA: str
+    labB: str
+    labC: str
+    ext: Dict[str, int]
+    dtype: torch.dtype
+    alpha: float
+    beta: float
+    dist: str = "uniform"          # uniform[-1,1] | normal | uniform_spiky
+    c_init: str = "zeros"          # zeros | uniform | nan
+    mode: str = "f64"
+
+    def shape(self, lab: str) -> Tuple[int, ...]:
+        return tuple(self.ext[x] for x in lab)
+
+    def flops(self) -> float:
+        return 2.0 * float(np.prod([self.ext[x] for x in set(self.labA + self.labB + self.labC)]))
+
+
+# The five workload shapes measured by bench.py and the tests.
+SPECS = {
+    # FP64, abcd <- aebf . dfce, every extent 16 (256^3 as a matrix product)
+    "small_f64": Spec("small_f64", "aebf", "dfce", "abcd", dict.fromkeys("abcdef", 16),
+                      torch.float64, 1.0, 0.0),
+    # FP64 coupled-cluster-style abij <- cadb . icjd, a..d = 96, i, j = 24
+    "cc4x4_f64": Spec("cc4x4_f64", "cadb", "icjd", "abij",
+                      dict(a=96, b=96, c=96, d=96, i=24, j=24), torch.float64, 0.5, 1.0,
+                      c_init="uniform"),
+    # FP32 abcd <- eafb . cfde, all 64, 1% of entries scaled by 1e3, BF16x3 mode
+    "spiky_f32": Spec("spiky_f32", "eafb", "cfde", "abcd", dict.fromkeys("abcdef", 64),
+                      torch.float32, 1.0, 0.0, dist="uniform_spiky", mode="bf16x3"),
+    # FP32 ijk <- ilmj . mkl, i, j, k = 128, l, m = 64, normal inputs, forward + backward
+    "grad_f32": Spec("grad_f32", "ilmj", "mkl", "ijk", dict(i=128, j=128, k=128, l=64, m=64),
+                     torch.float32, 1.0, 0.0, dist="normal", mode="bf16x3"),
+}
+
+
+def colmajor(flat: torch.Tensor, shape) -> torch.Tensor:
+    """View a flat tensor as `shape` in general column-major order."""
+    r = len(shape)
+    if r == 0:
+        return flat.reshape(())
+    return flat.reshape(tuple(reversed(shape))).permute(*reversed(range(r)))
+
+
+def _draw(g: torch.Generator, n: int, dist: str) -> torch.Tensor:
+    if dist == "uniform":
+        return torch.rand(n, generator=g, dtype=torch.float64) * 2 - 1
+    if dist == "normal":
+        return torch.randn(n, generator=g, dtype=torch.float64)
+    if dist == "uniform_spiky":
+        x = torch.rand(n, generator=g, dtype=torch.float64) * 2 - 1
+        mask = torch.rand(n, generator=g, dtype=torch.float64) < 0.01
+        return torch.where(mask, x * 1e3, x)
+    if dist == "int":
+        return torch.randint(-8, 9, (n,), generator=g).to(torch.float64)
+    raise ValueError(dist)
+
+
+def make_inputs(spec: Spec, seed: int, dist: Optional[str] = None):
+    """Host FP64 arrays (column-major) for A, B and the initial C, already
+    rounded to spec.dtype (so the oracle sees exactly the device values)."""
+    g = torch.Generator().manual_seed(seed)
+    dist = dist or spec.dist
+    out = {}
+    for name, lab in (("A", spec.labA), ("B", spec.labB)):
+        shape = spec.shape(lab)
+        n = int(np.prod(shape)) if shape else 1
+        out[name] = colmajor(_draw(g, n, dist).to(spec.dtype).to(torch.float64), shape)
+    shape = spec.shape(spec.labC)
+    n = int(np.prod(shape)) if shape else 1
+    if spec.c_init == "zeros":
+        c = torch.zeros(n, dtype=torch.float64)
+    elif spec.c_init == "nan":
+        c = torch.full((n,), float("nan"), dtype=torch.float64)
+    else:
+        c = _draw(g, n, "uniform" if dist != "int" else "int")
+    out["C"] = colmajor(c.to(spec.dtype).to(torch.float64), shape)
+    return out
+
+
+# ---- random contractions (batch workloads, parity sweeps) ---------------------------
+
+LETTERS = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+
+
+@dataclass
+class RandomProblem:
+    labA: str
+    labB: str
+    labC: str
+    ext: Dict[str, int]
+    # per-tensor dimension order of the storage (a permutation of the labels),
+    # giving a dense layout with randomly permuted strides
+    orderA: str = ""
+    orderB: str = ""
+    orderC: str = ""
+    alpha: float = 1.0
+    beta: float = 0.0
+
+    def flops(self):
+        return 2.0 * float(np.prod([self.ext[x] for x in set(self.labA + self.labB + self.labC)]))
+
+
+def random_problem(rng: np.random.Generator, dI=(1, 3), dJ=(1, 3), dP=(1, 3), ext=(8, 64),
+                   max_rank: int = 6, max_elems: int = 1 << 22, max_flops: float = 2.0 ** 34,
+                   allow_zero_bundles: bool = False) -> RandomProblem:
+    """Draw a contraction with d_I, d_J, d_P dims, extents uniform in `ext`,
+    random label orders in A, B, C and randomly permuted dense strides.
+    Redraws until every operand has at most `max_elems` elements and the flop
+    count is at most `max_flops`."""
+    lo = 0 if allow_zero_bundles else 1
+    while True:
+        nP = int(rng.integers(dP[0], dP[1] + 1))
+        nI = int(rng.integers(max(lo, dI[0]), dI[1] + 1))
+        nJ = int(rng.integers(max(lo, dJ[0]), dJ[1] + 1))
+        if nI + nP > max_rank or nJ + nP > max_rank or nI + nJ > max_rank:
+            continue
+        labs = list(rng.permutation(list(LETTERS[:nI + nJ + nP])))
+        I, J, P = labs[:nI], labs[nI:nI + nJ], labs[nI + nJ:]
+        e = {x: int(rng.integers(ext[0], ext[1] + 1)) for x in labs}
+        A = "".join(rng.permutation(I + P)) if I + P else ""
+        B = "".join(rng.permutation(P + J)) if P + J else ""
+        C = "".join(rng.permutation(I + J)) if I + J else ""
+        size = lambda s: int(np.prod([e[x] for x in s])) if s else 1
+        if max(size(A), size(B), size(C)) > max_elems:
+            continue
+        fl = 2.0 * size(I) * size(J) * size(P)
+        if fl > max_flops:
+            continue
+        oA = "".join(rng.permutation(list(A))) if A else ""
+        oB = "".join(rng.permutation(list(B))) if B else ""
+        oC = "".join(rng.permutation(list(C))) if C else ""
+        return RandomProblem(A, B, C, e, oA, oB, oC)
+
+
+def dense_permuted(flat: torch.Tensor, labels: str, order: str, ext: Dict[str, int]) -> torch.Tensor:
+    """View `flat` as a tensor indexed by `labels` whose storage is column-major
+    in the label order `order`."""
+    if not labels:
+        return flat.reshape(())
+    base = colmajor(flat, tuple(ext[x] for x in order))
+    perm = [order.index(x) for x in labels]
+    return base.permute(*perm)
+
+
+def make_random_inputs(p: RandomProblem, seed: int, dtype=torch.float64, dist: str = "uniform"):
+    g = torch.Generator().manual_seed(seed)
+    out = {}
+    for name, lab, order in (("A", p.labA, p.orderA), ("B", p.labB, p.orderB), ("C", p.labC, p.orderC)):
+        n = int(np.prod([p.ext[x] for x in lab])) if lab else 1
+        flat = _draw(g, n, dist).to(dtype).to(torch.float64)
+        out[name] = dense_permuted(flat, lab, order or lab, p.ext)
+    return out

@@ -1,0 +1,103 @@
+"""Host-side planning of libtc (no GPU): the C++ planner behind the C ABI
+against the oracle's restatement of Sections 4 and 7.3, plus error codes."""
+import numpy as np
+import pytest
+
+import oracle.bundle as ob
+import paper_1607_00291_gb300 as tc
+from paper_1607_00291_gb300 import _lib as L
+from paper_1607_00291_gb300 import workloads as W
+
+
+def cm(lab, ext):
+    acc, st = 1, []
+    for x in lab:
+        st.append(acc)
+        acc *= ext[x]
+    return tuple(ext[x] for x in lab), tuple(st)
+
+
+def compare(labA, sA, labB, sB, labC, sC):
+    got = tc.plan_describe(sA, labA, sB, labB, sC, labC)
+    ref = ob.normalize((labA, *sA), (labB, *sB), (labC, *sC))
+    assert got["swapped"] == ref.swapped
+    assert (got["m"], got["n"], got["k"]) == (ref.m, ref.n, ref.k)
+    for name, rb, key in (("I", ref.I, ("A", "C")), ("J", ref.J, ("B", "C")), ("P", ref.P, ("A", "B"))):
+        gb = got[name]
+        assert [d["labels"] for d in gb] == ["".join(d.labels) for d in rb], name
+        assert [d["n"] for d in gb] == [d.n for d in rb]
+        assert [tuple(d["s"]) for d in gb] == [(d.s[key[0]], d.s[key[1]]) for d in rb]
+    return got
+
+
+def test_worked_example_plan():
+    ext = dict(a=6, b=3, c=2, d=3, e=4, f=4)
+    g = compare("cfbd", cm("cfbd", ext), "fea", cm("fea", ext), "abcde", cm("abcde", ext))
+    assert g["m"] * g["n"] == 6 * 3 * 2 * 3 * 4 and g["k"] == 4
+
+
+def test_tilde_fold_plan():
+    ext = dict(a=6, b=3, c=2, d=3, e=4, f=4)
+    g = compare("cdbf", cm("cdbf", ext), "fae", cm("fae", ext), "cdbae", cm("cdbae", ext))
+    assert (len(g["I"]), len(g["J"]), len(g["P"])) == (1, 1, 1)
+    assert g["I"][0]["labels"] == "cdb" and g["J"][0]["labels"] == "ae"
+
+
+def test_benchmark_shapes_plan():
+    for spec in W.SPECS.values():
+        e = spec.ext
+        g = compare(spec.labA, cm(spec.labA, e), spec.labB, cm(spec.labB, e), spec.labC, cm(spec.labC, e))
+        assert g["c_m_contig"]
+    cc = W.SPECS["cc4x4_f64"]
+    g = tc.plan_describe(cm(cc.labA, cc.ext), cc.labA, cm(cc.labB, cc.ext), cc.labB, cm(cc.labC, cc.ext), cc.labC)
+    assert (g["m"], g["n"], g["k"]) == (9216, 576, 9216)
+    assert g["a_k_contig"] and not g["b_k_contig"]
+
+
+def test_random_plans_match_oracle():
+    rng = np.random.default_rng(0)
+    for t in range(300):
+        p = W.random_problem(rng, dI=(0, 3), dJ=(0, 3), dP=(0, 3), ext=(1, 6), allow_zero_bundles=True)
+        # random dense permuted layouts, plus sometimes padded or negative strides
+        def lay(lab, order):
+            acc, st = 1, {}
+            for x in order:
+                st[x] = acc
+                acc *= p.ext[x] + (1 if rng.random() < 0.2 else 0)
+            sgn = {x: (-1 if rng.random() < 0.1 else 1) for x in lab}
+            return tuple(p.ext[x] for x in lab), tuple(sgn[x] * st[x] for x in lab)
+        compare(p.labA, lay(p.labA, p.orderA), p.labB, lay(p.labB, p.orderB), p.labC,
+                lay(p.labC, p.orderC))
+
+
+def test_error_codes():
+    def code(labA, shA, labB, shB, labC, shC, stC=None):
+        keep = []
+        tA = L.make_tensor(shA, [1] * len(shA), labA, 0, keep)
+        tB = L.make_tensor(shB, [1] * len(shB), labB, 0, keep)
+        stC = stC or cm(labC, dict(zip(labC, shC)))[1]
+        tC = L.make_tensor(shC, stC, labC, 0, keep)
+        info = L.TcPlanInfo()
+        return L.lib().tc_plan_describe(tA, tB, tC, info)
+    assert code("ab", (2, 3), "bc", (3, 4), "ac", (2, 4)) == 0
+    assert code("ab", (2, 3), "bc", (3, 4), "ad", (2, 4)) == -2       # label in one tensor
+    assert code("ab", (2, 3), "bc", (3, 4), "abc", (2, 3, 4)) == -2   # label in all three
+    assert code("aa", (2, 2), "a", (2,), "", ()) == -2                # repeated label
+    assert code("ab", (2, 3), "bc", (4, 4), "ac", (2, 4)) == -3       # extent mismatch
+    assert code("ab", (2, 3), "bc", (3, 4), "ac", (2, 4), (1, 1)) == -4  # C overlaps itself
+    assert code("ab", (2, 3), "bc", (3, 4), "ac", (2, 4), (4, 1)) == 0   # row-major C is fine
+    keep = []
+    assert L.lib().tc_plan_describe(None, None, None, L.TcPlanInfo()) == -1
+    t = L.make_tensor((2,), (1,), "a", 0, keep)
+    t.rank = 17
+    assert L.lib().tc_plan_describe(t, t, t, L.TcPlanInfo()) == -1
+
+
+def test_workspace_is_vector_sized_not_operand_sized():
+    cc = W.SPECS["cc4x4_f64"]
+    keep = []
+    ds = [L.make_tensor(*cm(lab, cc.ext), lab, 0, keep) for lab in (cc.labA, cc.labB, cc.labC)]
+    n = L.c_sz(0)
+    assert L.lib().tc_workspace_size(L.TC_F64, L.TC_MODE_F64, *ds, n) == 0
+    m, nn, k = 9216, 576, 9216
+    assert n.value < 16 * 8 * (m + nn + k) + 4096  # O(m + n + k), far below the 680 MB operand
