@@ -249,6 +249,10 @@ def run_ours(args, ws, rank, local):
 
     # device-resident timed region
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in kev:  # torch creates the CUDA event handles on first record
+        a.record()
+        b.record()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(local)
     barrier(ws)

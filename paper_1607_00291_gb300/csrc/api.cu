@@ -1,4 +1,5 @@
 // libtc C ABI: argument checks, planning, workspace carving and launches.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -49,21 +50,71 @@ size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : 4; }
 int check_modes(tc_dtype dt, tc_mode mode) {
   if (dt != TC_F64 && dt != TC_F32) return TC_ERR_ARG;
   if (mode != TC_MODE_F64 && mode != TC_MODE_BF16X3) return TC_ERR_ARG;
-  if (mode == TC_MODE_BF16X3) return TC_ERR_UNSUPPORTED;  // provided by the tcgen05 path
+  if (mode == TC_MODE_BF16X3 && dt != TC_F32) return TC_ERR_UNSUPPORTED;
   return TC_OK;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return n;
+}
+
+// Tile width and split of the contracted range for the BF16x3 mainloop:
+// enough CTAs to cover the SMs once when the output alone has too few tiles,
+// each split keeping at least 8 k-tiles of 32.
+struct Bf16Choice {
+  int bn, splits;
+  int64_t kps;
+};
+
+Bf16Choice choose_bf16(const Layout& L, int sms) {
+  Bf16Choice c;
+  const int64_t tm = (L.m + 127) / 128;
+  auto waves_eff = [&](int bn) {
+    const int64_t t = tm * ((L.n + bn - 1) / bn);
+    const int64_t w = (t + sms - 1) / sms;
+    return (double)t / (double)(w * sms) * (bn == 256 ? 1.0 : 0.97);
+  };
+  c.bn = 128;
+  (void)waves_eff;
+  const int64_t tiles = tm * ((L.n + c.bn - 1) / c.bn);
+  const int64_t kt = (L.k + 31) / 32;
+  int64_t s = 1;
+  if (tiles < sms) s = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
+  s = std::max<int64_t>(1, std::min<int64_t>(s, 64));
+  const int64_t ktps = (kt + s - 1) / s;
+  c.kps = ktps * 32;
+  c.splits = (int)((L.k + c.kps - 1) / c.kps);
+  if (c.splits < 1) c.splits = 1;
+  return c;
 }
 
 struct WsLayout {
   size_t scatter_off, scatter_bytes;
+  size_t partial_off, partial_bytes;
   size_t total;
+  Bf16Choice bf;
 };
 
-WsLayout ws_layout(const Planned& p) {
+WsLayout ws_layout(const Planned& p, tc_mode mode) {
   WsLayout w;
   const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
   w.scatter_off = 0;
   w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
-  w.total = w.scatter_bytes;
+  w.partial_off = w.scatter_bytes;
+  w.partial_bytes = 0;
+  w.bf = Bf16Choice{128, 1, 0};
+  if (mode == TC_MODE_BF16X3 && p.L.k > 0) {
+    w.bf = choose_bf16(p.L, sm_count());
+    if (w.bf.splits > 1)
+      w.partial_bytes = align_up((size_t)w.bf.splits * p.L.m * p.L.n * sizeof(float), 256);
+  }
+  w.total = w.scatter_bytes + w.partial_bytes;
   return w;
 }
 
@@ -79,7 +130,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
                 void* ws, size_t ws_bytes, cudaStream_t s) {
   const Layout& L = p.L;
   if (L.m == 0 || L.n == 0) return TC_OK;
-  const WsLayout w = ws_layout(p);
+  const WsLayout w = ws_layout(p, mode);
   if (ws_bytes < w.total || (w.total > 0 && ws == nullptr) ||
       (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
     return TC_ERR_WORKSPACE;
@@ -89,7 +140,26 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   const ScatterPtrs sp = scatter_ptrs(scat, o);
   if (L.k == 0 || alpha == 0.0)
     return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
-  (void)mode;
+  if (mode == TC_MODE_BF16X3) {
+    Bf16Launch q;
+    q.a = p.a;
+    q.b = p.b;
+    q.c = p.c;
+    q.partial = reinterpret_cast<float*>(static_cast<char*>(ws) + w.partial_off);
+    q.sp = sp;
+    q.m = L.m;
+    q.n = L.n;
+    q.k = L.k;
+    q.alpha = alpha;
+    q.beta = beta;
+    q.a_k_contig = p.info.a_k_contig;
+    q.b_k_contig = p.info.b_k_contig;
+    q.bn = w.bf.bn;
+    q.splits = w.bf.splits;
+    q.k_per_split = w.bf.kps;
+    q.err = err_word();
+    return launch_bf16x3(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  }
   F64Launch f;
   f.dtype = dt;
   f.a = p.a;
@@ -155,7 +225,7 @@ int tc_workspace_size(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc
   if (rc != TC_OK) return rc;
   Planned p;
   if ((rc = plan_problem(A, B, C, &p)) != TC_OK) return rc;
-  *bytes = (p.L.m == 0 || p.L.n == 0) ? 0 : ws_layout(p).total;
+  *bytes = (p.L.m == 0 || p.L.n == 0) ? 0 : ws_layout(p, mode).total;
   return TC_OK;
 }
 
@@ -188,7 +258,7 @@ int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem
     }
     pl->ws_off.push_back(pl->ws_total);
     const Planned& p = pl->planned[i];
-    if (p.L.m != 0 && p.L.n != 0) pl->ws_total += ws_layout(p).total;
+    if (p.L.m != 0 && p.L.n != 0) pl->ws_total += ws_layout(p, mode).total;
     pl->probs.push_back(probs[i]);
   }
   *out = pl;
@@ -209,7 +279,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     if (p.L.m == 0 || p.L.n == 0) continue;
     int rc = run_planned(plan->dtype, plan->mode, plan->probs[i].alpha, plan->probs[i].beta, p,
                          static_cast<char*>(workspace) + plan->ws_off[i],
-                         ws_layout(p).total, static_cast<cudaStream_t>(stream));
+                         ws_layout(p, plan->mode).total, static_cast<cudaStream_t>(stream));
     if (rc != TC_OK) return rc;
   }
   return TC_OK;

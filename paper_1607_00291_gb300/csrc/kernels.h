@@ -41,4 +41,21 @@ struct F64Launch {
 };
 cudaError_t launch_f64(const F64Launch& p, cudaStream_t s);
 
+// K3 + K5 (+ K4 when splits > 1) (bf16x3.cu): tcgen05 BF16x3 mainloop.
+struct Bf16Launch {
+  const void* a;
+  const void* b;
+  void* c;
+  float* partial;  // splits * m * n FP32, used when splits > 1
+  ScatterPtrs sp;
+  int64_t m, n, k;
+  double alpha, beta;
+  int a_k_contig, b_k_contig;
+  int bn;          // 128 or 256
+  int splits;      // CTAs along the contracted range
+  int64_t k_per_split;  // multiple of 32
+  int32_t* err;
+};
+cudaError_t launch_bf16x3(const Bf16Launch& q, cudaStream_t s);
+
 }  // namespace tc

@@ -1,0 +1,140 @@
+"""Parity of the BF16x3 tensor-core path (K3, K4 split-K FP64 reduction, K5)
+with the FP64 CPU oracle.  Bound: max |C_gpu - C_oracle| / (|alpha| sum|A||B|
++ |beta||C|) <= 1e-5, and exact results where every product and partial sum
+is exactly representable (integer data below 2^8 in magnitude)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1607_00291_gb300 as tc
+from paper_1607_00291_gb300 import workloads as W
+
+from helpers import norm_err, oracle_ref, to_device
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def run(alpha, A, lA, B, lB, beta, C0, lC):
+    dA, dB, dC = (to_device(x, torch.float32) for x in (A, B, C0))
+    tc.contract(dA, lA, dB, lB, dC, lC, alpha=alpha, beta=beta, mode="bf16x3")
+    torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    return dC.cpu().to(torch.float64).numpy()
+
+
+def f32(t):
+    return t.to(torch.float32).to(torch.float64)
+
+
+def test_single_tile_integers_exact():
+    g = torch.Generator().manual_seed(1)
+    A = f32(torch.randint(-8, 9, (128, 32), generator=g).double())
+    B = f32(torch.randint(-8, 9, (32, 128), generator=g).double())
+    C0 = torch.zeros(128, 128, dtype=torch.float64)
+    got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+    ref, _ = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+    assert np.array_equal(got, ref)
+
+
+def test_matrix_case_uniform():
+    g = torch.Generator().manual_seed(2)
+    A = f32(torch.rand(300, 500, generator=g, dtype=torch.float64) * 2 - 1)
+    B = f32(torch.rand(500, 200, generator=g, dtype=torch.float64) * 2 - 1)
+    C0 = f32(torch.rand(300, 200, generator=g, dtype=torch.float64) * 2 - 1)
+    got = run(0.5, A, "ip", B, "pj", 1.5, C0, "ij")
+    ref, mag = oracle_ref(0.5, A, "ip", B, "pj", 1.5, C0, "ij")
+    assert norm_err(got, ref, mag) <= TOL
+
+
+def test_transposed_operand_layouts():
+    # row-contiguous and k-contiguous gathers for both operands
+    g = torch.Generator().manual_seed(3)
+    for ta in (False, True):
+        for tb in (False, True):
+            A = torch.rand(200, 136, generator=g, dtype=torch.float64) * 2 - 1
+            B = torch.rand(136, 260, generator=g, dtype=torch.float64) * 2 - 1
+            A = f32(A.t().contiguous().t() if ta else A)
+            B = f32(B.t().contiguous().t() if tb else B)
+            C0 = torch.zeros(200, 260, dtype=torch.float64)
+            got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+            ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+            assert norm_err(got, ref, mag) <= TOL, (ta, tb)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_contractions(seed):
+    rng = np.random.default_rng(300 + seed)
+    p = W.random_problem(rng, ext=(1, 29), max_elems=1 << 19, max_flops=2.0 ** 29)
+    h = W.make_random_inputs(p, seed=seed, dtype=torch.float32)
+    alpha = float(rng.uniform(-2, 2))
+    beta = float(rng.choice([0.0, 1.0, rng.uniform(-2, 2)]))
+    got = run(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
+    ref, mag = oracle_ref(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
+    assert norm_err(got, ref, mag) <= TOL
+
+
+def test_split_k_fp64_reduction():
+    # few output tiles and a long contracted range: the contracted range is
+    # split across CTAs and the FP32 partials are reduced in FP64
+    g = torch.Generator().manual_seed(4)
+    A = f32(torch.randn(256, 8192, generator=g, dtype=torch.float64))
+    B = f32(torch.randn(8192, 100, generator=g, dtype=torch.float64))
+    C0 = f32(torch.randn(256, 100, generator=g, dtype=torch.float64))
+    got = run(1.0, A, "ip", B, "pj", -1.0, C0, "ij")
+    ref, mag = oracle_ref(1.0, A, "ip", B, "pj", -1.0, C0, "ij")
+    assert norm_err(got, ref, mag) <= TOL
+
+
+def test_degenerate_shapes():
+    g = torch.Generator().manual_seed(5)
+    r = lambda *s: f32(torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1)
+    for args in ((1.0, r(50, 70), "ab", r(70, 50), "ba", 0.0, torch.zeros(()), ""),   # rank-0 C
+                 (1.0, r(33), "p", r(33, 70), "pj", 0.0, torch.zeros(70), "j"),       # m = 1
+                 (1.0, r(130), "i", r(70), "j", 0.0, torch.zeros(70, 130), "ji"),     # k = 1
+                 (1.0, r(1, 20, 3), "xap", r(3, 1, 9), "pyb", 0.0, torch.zeros(20, 1, 9, 1), "axby")):
+        got = run(*args)
+        ref, mag = oracle_ref(*args)
+        assert norm_err(got, ref, mag) <= TOL
+
+
+def test_beta_zero_nan_c_and_alpha_zero():
+    g = torch.Generator().manual_seed(6)
+    A = f32(torch.rand(64, 48, generator=g, dtype=torch.float64))
+    B = f32(torch.rand(48, 80, generator=g, dtype=torch.float64))
+    got = run(1.0, A, "ip", B, "pj", 0.0, torch.full((64, 80), float("nan"), dtype=torch.float64), "ij")
+    assert np.all(np.isfinite(got))
+    C0 = f32(torch.rand(64, 80, generator=g, dtype=torch.float64))
+    got = run(0.0, A, "ip", B, "pj", 2.0, C0, "ij")
+    assert np.array_equal(got, (2.0 * C0).numpy().astype(np.float32).astype(np.float64))
+
+
+def sampled_check(spec, seed, ranges=4, width=400):
+    h = W.make_inputs(spec, seed=seed)
+    dA, dB, dC = (to_device(h[x], torch.float32) for x in "ABC")
+    tc.contract(dA, spec.labA, dB, spec.labB, dC, spec.labC, alpha=spec.alpha, beta=spec.beta,
+                mode="bf16x3")
+    torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    got = dC.cpu().to(torch.float64).numpy().ravel(order="F")
+    a, b = h["A"].numpy(), h["B"].numpy()
+    n = got.size
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for start in list(rng.integers(0, n - width, ranges)) + [0, n - width]:
+        c = np.array(h["C"].numpy(), copy=True)
+        mag = oracle.contract_(spec.alpha, a, spec.labA, b, spec.labB, spec.beta, c, spec.labC,
+                               begin=int(start), end=int(start) + width)
+        sel = slice(int(start), int(start) + width)
+        worst = max(worst, norm_err(got[sel], c.ravel(order="F")[sel], mag.ravel(order="F")[sel]))
+    assert worst <= TOL, worst
+    return worst
+
+
+def test_spiky_f32_full_size_sampled():
+    sampled_check(W.SPECS["spiky_f32"], seed=1002)
+
+
+def test_grad_f32_forward_full_size_sampled():
+    sampled_check(W.SPECS["grad_f32"], seed=1003)
