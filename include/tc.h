@@ -65,7 +65,8 @@ enum {
   TC_ERR_CUDA = -6,           /* a CUDA runtime call failed */
   TC_ERR_DEVICE_TIMEOUT = -7, /* a kernel's bounded wait expired (device error word) */
   TC_ERR_UNSUPPORTED = -8,    /* combination not provided (e.g. BF16X3 on F64 data) */
-  TC_ERR_DEVICE_BOUNDS = -9   /* a kernel computed an offset outside an operand */
+  TC_ERR_DEVICE_BOUNDS = -9,  /* a kernel computed an offset outside an operand */
+  TC_ERR_SCRATCH_LIMIT = -10  /* tc_contract_noalloc: problem needs more than its fixed scratch */
 };
 
 /* One tensor operand: `rank` dimensions with lengths `len[d]` >= 0, strides
@@ -181,6 +182,33 @@ TC_API int tc_scatter_count(const tc_tensor* A, const tc_tensor* B, const tc_ten
  * one-element block has stride 1. */
 TC_API int tc_build_scatter(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,
                      int64_t* out, int64_t count, void* stream);
+
+/* ---- contraction without any device allocation ------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory at all -- code running while another part of
+ * the program captures a CUDA graph, real-time or embedded hosts whose device
+ * memory is divided up once at start-up, plug-ins whose host application owns
+ * every allocation.
+ *
+ * Same operation and argument rules as tc_contract in FP64 mode (F64 data, or
+ * F32 data widened to FP64), but it takes no workspace and allocates nothing:
+ * the scatter and block-scatter vectors live in one fixed array of
+ * TC_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  A problem whose vectors
+ * need more -- 2(m + n + k) + 2(ceil(m/4) + ceil(n/4) + ceil(k/4)) int64
+ * entries after the planner's folding, i.e. m + n + k up to about 104,000 --
+ * is rejected with TC_ERR_SCRATCH_LIMIT before anything is launched.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array: calls whose kernels overlap on the
+ * GPU (different streams, or different host threads, without ordering between
+ * them) race on it and must be serialised by the caller.  Nothing in the array
+ * needs to start at zero: each call writes every entry it reads. */
+#define TC_NOALLOC_SCRATCH_BYTES (2u << 20)
+TC_API int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor* A,
+                               const tc_tensor* B, double beta, const tc_tensor* C, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------------ */
 

@@ -13,7 +13,7 @@ TC_MODE_F64, TC_MODE_BF16X3 = 0, 1
 TC_OK = 0
 STATUS = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_LABEL", -3: "TC_ERR_EXTENT", -4: "TC_ERR_OVERLAP",
           -5: "TC_ERR_WORKSPACE", -6: "TC_ERR_CUDA", -7: "TC_ERR_DEVICE_TIMEOUT",
-          -8: "TC_ERR_UNSUPPORTED", -9: "TC_ERR_DEVICE_BOUNDS"}
+          -8: "TC_ERR_UNSUPPORTED", -9: "TC_ERR_DEVICE_BOUNDS", -10: "TC_ERR_SCRATCH_LIMIT"}
 
 
 class TcTensor(ctypes.Structure):
@@ -52,6 +52,8 @@ SIGNATURES = {
     "tc_scatter_count": (c_i32, [ctypes.POINTER(TcTensor)] * 3 + [c_i32, ctypes.POINTER(c_i64)]),
     "tc_build_scatter": (c_i32, [ctypes.POINTER(TcTensor)] * 3 + [c_i32, c_vp, c_i64, c_vp]),
     "tc_get_device_error": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
+    "tc_contract_noalloc": (c_i32, [c_i32, c_dbl, ctypes.POINTER(TcTensor), ctypes.POINTER(TcTensor), c_dbl,
+                                    ctypes.POINTER(TcTensor), c_vp]),
     "tc_set_mainloop_events": (c_i32, [c_vp, c_vp]),
     "tc_launch_count": (ctypes.c_uint64, []),
     "tc_status_string": (ctypes.c_char_p, [c_i32]),

@@ -204,6 +204,7 @@ const char* tc_status_string(int status) {
     case TC_ERR_DEVICE_TIMEOUT: return "device-side bounded wait expired";
     case TC_ERR_UNSUPPORTED: return "unsupported dtype/mode combination";
     case TC_ERR_DEVICE_BOUNDS: return "device-side offset outside an operand";
+    case TC_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of tc_contract_noalloc";
     default: return "unknown status";
   }
 }
