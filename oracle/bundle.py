@@ -18,6 +18,12 @@ Readings (the paper does not say): sorting uses |stride| and is stable in the
 order the labels appear in C (I, J) or A (P); folding merges a pair (x, y)
 whenever s_y(T) == s_x(T) * n_x in both tensors of the bundle, scanning pairs
 in label order and repeating until no pair merges.  The steps move no data.
+
+``normalize(..., gpu_p_order=True)`` adds one step that is not the paper's:
+6. when A's smallest stride lies outside P (A is then read along its rows and
+   the P order does not affect its access) but B's smallest stride lies in P,
+   re-sort P by increasing |stride| in B, so that B is read along its own unit
+   stride.  Step 5's aim -- stride-1 access for A -- is unaffected.
 """
 from dataclasses import dataclass, field
 from typing import Dict, List, Tuple
@@ -118,10 +124,10 @@ def _fold(dims: List[Dim]) -> List[Dim]:
     return dims
 
 
-def normalize(A, B, C) -> Bundles:
+def normalize(A, B, C, gpu_p_order: bool = False) -> Bundles:
     """A, B, C are (labels, lens, strides) triples.  Returns the bundles after
     the five steps of Section 7.3 (names 'A' and 'B' in Dim.s refer to the
-    tensors *after* any swap)."""
+    tensors *after* any swap), plus step 6 above when ``gpu_p_order``."""
     I, J, P = _dims(A, B, C)
     # 1. remove dimensions of length one
     I = [d for d in I if d.n != 1]
@@ -142,4 +148,14 @@ def normalize(A, B, C) -> Bundles:
         P = [Dim(d.labels, d.n, {"A": d.s["B"], "B": d.s["A"]}) for d in P]
     # 5. sort P by increasing stride in A
     P = sorted(P, key=lambda d: abs(d.s["A"]))
+    # 6. (not in the paper) let B's unit stride order P when A's lies outside P
+    if gpu_p_order and P:
+        minA_P = min(abs(d.s["A"]) for d in P)
+        minA_I = min((abs(d.s["A"]) for d in I), default=None)
+        minB_P = min(abs(d.s["B"]) for d in P)
+        minB_J = min((abs(d.s["B"]) for d in J), default=None)
+        a_rows = minA_I is not None and minA_I <= minA_P
+        b_k = minB_J is None or minB_P < minB_J
+        if a_rows and b_k:
+            P = sorted(P, key=lambda d: abs(d.s["B"]))
     return Bundles(I, J, P, swapped)

@@ -17,7 +17,7 @@ from ._lib import TcError  # noqa: F401
 __all__ = ["contract", "workspace_size", "plan_describe", "build_scatter", "device_error",
            "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
 
-_MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3}
+_MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3, "bf16x6": L.TC_MODE_BF16X6}
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -65,7 +65,8 @@ def contract(A, labA: str, B, labB: str, C, labC: str, alpha: float = 1.0, beta:
     ``labX`` gives one single-character label per dimension of X.  Labels shared
     by A and C form I, by B and C form J, by A and B form P (summed).  Any
     strides are accepted for A and B (C must not overlap itself).  ``mode`` is
-    "f64" (FP64 products and sums) or "bf16x3" (float32 data only).
+    "f64" (FP64 products and sums), "bf16x3" or "bf16x6" (float32 data only;
+    tensor-core products of two or three bf16 pieces per operand).
     """
     _check_operands(A, B, C)
     keep = []

@@ -9,7 +9,7 @@ c_i32, c_i64, c_dbl, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_doubl
 MAX_RANK = 16
 
 TC_F64, TC_F32 = 0, 1
-TC_MODE_F64, TC_MODE_BF16X3 = 0, 1
+TC_MODE_F64, TC_MODE_BF16X3, TC_MODE_BF16X6 = 0, 1, 2
 TC_OK = 0
 STATUS = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_LABEL", -3: "TC_ERR_EXTENT", -4: "TC_ERR_OVERLAP",
           -5: "TC_ERR_WORKSPACE", -6: "TC_ERR_CUDA", -7: "TC_ERR_DEVICE_TIMEOUT",

@@ -49,8 +49,8 @@ size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : 4; }
 
 int check_modes(tc_dtype dt, tc_mode mode) {
   if (dt != TC_F64 && dt != TC_F32) return TC_ERR_ARG;
-  if (mode != TC_MODE_F64 && mode != TC_MODE_BF16X3) return TC_ERR_ARG;
-  if (mode == TC_MODE_BF16X3 && dt != TC_F32) return TC_ERR_UNSUPPORTED;
+  if (mode != TC_MODE_F64 && mode != TC_MODE_BF16X3 && mode != TC_MODE_BF16X6) return TC_ERR_ARG;
+  if (mode != TC_MODE_F64 && dt != TC_F32) return TC_ERR_UNSUPPORTED;
   return TC_OK;
 }
 
@@ -64,9 +64,15 @@ int sm_count() {
   return n;
 }
 
-// Tile width and split of the contracted range for the BF16x3 mainloop:
-// enough CTAs to cover the SMs once when the output alone has too few tiles,
-// each split keeping at least 8 k-tiles of 32.
+// Tile width and split of the contracted range for the tensor-core mainloop.
+// Two constraints fix the split count S:
+//  * accuracy: the tensor core accumulates in FP32 with unspecified rounding,
+//    so each CTA's chain is capped at kChainTiles k-tiles of 32 (1024 terms);
+//    the FP32 partials of the S chains are then summed in FP64 (K4);
+//  * parallelism: when the output alone has fewer tiles than SMs, split
+//    further so the grid covers the SMs, keeping at least 8 k-tiles a split.
+constexpr int64_t kChainTiles = 32;
+
 struct Bf16Choice {
   int bn, splits;
   int64_t kps;
@@ -80,13 +86,14 @@ Bf16Choice choose_bf16(const Layout& L, int sms) {
     const int64_t w = (t + sms - 1) / sms;
     return (double)t / (double)(w * sms) * (bn == 256 ? 1.0 : 0.97);
   };
-  c.bn = 128;
-  (void)waves_eff;
+  c.bn = (L.n > 128 && waves_eff(256) >= waves_eff(128)) ? 256 : 128;
   const int64_t tiles = tm * ((L.n + c.bn - 1) / c.bn);
   const int64_t kt = (L.k + 31) / 32;
-  int64_t s = 1;
-  if (tiles < sms) s = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
-  s = std::max<int64_t>(1, std::min<int64_t>(s, 64));
+  const int64_t s_acc = (kt + kChainTiles - 1) / kChainTiles;
+  int64_t s_par = 1;
+  if (tiles < sms) s_par = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
+  int64_t s = std::max<int64_t>(1, std::max(s_acc, s_par));
+  s = std::min<int64_t>(s, std::max<int64_t>(kt, 1));
   const int64_t ktps = (kt + s - 1) / s;
   c.kps = ktps * 32;
   c.splits = (int)((L.k + c.kps - 1) / c.kps);
@@ -109,7 +116,7 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
   w.partial_off = w.scatter_bytes;
   w.partial_bytes = 0;
   w.bf = Bf16Choice{128, 1, 0};
-  if (mode == TC_MODE_BF16X3 && p.L.k > 0) {
+  if (mode != TC_MODE_F64 && p.L.k > 0) {
     w.bf = choose_bf16(p.L, sm_count());
     if (w.bf.splits > 1)
       w.partial_bytes = align_up((size_t)w.bf.splits * p.L.m * p.L.n * sizeof(float), 256);
@@ -140,8 +147,9 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   const ScatterPtrs sp = scatter_ptrs(scat, o);
   if (L.k == 0 || alpha == 0.0)
     return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
-  if (mode == TC_MODE_BF16X3) {
+  if (mode != TC_MODE_F64) {
     Bf16Launch q;
+    q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.a = p.a;
     q.b = p.b;
     q.c = p.c;

@@ -27,38 +27,50 @@ namespace {
 
 using namespace ptx;
 
-constexpr int BM = 128, BK = 32, STAGES = 4;
+constexpr int BM = 128, BK = 32;
 constexpr int NPROD = 256;
 constexpr int NT = NPROD + 32;
 constexpr int MMA_WARP = NPROD / 32;
 
-template <int BN>
+// Shared-memory plan for NS bf16 pieces per operand.  Per stage:
+// [A piece 0 .. NS-1][B piece 0 .. NS-1], each piece an R x BK K-major panel.
+template <int BN, int NS>
 struct Lay {
-  static constexpr int A_BYTES = BM * BK * 2;  // one bf16 copy (hi or lo) of the A panel
+  static constexpr int STAGES = NS == 2 ? 4 : 3;
+  static constexpr int A_BYTES = BM * BK * 2;  // one bf16 piece of the A panel
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int B_OFF = NS * A_BYTES;
+  static constexpr int STAGE = NS * A_BYTES + NS * B_BYTES;
   static constexpr int OPS = STAGES * STAGE;
   static constexpr int SCAT = OPS;  // int64: rA[BM] rC[BM] cB[BN] cC[BN]
   static constexpr int BARS = SCAT + (2 * BM + 2 * BN) * 8;
   static constexpr int MISC = BARS + (2 * STAGES + 1) * 8;  // tmem slot + abort flag
   static constexpr int END = MISC + 16;
-  // Slack so that every address a descriptor can reach stays inside the
-  // allocation even under the other reading of LBO/SBO, plus 1 KB alignment.
-  static constexpr int ALLOC = END + 32 * 1024 + 1024;
+  static constexpr int ALLOC = END + 1024;  // + alignment of the base to 1 KB
+  static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
 };
 
-__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
+// Split 8 FP32 values into NS bf16 pieces: piece 0 = RN_bf16(x), piece i =
+// RN_bf16(x - pieces 0..i-1) (each residual is exact in FP32), stored to the
+// NS panels at byte offset `off` (one 16-byte core-matrix row each).
+template <int NS>
+__device__ __forceinline__ void split8_store(float (&v)[8], uint8_t* piece0, int piece_bytes,
+                                             uint32_t off) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    __nv_bfloat162 bh = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    float2 fh = __bfloat1622float2(bh);
-    __nv_bfloat162 bl = __floats2bfloat162_rn(v[2 * j] - fh.x, v[2 * j + 1] - fh.y);
-    h[j] = *reinterpret_cast<uint32_t*>(&bh);
-    l[j] = *reinterpret_cast<uint32_t*>(&bl);
+  for (int sidx = 0; sidx < NS; ++sidx) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      if (sidx + 1 < NS) {
+        const float2 f = __bfloat1622float2(b);
+        v[2 * j] -= f.x;
+        v[2 * j + 1] -= f.y;
+      }
+      w[j] = *reinterpret_cast<uint32_t*>(&b);
+    }
+    *reinterpret_cast<uint4*>(piece0 + sidx * piece_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // byte offset of (row r, k-chunk q of 8 elements) in an R-row K-major panel
@@ -85,13 +97,13 @@ struct Args {
 // Gather one R x BK panel (rows through rowsc, k through ksc/kbs) of FP32,
 // split it into hi/lo BF16, store both in the canonical layout.
 // chunk c of this operand: k-contiguous -> (row, 8 k); else -> (4 rows, 8 k).
-template <int R>
+template <int R, int NS>
 __device__ __forceinline__ void panel_chunk(int c, const float* __restrict__ base,
                                             const int64_t* rowsc, int rows_valid,
                                             const int64_t* __restrict__ ksc,
                                             const int64_t* __restrict__ kbs, int64_t k0,
-                                            int64_t kend, bool kcontig, uint8_t* hi_s,
-                                            uint8_t* lo_s) {
+                                            int64_t kend, bool kcontig, uint8_t* piece0) {
+  constexpr int PB = R * BK * 2;
   if (kcontig) {
     const int r = c >> 2, q = c & 3;
     const int64_t kk = k0 + q * 8;
@@ -117,11 +129,7 @@ __device__ __forceinline__ void panel_chunk(int c, const float* __restrict__ bas
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = 0.f;
     }
-    uint4 h, l;
-    split8(v, h, l);
-    const uint32_t off = panel_off<R>(r, q);
-    *reinterpret_cast<uint4*>(hi_s + off) = h;
-    *reinterpret_cast<uint4*>(lo_s + off) = l;
+    split8_store<NS>(v, piece0, PB, panel_off<R>(r, q));
   } else {
     const int g = c % (R / 4), q = c / (R / 4);
     const int r0 = 4 * g;
@@ -152,13 +160,7 @@ __device__ __forceinline__ void panel_chunk(int c, const float* __restrict__ bas
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint4 h, l;
-      split8(v[i], h, l);
-      const uint32_t off = panel_off<R>(r0 + i, q);
-      *reinterpret_cast<uint4*>(hi_s + off) = h;
-      *reinterpret_cast<uint4*>(lo_s + off) = l;
-    }
+    for (int i = 0; i < 4; ++i) split8_store<NS>(v[i], piece0, PB, panel_off<R>(r0 + i, q));
   }
 }
 
@@ -167,9 +169,10 @@ __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err
   if (err) atomicCAS(err, 0, kDevTimeout);
 }
 
-template <int BN>
+template <int BN, int NS>
 __global__ void __launch_bounds__(NT, 1) k_bf16x3(const Args p) {
-  using Ly = Lay<BN>;
+  using Ly = Lay<BN, NS>;
+  constexpr int STAGES = Ly::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -234,11 +237,10 @@ __global__ void __launch_bounds__(NT, 1) k_bf16x3(const Args p) {
       const int64_t k0 = kbeg + kt * BK;
       for (int c = tid; c < chunks_a + chunks_b; c += NPROD) {
         if (c < chunks_a)
-          panel_chunk<BM>(c, p.a, sRA, rows_a, p.sp.cA, p.sp.cbsA, k0, kend, p.a_kc, st,
-                          st + Ly::A_BYTES);
+          panel_chunk<BM, NS>(c, p.a, sRA, rows_a, p.sp.cA, p.sp.cbsA, k0, kend, p.a_kc, st);
         else
-          panel_chunk<BN>(c - chunks_a, p.b, sCB, rows_b, p.sp.rB, p.sp.rbsB, k0, kend, p.b_kc,
-                          st + 2 * Ly::A_BYTES, st + 2 * Ly::A_BYTES + Ly::B_BYTES);
+          panel_chunk<BN, NS>(c - chunks_a, p.b, sCB, rows_b, p.sp.rB, p.sp.rbsB, k0, kend,
+                              p.b_kc, st + Ly::B_OFF);
       }
       fence_proxy_async_smem();
       mbar_arrive(&full[s]);
@@ -292,19 +294,23 @@ __global__ void __launch_bounds__(NT, 1) k_bf16x3(const Args p) {
       }
       tc_fence_after();
       const uint32_t st = base + s * Ly::STAGE;
-      const uint32_t a_hi = st, a_lo = st + Ly::A_BYTES;
-      const uint32_t b_hi = st + 2 * Ly::A_BYTES, b_lo = b_hi + Ly::B_BYTES;
 #pragma unroll
       for (int ksl = 0; ksl < BK / 16; ++ksl) {
         // k-slice ksl covers k-chunks 2*ksl, 2*ksl+1 (LBO apart); row groups SBO = 128 B apart
         const uint32_t ao = ksl * 2 * (BM / 8) * 128, bo = ksl * 2 * (BN / 8) * 128;
-        const uint64_t dAh = smem_desc(a_hi + ao, (BM / 8) * 128, 128);
-        const uint64_t dAl = smem_desc(a_lo + ao, (BM / 8) * 128, 128);
-        const uint64_t dBh = smem_desc(b_hi + bo, (BN / 8) * 128, 128);
-        const uint64_t dBl = smem_desc(b_lo + bo, (BN / 8) * 128, 128);
-        mma_bf16_ss(tmem, dAh, dBh, idesc, (kt > 0 || ksl > 0) ? 1u : 0u);
-        mma_bf16_ss(tmem, dAh, dBl, idesc, 1u);
-        mma_bf16_ss(tmem, dAl, dBh, idesc, 1u);
+        uint64_t dA[NS], dB[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          dA[i] = smem_desc(st + i * Ly::A_BYTES + ao, (BM / 8) * 128, 128);
+          dB[i] = smem_desc(st + Ly::B_OFF + i * Ly::B_BYTES + bo, (BN / 8) * 128, 128);
+        }
+        // every product of pieces i, j with i + j < NS: the terms of relative
+        // size above 2^-8NS (three for NS = 2, six for NS = 3)
+        mma_bf16_ss(tmem, dA[0], dB[0], idesc, (kt > 0 || ksl > 0) ? 1u : 0u);
+#pragma unroll
+        for (int tsum = 1; tsum < NS; ++tsum)
+#pragma unroll
+          for (int i = 0; i <= tsum; ++i) mma_bf16_ss(tmem, dA[i], dB[tsum - i], idesc, 1u);
       }
       mma_commit(&empty[s]);
     }
@@ -339,14 +345,15 @@ __global__ void k_splitk_reduce(const float* __restrict__ partial, float* __rest
   }
 }
 
-template <int BN>
+template <int BN, int NS>
 cudaError_t launch_bn(const Bf16Launch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_bf16x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Lay<BN>::ALLOC);
+    cudaError_t e = cudaFuncSetAttribute(k_bf16x3<BN, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Lay<BN, NS>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -372,7 +379,7 @@ cudaError_t launch_bn(const Bf16Launch& q, cudaStream_t s) {
   if (tiles > 0x7fffffffLL || q.splits > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)tiles, (unsigned)q.splits);
   mainloop_event_before(s);
-  k_bf16x3<BN><<<grid, NT, Lay<BN>::ALLOC, s>>>(a);
+  k_bf16x3<BN, NS><<<grid, NT, Lay<BN, NS>::ALLOC, s>>>(a);
   note_launch();
   if (q.splits > 1) {
     int64_t blocks = (q.m * q.n + 255) / 256;
@@ -387,10 +394,9 @@ cudaError_t launch_bn(const Bf16Launch& q, cudaStream_t s) {
 
 }  // namespace
 
-int bf16x3_tile_n(int64_t n) { return n >= 256 ? 256 : 128; }
-
 cudaError_t launch_bf16x3(const Bf16Launch& q, cudaStream_t s) {
-  return q.bn == 256 ? launch_bn<256>(q, s) : launch_bn<128>(q, s);
+  if (q.pieces == 3) return q.bn == 256 ? launch_bn<256, 3>(q, s) : launch_bn<128, 3>(q, s);
+  return q.bn == 256 ? launch_bn<256, 2>(q, s) : launch_bn<128, 2>(q, s);
 }
 
 }  // namespace tc

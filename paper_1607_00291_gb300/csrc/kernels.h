@@ -52,6 +52,7 @@ struct Bf16Launch {
   double alpha, beta;
   int a_k_contig, b_k_contig;
   int bn;          // 128 or 256
+  int pieces;      // bf16 pieces per operand: 2 (BF16x3) or 3 (BF16x6)
   int splits;      // CTAs along the contracted range
   int64_t k_per_split;  // multiple of 32
   int32_t* err;

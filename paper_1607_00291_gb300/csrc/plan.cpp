@@ -11,6 +11,10 @@
 //      i.e. compute C^T = B^T A^T so that C's unit stride runs along M;
 //   5. sort P by increasing |stride| in A (stable in the original A's order).
 // No data moves; the result only fixes the iteration order of the kernels.
+// One GPU-specific step follows the paper's five:
+//   6. if A's smallest |stride| lies outside P (A is read along its rows, so
+//      the P order does not affect it) and B's smallest |stride| lies in P,
+//      re-sort P by |stride| in B, so that B's k-runs are contiguous.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -194,6 +198,19 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
   }
   // step 5: sort P by |stride| in A
   stable_sort(P, nP, [](const LDim& x) { return std::llabs(x.s0); });
+  // step 6 (GPU): B's unit stride orders P when A's lies outside P
+  if (nP > 0) {
+    int64_t minAP = INT64_MAX, minAI = INT64_MAX, minBP = INT64_MAX, minBJ = INT64_MAX;
+    for (int i = 0; i < nP; ++i) {
+      minAP = std::min<int64_t>(minAP, std::llabs(P[i].s0));
+      minBP = std::min<int64_t>(minBP, std::llabs(P[i].s1));
+    }
+    for (int i = 0; i < nI; ++i) minAI = std::min<int64_t>(minAI, std::llabs(I[i].s0));
+    for (int i = 0; i < nJ; ++i) minBJ = std::min<int64_t>(minBJ, std::llabs(J[i].s0));
+    const bool a_rows = nI > 0 && minAI <= minAP;
+    const bool b_k = nJ == 0 || minBP < minBJ;
+    if (a_rows && b_k) stable_sort(P, nP, [](const LDim& x) { return std::llabs(x.s1); });
+  }
 
   Layout& L = out->L;
   tc_plan_info& info = out->info;

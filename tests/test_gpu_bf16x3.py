@@ -1,7 +1,15 @@
-"""Parity of the BF16x3 tensor-core path (K3, K4 split-K FP64 reduction, K5)
-with the FP64 CPU oracle.  Bound: max |C_gpu - C_oracle| / (|alpha| sum|A||B|
-+ |beta||C|) <= 1e-5, and exact results where every product and partial sum
-is exactly representable (integer data below 2^8 in magnitude)."""
+"""Parity of the tensor-core path (K3, K4 split-K FP64 reduction, K5) with the
+FP64 CPU oracle, per element, normalised by |alpha| sum|A||B| + |beta||C|.
+
+Bounds, from the arithmetic:
+* bf16x3: two bf16 pieces keep 16 significand bits, so |x - (hi + lo)| <=
+  2^-16 |x|; with the dropped lo*lo term a product is off by at most
+  3 * 2^-16 |a||b|.  Allowance for FP32 accumulation and the final FP32
+  rounding: 8 * 2^-24.
+* bf16x6: three pieces represent a normal FP32 value exactly; the dropped
+  terms b1*b2, b2*b1, b2*b2 are below 2^-23 |a||b|; the bound used is the
+  stated 1e-5.
+Integer data below 2^8 in magnitude is exact in both modes."""
 import numpy as np
 import pytest
 import torch
@@ -13,12 +21,13 @@ from paper_1607_00291_gb300 import workloads as W
 from helpers import norm_err, oracle_ref, to_device
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-5
+TOLS = {"bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24, "bf16x6": 1e-5}
+MODES = sorted(TOLS)
 
 
-def run(alpha, A, lA, B, lB, beta, C0, lC):
+def run(alpha, A, lA, B, lB, beta, C0, lC, mode="bf16x6"):
     dA, dB, dC = (to_device(x, torch.float32) for x in (A, B, C0))
-    tc.contract(dA, lA, dB, lB, dC, lC, alpha=alpha, beta=beta, mode="bf16x3")
+    tc.contract(dA, lA, dB, lB, dC, lC, alpha=alpha, beta=beta, mode=mode)
     torch.cuda.synchronize()
     assert tc.device_error() == 0
     return dC.cpu().to(torch.float64).numpy()
@@ -28,27 +37,31 @@ def f32(t):
     return t.to(torch.float32).to(torch.float64)
 
 
-def test_single_tile_integers_exact():
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [128, 256])
+def test_single_tile_integers_exact(mode, n):
     g = torch.Generator().manual_seed(1)
     A = f32(torch.randint(-8, 9, (128, 32), generator=g).double())
-    B = f32(torch.randint(-8, 9, (32, 128), generator=g).double())
-    C0 = torch.zeros(128, 128, dtype=torch.float64)
-    got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+    B = f32(torch.randint(-8, 9, (32, n), generator=g).double())
+    C0 = torch.zeros(128, n, dtype=torch.float64)
+    got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij", mode)
     ref, _ = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
     assert np.array_equal(got, ref)
 
 
-def test_matrix_case_uniform():
+@pytest.mark.parametrize("mode", MODES)
+def test_matrix_case_uniform(mode):
     g = torch.Generator().manual_seed(2)
     A = f32(torch.rand(300, 500, generator=g, dtype=torch.float64) * 2 - 1)
-    B = f32(torch.rand(500, 200, generator=g, dtype=torch.float64) * 2 - 1)
-    C0 = f32(torch.rand(300, 200, generator=g, dtype=torch.float64) * 2 - 1)
-    got = run(0.5, A, "ip", B, "pj", 1.5, C0, "ij")
+    B = f32(torch.rand(500, 700, generator=g, dtype=torch.float64) * 2 - 1)
+    C0 = f32(torch.rand(300, 700, generator=g, dtype=torch.float64) * 2 - 1)
+    got = run(0.5, A, "ip", B, "pj", 1.5, C0, "ij", mode)
     ref, mag = oracle_ref(0.5, A, "ip", B, "pj", 1.5, C0, "ij")
-    assert norm_err(got, ref, mag) <= TOL
+    assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
-def test_transposed_operand_layouts():
+@pytest.mark.parametrize("mode", MODES)
+def test_transposed_operand_layouts(mode):
     # row-contiguous and k-contiguous gathers for both operands
     g = torch.Generator().manual_seed(3)
     for ta in (False, True):
@@ -58,63 +71,67 @@ def test_transposed_operand_layouts():
             A = f32(A.t().contiguous().t() if ta else A)
             B = f32(B.t().contiguous().t() if tb else B)
             C0 = torch.zeros(200, 260, dtype=torch.float64)
-            got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+            got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij", mode)
             ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
-            assert norm_err(got, ref, mag) <= TOL, (ta, tb)
+            assert norm_err(got, ref, mag) <= TOLS[mode], (ta, tb)
 
 
-@pytest.mark.parametrize("seed", range(12))
-def test_random_contractions(seed):
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("seed", range(10))
+def test_random_contractions(seed, mode):
     rng = np.random.default_rng(300 + seed)
     p = W.random_problem(rng, ext=(1, 29), max_elems=1 << 19, max_flops=2.0 ** 29)
     h = W.make_random_inputs(p, seed=seed, dtype=torch.float32)
     alpha = float(rng.uniform(-2, 2))
     beta = float(rng.choice([0.0, 1.0, rng.uniform(-2, 2)]))
-    got = run(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
+    got = run(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC, mode)
     ref, mag = oracle_ref(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
-    assert norm_err(got, ref, mag) <= TOL
+    assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
-def test_split_k_fp64_reduction():
+@pytest.mark.parametrize("mode", MODES)
+def test_split_k_fp64_reduction(mode):
     # few output tiles and a long contracted range: the contracted range is
     # split across CTAs and the FP32 partials are reduced in FP64
     g = torch.Generator().manual_seed(4)
     A = f32(torch.randn(256, 8192, generator=g, dtype=torch.float64))
     B = f32(torch.randn(8192, 100, generator=g, dtype=torch.float64))
     C0 = f32(torch.randn(256, 100, generator=g, dtype=torch.float64))
-    got = run(1.0, A, "ip", B, "pj", -1.0, C0, "ij")
+    got = run(1.0, A, "ip", B, "pj", -1.0, C0, "ij", mode)
     ref, mag = oracle_ref(1.0, A, "ip", B, "pj", -1.0, C0, "ij")
-    assert norm_err(got, ref, mag) <= TOL
+    assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
-def test_degenerate_shapes():
+@pytest.mark.parametrize("mode", MODES)
+def test_degenerate_shapes(mode):
     g = torch.Generator().manual_seed(5)
     r = lambda *s: f32(torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1)
     for args in ((1.0, r(50, 70), "ab", r(70, 50), "ba", 0.0, torch.zeros(()), ""),   # rank-0 C
                  (1.0, r(33), "p", r(33, 70), "pj", 0.0, torch.zeros(70), "j"),       # m = 1
                  (1.0, r(130), "i", r(70), "j", 0.0, torch.zeros(70, 130), "ji"),     # k = 1
                  (1.0, r(1, 20, 3), "xap", r(3, 1, 9), "pyb", 0.0, torch.zeros(20, 1, 9, 1), "axby")):
-        got = run(*args)
+        got = run(*args, mode=mode)
         ref, mag = oracle_ref(*args)
-        assert norm_err(got, ref, mag) <= TOL
+        assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
-def test_beta_zero_nan_c_and_alpha_zero():
+@pytest.mark.parametrize("mode", MODES)
+def test_beta_zero_nan_c_and_alpha_zero(mode):
     g = torch.Generator().manual_seed(6)
     A = f32(torch.rand(64, 48, generator=g, dtype=torch.float64))
     B = f32(torch.rand(48, 80, generator=g, dtype=torch.float64))
-    got = run(1.0, A, "ip", B, "pj", 0.0, torch.full((64, 80), float("nan"), dtype=torch.float64), "ij")
+    got = run(1.0, A, "ip", B, "pj", 0.0, torch.full((64, 80), float("nan"), dtype=torch.float64), "ij", mode)
     assert np.all(np.isfinite(got))
     C0 = f32(torch.rand(64, 80, generator=g, dtype=torch.float64))
-    got = run(0.0, A, "ip", B, "pj", 2.0, C0, "ij")
+    got = run(0.0, A, "ip", B, "pj", 2.0, C0, "ij", mode)
     assert np.array_equal(got, (2.0 * C0).numpy().astype(np.float32).astype(np.float64))
 
 
-def sampled_check(spec, seed, ranges=4, width=400):
+def sampled_check(spec, seed, mode, ranges=4, width=400):
     h = W.make_inputs(spec, seed=seed)
     dA, dB, dC = (to_device(h[x], torch.float32) for x in "ABC")
     tc.contract(dA, spec.labA, dB, spec.labB, dC, spec.labC, alpha=spec.alpha, beta=spec.beta,
-                mode="bf16x3")
+                mode=mode)
     torch.cuda.synchronize()
     assert tc.device_error() == 0
     got = dC.cpu().to(torch.float64).numpy().ravel(order="F")
@@ -128,13 +145,15 @@ def sampled_check(spec, seed, ranges=4, width=400):
                                begin=int(start), end=int(start) + width)
         sel = slice(int(start), int(start) + width)
         worst = max(worst, norm_err(got[sel], c.ravel(order="F")[sel], mag.ravel(order="F")[sel]))
-    assert worst <= TOL, worst
+    assert worst <= TOLS[mode], worst
     return worst
 
 
-def test_spiky_f32_full_size_sampled():
-    sampled_check(W.SPECS["spiky_f32"], seed=1002)
+@pytest.mark.parametrize("mode", MODES)
+def test_spiky_f32_full_size_sampled(mode):
+    sampled_check(W.SPECS["spiky_f32"], seed=1002, mode=mode)
 
 
-def test_grad_f32_forward_full_size_sampled():
-    sampled_check(W.SPECS["grad_f32"], seed=1003)
+@pytest.mark.parametrize("mode", MODES)
+def test_grad_f32_forward_full_size_sampled(mode):
+    sampled_check(W.SPECS["grad_f32"], seed=1003, mode=mode)

@@ -19,7 +19,7 @@ def cm(lab, ext):
 
 def compare(labA, sA, labB, sB, labC, sC):
     got = tc.plan_describe(sA, labA, sB, labB, sC, labC)
-    ref = ob.normalize((labA, *sA), (labB, *sB), (labC, *sC))
+    ref = ob.normalize((labA, *sA), (labB, *sB), (labC, *sC), gpu_p_order=True)
     assert got["swapped"] == ref.swapped
     assert (got["m"], got["n"], got["k"]) == (ref.m, ref.n, ref.k)
     for name, rb, key in (("I", ref.I, ("A", "C")), ("J", ref.J, ("B", "C")), ("P", ref.P, ("A", "B"))):
@@ -91,6 +91,17 @@ def test_error_codes():
     t = L.make_tensor((2,), (1,), "a", 0, keep)
     t.rank = 17
     assert L.lib().tc_plan_describe(t, t, t, L.TcPlanInfo()) == -1
+
+
+def test_gpu_p_order_step():
+    # grad_f32: A_ilmj is read along i (rows); B_mkl has unit stride on m in P,
+    # so P is ordered (m, l) by B's strides rather than (l, m) by A's
+    s = W.SPECS["grad_f32"]
+    g = tc.plan_describe(cm(s.labA, s.ext), s.labA, cm(s.labB, s.ext), s.labB, cm(s.labC, s.ext), s.labC)
+    assert [d["labels"] for d in g["P"]] == ["m", "l"]
+    paper = ob.normalize((s.labA, *cm(s.labA, s.ext)), (s.labB, *cm(s.labB, s.ext)),
+                         (s.labC, *cm(s.labC, s.ext)))
+    assert ["".join(d.labels) for d in paper.P] == ["l", "m"]  # the paper's step 5 alone
 
 
 def test_workspace_is_vector_sized_not_operand_sized():
