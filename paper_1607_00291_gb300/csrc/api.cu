@@ -121,6 +121,11 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
     if (w.bf.splits > 1)
       w.partial_bytes = align_up((size_t)w.bf.splits * p.L.m * p.L.n * sizeof(float), 256);
   }
+  if (mode == TC_MODE_F64 && p.L.k > 0) {
+    const int sms = sm_count();
+    if (f64_grid(p.L.m, p.L.n, p.L.k, sms, true) != f64_grid(p.L.m, p.L.n, p.L.k, 0, false))
+      w.partial_bytes = align_up(f64_partial_bytes(sms), 256);
+  }
   w.total = w.scatter_bytes + w.partial_bytes;
   return w;
 }
@@ -181,6 +186,9 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   f.beta = beta;
   f.a_k_contig = p.info.a_k_contig;
   f.b_k_contig = p.info.b_k_contig;
+  f.partial = w.partial_bytes ? reinterpret_cast<double*>(static_cast<char*>(ws) + w.partial_off)
+                              : nullptr;
+  f.max_ctas = sm_count();
   f.err = err_word();
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

@@ -12,8 +12,8 @@
 // rscat(C) + cscat(C) or, when the contracted range is split across CTAs,
 // stores FP32 partials that K4 reduces in FP64.
 //
-// Roles (288 threads): warps 0-7 load/convert (producers) and later run the
-// epilogue; warp 8 owns the Tensor Memory allocation and its lane 0 issues the
+// Roles (288 threads): warps 0-7 load (one k-tile ahead, in registers),
+// convert and stage (producers), and later run the epilogue; warp 8 owns the Tensor Memory allocation and its lane 0 issues the
 // MMAs.  Stages are handed over through mbarriers: `full` (producers -> MMA)
 // and `empty` (tcgen05.commit -> producers).  Every wait is bounded; on expiry
 // the CTA records TC_ERR_DEVICE_TIMEOUT in the device error word and unwinds.
@@ -94,73 +94,122 @@ struct Args {
   int32_t* err;
 };
 
-// Gather one R x BK panel (rows through rowsc, k through ksc/kbs) of FP32,
-// split it into hi/lo BF16, store both in the canonical layout.
-// chunk c of this operand: k-contiguous -> (row, 8 k); else -> (4 rows, 8 k).
-template <int R, int NS>
-__device__ __forceinline__ void panel_chunk(int c, const float* __restrict__ base,
-                                            const int64_t* rowsc, int rows_valid,
-                                            const int64_t* __restrict__ ksc,
-                                            const int64_t* __restrict__ kbs, int64_t k0,
-                                            int64_t kend, bool kcontig, uint8_t* piece0) {
-  constexpr int PB = R * BK * 2;
+// Register-staged gather of one R x BK FP32 panel.  Each producer thread owns
+// a fixed set of chunks, so a panel can be loaded into registers one k-tile
+// ahead of its conversion:
+//  * k-contiguous operand: chunks of (1 row, 8 consecutive k), two 16-byte
+//    loads where the block-scatter entry says the 4-run has unit stride and
+//    the address is 16-byte aligned, scalar loads through the scatter vectors
+//    otherwise;
+//  * row-contiguous operand: chunks of (2 consecutive rows, 8 k), one 8-byte
+//    load per k where the two rows are adjacent, scalar loads otherwise.
+// Consecutive threads take consecutive chunks along the unit-stride index, so
+// a warp's loads are coalesced.
+template <int R>
+struct PanelRegs {
+  static constexpr int E = R * BK / NPROD;  // floats per thread (16 or 32)
+  float v[E];
+};
+
+template <int R>
+__device__ __forceinline__ void panel_load(PanelRegs<R>& pr, int tid,
+                                           const float* __restrict__ base, const int64_t* rowsc,
+                                           int rows_valid, const int64_t* __restrict__ ksc,
+                                           const int64_t* __restrict__ kbs, int64_t k0,
+                                           int64_t kend, bool kcontig) {
+  constexpr int E = PanelRegs<R>::E;
   if (kcontig) {
-    const int r = c >> 2, q = c & 3;
-    const int64_t kk = k0 + q * 8;
-    float v[8];
-    if (r < rows_valid) {
-      const float* rowp = base + rowsc[r];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t kq = kk + 4 * h;
-        const float* p = kq < kend ? rowp + ksc[kq] : rowp;
-        if (kq + 3 < kend && kbs[kq >> 2] == 1 && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-          const float4 f = __ldg(reinterpret_cast<const float4*>(p));
-          v[4 * h] = f.x;
-          v[4 * h + 1] = f.y;
-          v[4 * h + 2] = f.z;
-          v[4 * h + 3] = f.w;
-        } else {
+    for (int i = 0; i < E / 8; ++i) {
+      const int c = tid + i * NPROD;
+      const int r = c >> 2, q = c & 3;
+      const int64_t kk = k0 + q * 8;
+      float* v = pr.v + 8 * i;
+      if (r < rows_valid) {
+        const float* rowp = base + rowsc[r];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) v[4 * h + j] = (kq + j < kend) ? __ldg(rowp + ksc[kq + j]) : 0.f;
-        }
-      }
-    } else {
+        for (int h = 0; h < 2; ++h) {
+          const int64_t kq = kk + 4 * h;
+          const float* p = kq < kend ? rowp + ksc[kq] : rowp;
+          if (kq + 3 < kend && kbs[kq >> 2] == 1 &&
+              ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+            v[4 * h] = f.x;
+            v[4 * h + 1] = f.y;
+            v[4 * h + 2] = f.z;
+            v[4 * h + 3] = f.w;
+          } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = 0.f;
-    }
-    split8_store<NS>(v, piece0, PB, panel_off<R>(r, q));
-  } else {
-    const int g = c % (R / 4), q = c / (R / 4);
-    const int r0 = 4 * g;
-    const int64_t kk = k0 + q * 8;
-    float v[4][8];
-    const bool rows_ok = r0 + 3 < rows_valid && rowsc[r0 + 1] == rowsc[r0] + 1 &&
-                         rowsc[r0 + 2] == rowsc[r0] + 2 && rowsc[r0 + 3] == rowsc[r0] + 3;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t k = kk + j;
-      if (k < kend) {
-        const int64_t ko = ksc[k];
-        const float* p = base + rowsc[r0] + ko;
-        if (rows_ok && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-          const float4 f = __ldg(reinterpret_cast<const float4*>(p));
-          v[0][j] = f.x;
-          v[1][j] = f.y;
-          v[2][j] = f.z;
-          v[3][j] = f.w;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            v[i][j] = (r0 + i < rows_valid) ? __ldg(base + rowsc[r0 + i] + ko) : 0.f;
+            for (int j = 0; j < 4; ++j)
+              v[4 * h + j] = (kq + j < kend) ? __ldg(rowp + ksc[kq + j]) : 0.f;
+          }
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i][j] = 0.f;
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
       }
     }
+  } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) split8_store<NS>(v[i], piece0, PB, panel_off<R>(r0 + i, q));
+    for (int i = 0; i < E / 16; ++i) {
+      const int c = tid + i * NPROD;
+      const int g = c % (R / 2), q = c / (R / 2);
+      const int r0 = 2 * g;
+      const int64_t kk = k0 + q * 8;
+      float* v = pr.v + 16 * i;
+      const bool r0v = r0 < rows_valid, r1v = r0 + 1 < rows_valid;
+      const int64_t o0 = rowsc[r0], o1 = rowsc[r0 + 1];
+      const bool pair = r1v && o1 == o0 + 1;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t k = kk + j;
+        if (k < kend) {
+          const int64_t ko = ksc[k];
+          const float* p = base + o0 + ko;
+          if (pair && ((reinterpret_cast<uintptr_t>(p) & 7) == 0)) {
+            const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+            v[j] = f.x;
+            v[8 + j] = f.y;
+          } else {
+            v[j] = r0v ? __ldg(p) : 0.f;
+            v[8 + j] = r1v ? __ldg(base + o1 + ko) : 0.f;
+          }
+        } else {
+          v[j] = 0.f;
+          v[8 + j] = 0.f;
+        }
+      }
+    }
+  }
+}
+
+template <int R, int NS>
+__device__ __forceinline__ void panel_store(const PanelRegs<R>& pr, int tid, bool kcontig,
+                                            uint8_t* piece0) {
+  constexpr int E = PanelRegs<R>::E;
+  constexpr int PB = R * BK * 2;
+  if (kcontig) {
+#pragma unroll
+    for (int i = 0; i < E / 8; ++i) {
+      const int c = tid + i * NPROD;
+      float w[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = pr.v[8 * i + j];
+      split8_store<NS>(w, piece0, PB, panel_off<R>(c >> 2, c & 3));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E / 16; ++i) {
+      const int c = tid + i * NPROD;
+      const int g = c % (R / 2), q = c / (R / 2);
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        float w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = pr.v[16 * i + 8 * rr + j];
+        split8_store<NS>(w, piece0, PB, panel_off<R>(2 * g + rr, q));
+      }
+    }
   }
 }
 
@@ -223,27 +272,35 @@ __global__ void __launch_bounds__(NT, 1) k_bf16x3(const Args p) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp < MMA_WARP) {
-    // ---- producers: gather, split, stage ----
-    const int chunks_a = p.a_kc ? BM * 4 : BM;
-    const int chunks_b = p.b_kc ? BN * 4 : BN;
-    for (int64_t kt = 0; kt < KT; ++kt) {
+    // ---- producers: gather one k-tile ahead, split, stage ----
+    PanelRegs<BM> ra0, ra1;
+    PanelRegs<BN> rb0, rb1;
+    auto load = [&](int64_t kt, PanelRegs<BM>& ra, PanelRegs<BN>& rb) {
+      const int64_t k0 = kbeg + kt * BK;
+      panel_load<BM>(ra, tid, p.a, sRA, rows_a, p.sp.cA, p.sp.cbsA, k0, kend, p.a_kc);
+      panel_load<BN>(rb, tid, p.b, sCB, rows_b, p.sp.rB, p.sp.rbsB, k0, kend, p.b_kc);
+    };
+    auto stage = [&](int64_t kt, const PanelRegs<BM>& ra, const PanelRegs<BN>& rb) -> bool {
       const int s = (int)(kt % STAGES);
       const uint32_t ph = (uint32_t)((kt / STAGES) & 1);
       if (!mbar_wait(&empty[s], ph ^ 1, abort)) {
         record_timeout(abort, p.err);
-        break;
+        return false;
       }
       uint8_t* st = smem + s * Ly::STAGE;
-      const int64_t k0 = kbeg + kt * BK;
-      for (int c = tid; c < chunks_a + chunks_b; c += NPROD) {
-        if (c < chunks_a)
-          panel_chunk<BM, NS>(c, p.a, sRA, rows_a, p.sp.cA, p.sp.cbsA, k0, kend, p.a_kc, st);
-        else
-          panel_chunk<BN, NS>(c - chunks_a, p.b, sCB, rows_b, p.sp.rB, p.sp.rbsB, k0, kend,
-                              p.b_kc, st + Ly::B_OFF);
-      }
+      panel_store<BM, NS>(ra, tid, p.a_kc, st);
+      panel_store<BN, NS>(rb, tid, p.b_kc, st + Ly::B_OFF);
       fence_proxy_async_smem();
       mbar_arrive(&full[s]);
+      return true;
+    };
+    if (KT > 0) load(0, ra0, rb0);
+    for (int64_t kt = 0; kt < KT; kt += 2) {
+      if (kt + 1 < KT) load(kt + 1, ra1, rb1);
+      if (!stage(kt, ra0, rb0)) break;
+      if (kt + 1 >= KT) break;
+      if (kt + 2 < KT) load(kt + 2, ra0, rb0);
+      if (!stage(kt + 1, ra1, rb1)) break;
     }
     // ---- epilogue ----
     bool have_acc = KT > 0;

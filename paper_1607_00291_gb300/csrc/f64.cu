@@ -10,9 +10,15 @@
 // and updates C through rscat(C) + cscat(C) (Section 6.1's scattered
 // micro-tile update), reading C only when beta != 0.
 //
+// Scheduling: plain tiling when the tiles fill whole waves of CTAs, else a
+// stream-K split of the (tile, k-tile) iteration space over one CTA per SM
+// with a deterministic FP64 fix-up of the cut tiles.
+//
 // GB300 has no tcgen05 kind for FP64, and its FP64 rate (DMMA ~= DFMA) is low
 // enough that a register-blocked warp-level DMMA tile keeps the pipe saturated;
 // global traffic is far below HBM bandwidth at every tile size used here.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace tc {
@@ -31,11 +37,28 @@ __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
                : "d"(a), "d"(b));
 }
 
+// Work split (stream-K): the T = tiles * KT (tile, k-tile) iterations are cut
+// into G equal contiguous ranges, one per CTA.  CTA c walks its range tile by
+// tile; a tile it covers whole is finished in place (fused epilogue), a tile
+// cut by a range boundary leaves FP64 partial sums in one of the CTA's two
+// slots (slot 0: the segment at the start of its range, slot 1: the segment at
+// its end), and k_f64_fixup adds them up in k order and applies the epilogue.
+// With G = tiles every range is exactly one tile (plain data-parallel tiling).
+struct SkArgs {
+  int64_t tiles, tiles_n, KT;
+  int64_t G;
+  double* partial;  // [G][2][BM*BN], element (mm, nn) at nn*BM + mm
+};
+
+__host__ __device__ __forceinline__ int64_t sk_start(int64_t c, int64_t T, int64_t G) {
+  return (int64_t)(((__int128)c * T) / G);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT, 1)
     k_f64(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ c, const ScatterPtrs sp,
           const int64_t M, const int64_t N, const int64_t K, const double alpha, const double beta,
-          const int a_kc, const int b_kc, const int64_t tiles_n) {
+          const int a_kc, const int b_kc, const SkArgs sk) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* As = reinterpret_cast<double*>(smem);  // [2][BK][LDA]
   double* Bs = As + 2 * BK * LDA;                // [2][BK][LDB]
@@ -47,29 +70,8 @@ __global__ void __launch_bounds__(NT, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tig = lane & 3;
   const int wm = warp >> 1, wn = warp & 1;
-  const int64_t tile = blockIdx.x;
-  const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-
-  for (int i = tid; i < BM; i += NT) {
-    const int64_t gm = m0 + i;
-    sRA[i] = gm < M ? sp.rA[gm] : 0;
-    sRC[i] = gm < M ? sp.rC[gm] : 0;
-  }
-  for (int i = tid; i < BN; i += NT) {
-    const int64_t gn = n0 + i;
-    sCB[i] = gn < N ? sp.cB[gn] : 0;
-    sCC[i] = gn < N ? sp.cC[gn] : 0;
-  }
-  __syncthreads();
-
-  double acc[4][4][2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-
-  double ra[A_PER_T], rb[B_PER_T];
-  const int64_t KT = (K + BK - 1) / BK;
+  const int64_t Tt = sk.tiles * sk.KT;
+  const int64_t start = sk_start(blockIdx.x, Tt, sk.G), end = sk_start(blockIdx.x + 1, Tt, sk.G);
 
   // element e of a panel -> (row, k) with consecutive threads along the
   // operand's unit-stride index
@@ -79,79 +81,152 @@ __global__ void __launch_bounds__(NT, 1)
   auto b_coord = [&](int e, int& nn, int& kk) {
     if (b_kc) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
   };
-  auto load = [&](int64_t kt) {
-    const int64_t k0 = kt * BK;
-#pragma unroll
-    for (int i = 0; i < A_PER_T; ++i) {
-      int mm, kk;
-      a_coord(tid + i * NT, mm, kk);
-      const int64_t gm = m0 + mm, gk = k0 + kk;
-      ra[i] = (gm < M && gk < K) ? (double)a[sRA[mm] + sp.cA[gk]] : 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < B_PER_T; ++i) {
-      int nn, kk;
-      b_coord(tid + i * NT, nn, kk);
-      const int64_t gn = n0 + nn, gk = k0 + kk;
-      rb[i] = (gn < N && gk < K) ? (double)b[sp.rB[gk] + sCB[nn]] : 0.0;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int i = 0; i < A_PER_T; ++i) {
-      int mm, kk;
-      a_coord(tid + i * NT, mm, kk);
-      As[(buf * BK + kk) * LDA + mm] = ra[i];
-    }
-#pragma unroll
-    for (int i = 0; i < B_PER_T; ++i) {
-      int nn, kk;
-      b_coord(tid + i * NT, nn, kk);
-      Bs[(buf * BK + kk) * LDB + nn] = rb[i];
-    }
-  };
 
-  if (KT > 0) {
-    load(0);
+  for (int64_t it = start; it < end;) {
+    const int64_t tile = it / sk.KT;
+    const int64_t kb = it - tile * sk.KT;
+    const int64_t ke = (end - tile * sk.KT) < sk.KT ? (end - tile * sk.KT) : sk.KT;
+    const int64_t m0 = (tile / sk.tiles_n) * BM, n0 = (tile % sk.tiles_n) * BN;
+
+    __syncthreads();  // the previous tile's epilogue is done with sRC/sCC
+    for (int i = tid; i < BM; i += NT) {
+      const int64_t gm = m0 + i;
+      sRA[i] = gm < M ? sp.rA[gm] : 0;
+      sRC[i] = gm < M ? sp.rC[gm] : 0;
+    }
+    for (int i = tid; i < BN; i += NT) {
+      const int64_t gn = n0 + i;
+      sCB[i] = gn < N ? sp.cB[gn] : 0;
+      sCC[i] = gn < N ? sp.cC[gn] : 0;
+    }
+    __syncthreads();
+
+    double acc[4][4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+    double ra[A_PER_T], rb[B_PER_T];
+    auto load = [&](int64_t kt) {
+      const int64_t k0 = kt * BK;
+#pragma unroll
+      for (int i = 0; i < A_PER_T; ++i) {
+        int mm, kk;
+        a_coord(tid + i * NT, mm, kk);
+        const int64_t gm = m0 + mm, gk = k0 + kk;
+        ra[i] = (gm < M && gk < K) ? (double)a[sRA[mm] + sp.cA[gk]] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < B_PER_T; ++i) {
+        int nn, kk;
+        b_coord(tid + i * NT, nn, kk);
+        const int64_t gn = n0 + nn, gk = k0 + kk;
+        rb[i] = (gn < N && gk < K) ? (double)b[sp.rB[gk] + sCB[nn]] : 0.0;
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int i = 0; i < A_PER_T; ++i) {
+        int mm, kk;
+        a_coord(tid + i * NT, mm, kk);
+        As[(buf * BK + kk) * LDA + mm] = ra[i];
+      }
+#pragma unroll
+      for (int i = 0; i < B_PER_T; ++i) {
+        int nn, kk;
+        b_coord(tid + i * NT, nn, kk);
+        Bs[(buf * BK + kk) * LDB + nn] = rb[i];
+      }
+    };
+
+    load(kb);
     store(0);
-  }
-  __syncthreads();
-  for (int64_t kt = 0; kt < KT; ++kt) {
-    const int buf = (int)(kt & 1);
-    if (kt + 1 < KT) load(kt + 1);
-    const double* Ab = As + buf * BK * LDA + wm * 32 + g;
-    const double* Bb = Bs + buf * BK * LDB + wn * 32 + g;
+    __syncthreads();
+    for (int64_t kt = kb; kt < ke; ++kt) {
+      const int buf = (int)((kt - kb) & 1);
+      if (kt + 1 < ke) load(kt + 1);
+      const double* Ab = As + buf * BK * LDA + wm * 32 + g;
+      const double* Bb = Bs + buf * BK * LDB + wn * 32 + g;
 #pragma unroll
-    for (int kk = 0; kk < BK; kk += 4) {
-      double af[4], bf[4];
+      for (int kk = 0; kk < BK; kk += 4) {
+        double af[4], bf[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) af[i] = Ab[(kk + tig) * LDA + i * 8];
+        for (int i = 0; i < 4; ++i) af[i] = Ab[(kk + tig) * LDA + i * 8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bf[j] = Bb[(kk + tig) * LDB + j * 8];
+        for (int j = 0; j < 4; ++j) bf[j] = Bb[(kk + tig) * LDB + j * 8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+      }
+      if (kt + 1 < ke) store(buf ^ 1);
+      __syncthreads();
+    }
+
+    if (kb == 0 && ke == sk.KT) {
+      // K5: scattered epilogue, C[rscat + cscat] = alpha * acc + beta * C
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
+            if (m0 + mm < M && n0 + nn < N) {
+              T* p = c + sRC[mm] + sCC[nn];
+              double v = alpha * acc[i][j][q];
+              if (beta != 0.0) v += beta * (double)*p;
+              *p = (T)v;
+            }
+          }
+    } else {
+      double* slot = sk.partial + ((int64_t)blockIdx.x * 2 + (it == start ? 0 : 1)) * (BM * BN);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
+            slot[nn * BM + mm] = acc[i][j][q];
+          }
     }
-    if (kt + 1 < KT) store(buf ^ 1);
-    __syncthreads();
+    it = tile * sk.KT + ke;
   }
+}
 
-  // K5: scattered epilogue, C[rscat + cscat] = alpha * acc + beta * C
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
-        if (m0 + mm < M && n0 + nn < N) {
-          T* p = c + sRC[mm] + sCC[nn];
-          double v = alpha * acc[i][j][q];
-          if (beta != 0.0) v += beta * (double)*p;
-          *p = (T)v;
-        }
-      }
+// CTA f handles the tile cut by the boundary between ranges f and f+1, if that
+// boundary lies inside a tile and is the first boundary inside it.
+template <typename T>
+__global__ void __launch_bounds__(NT)
+    k_f64_fixup(T* __restrict__ c, const ScatterPtrs sp, const int64_t M, const int64_t N,
+                const double alpha, const double beta, const SkArgs sk) {
+  const int64_t Tt = sk.tiles * sk.KT;
+  const int64_t f = blockIdx.x;
+  if (f + 1 >= sk.G) return;
+  const int64_t bnd = sk_start(f + 1, Tt, sk.G);
+  if (bnd % sk.KT == 0) return;
+  const int64_t tile = bnd / sk.KT;
+  const int64_t t0 = tile * sk.KT, t1 = t0 + sk.KT;
+  if (sk_start(f, Tt, sk.G) > t0) return;  // an earlier boundary inside this tile owns it
+  // contributing CTAs: f (holding the start of the tile) up to the one holding t1 - 1
+  int64_t clast = f + 1;
+  while (clast + 1 < sk.G && sk_start(clast + 1, Tt, sk.G) < t1) ++clast;
+  const int64_t m0 = (tile / sk.tiles_n) * BM, n0 = (tile % sk.tiles_n) * BN;
+  for (int e = threadIdx.x; e < BM * BN; e += NT) {
+    const int mm = e % BM, nn = e / BM;
+    if (m0 + mm >= M || n0 + nn >= N) continue;
+    double s = 0.0;
+    for (int64_t cc = f; cc <= clast; ++cc) {
+      const int slot = sk_start(cc, Tt, sk.G) >= t0 ? 0 : 1;
+      s += sk.partial[(cc * 2 + slot) * (BM * BN) + e];
+    }
+    T* p = c + sp.rC[m0 + mm] + sp.cC[n0 + nn];
+    double v = alpha * s;
+    if (beta != 0.0) v += beta * (double)*p;
+    *p = (T)v;
+  }
 }
 
 template <typename T>
@@ -166,19 +241,43 @@ cudaError_t launch_t(const F64Launch& p, cudaStream_t s) {
     attr_set[dev] = true;
   }
   const int64_t tm = (p.m + BM - 1) / BM, tn = (p.n + BN - 1) / BN;
-  const int64_t tiles = tm * tn;
-  if (tiles == 0) return cudaSuccess;
-  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  SkArgs sk;
+  sk.tiles = tm * tn;
+  sk.tiles_n = tn;
+  sk.KT = (p.k + BK - 1) / BK;
+  sk.partial = p.partial;
+  sk.G = f64_grid(p.m, p.n, p.k, p.max_ctas, p.partial != nullptr);
+  if (sk.tiles == 0 || sk.KT == 0) return cudaSuccess;
+  if (sk.G > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   mainloop_event_before(s);
-  k_f64<T><<<(unsigned)tiles, NT, kSmem, s>>>((const T*)p.a, (const T*)p.b, (T*)p.c, p.sp, p.m,
-                                               p.n, p.k, p.alpha, p.beta, p.a_k_contig,
-                                               p.b_k_contig, tn);
+  k_f64<T><<<(unsigned)sk.G, NT, kSmem, s>>>((const T*)p.a, (const T*)p.b, (T*)p.c, p.sp, p.m,
+                                              p.n, p.k, p.alpha, p.beta, p.a_k_contig,
+                                              p.b_k_contig, sk);
   note_launch();
+  if (sk.G != sk.tiles) {
+    k_f64_fixup<T><<<(unsigned)sk.G, NT, 0, s>>>((T*)p.c, p.sp, p.m, p.n, p.alpha, p.beta, sk);
+    note_launch();
+  }
   mainloop_event_after(s);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// CTAs for the FP64 mainloop: plain tiling (one CTA per tile) when the tiles
+// fill whole waves of `max_ctas` (or no partial workspace is available),
+// otherwise stream-K over max_ctas CTAs, each taking at least 4 k-tiles.
+int64_t f64_grid(int64_t m, int64_t n, int64_t k, int64_t max_ctas, bool can_split) {
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const int64_t KT = (k + BK - 1) / BK;
+  if (!can_split || max_ctas <= 0 || tiles == 0 || KT == 0) return tiles;
+  const int64_t waves = (tiles + max_ctas - 1) / max_ctas;
+  if ((double)tiles / (double)(waves * max_ctas) >= 0.99) return tiles;
+  int64_t G = std::min<int64_t>(max_ctas, std::max<int64_t>(1, tiles * KT / 4));
+  return std::max<int64_t>(G, 1);
+}
+
+size_t f64_partial_bytes(int64_t max_ctas) { return (size_t)max_ctas * 2 * BM * BN * sizeof(double); }
 
 cudaError_t launch_f64(const F64Launch& p, cudaStream_t s) {
   return p.dtype == TC_F64 ? launch_t<double>(p, s) : launch_t<float>(p, s);

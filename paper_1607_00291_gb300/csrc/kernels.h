@@ -37,9 +37,13 @@ struct F64Launch {
   int64_t m, n, k;
   double alpha, beta;
   int a_k_contig, b_k_contig;
+  double* partial;   // stream-K partial tiles (f64_partial_bytes(max_ctas)), or null
+  int64_t max_ctas;  // CTAs for stream-K (one per SM); ignored without `partial`
   int32_t* err;
 };
 cudaError_t launch_f64(const F64Launch& p, cudaStream_t s);
+int64_t f64_grid(int64_t m, int64_t n, int64_t k, int64_t max_ctas, bool can_split);
+size_t f64_partial_bytes(int64_t max_ctas);
 
 // K3 + K5 (+ K4 when splits > 1) (bf16x3.cu): tcgen05 BF16x3 mainloop.
 struct Bf16Launch {

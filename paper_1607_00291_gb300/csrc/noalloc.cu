@@ -86,6 +86,8 @@ extern "C" int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor
   f.beta = beta;
   f.a_k_contig = p.info.a_k_contig;
   f.b_k_contig = p.info.b_k_contig;
+  f.partial = nullptr;  // plain tiling only: no stream-K partials in the fixed array
+  f.max_ctas = 0;
   f.err = nullptr;
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
