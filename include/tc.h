@@ -52,7 +52,8 @@ typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
  *  TC_MODE_BF16X3 -- F32 data only: each operand split as x = hi + lo with
  *                    hi = RN_bf16(x), lo = RN_bf16(x - hi); hi*hi + hi*lo + lo*hi
  *                    on the tensor cores with FP32 accumulation, split-K
- *                    partials reduced in FP64.  Two bf16 pieces hold 16 of
+ *                    partials summed with compensated (two-sum) FP32
+ *                    arithmetic.  Two bf16 pieces hold 16 of
  *                    FP32's 24 significand bits: a single product can be off
  *                    by up to about 3 * 2^-16 of |a||b|.
  *  TC_MODE_BF16X6 -- as BF16X3 with three pieces x = b0 + b1 + b2 (exact for

@@ -1,6 +1,7 @@
 // libtc C ABI: argument checks, planning, workspace carving and launches.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -64,35 +65,44 @@ int sm_count() {
   return n;
 }
 
-// Tile width and split of the contracted range for the tensor-core mainloop.
-// Two constraints fix the split count S:
-//  * accuracy: the tensor core accumulates in FP32 with unspecified rounding,
-//    so each CTA's chain is capped at kChainTiles k-tiles of 32 (1024 terms);
-//    the FP32 partials of the S chains are then summed in FP64 (K4);
-//  * parallelism: when the output alone has fewer tiles than SMs, split
-//    further so the grid covers the SMs, keeping at least 8 k-tiles a split.
+// Tile shape and split of the contracted range for the tensor-core mainloop.
+//  * tile width bn: the next multiple of 16 above n when n < 128; otherwise
+//    128, or 256 (two-piece mode only) when that fills the SMs' waves as well;
+//  * split count S, from two constraints: accuracy -- the tensor core
+//    accumulates in FP32 with unspecified rounding, so each CTA's chain is
+//    capped at kChainTiles k-tiles of 32 (1024 terms) and the FP32 partials are
+//    summed with compensated FP32 arithmetic (K4); parallelism -- when the output alone has fewer tiles
+//    than SMs, split further so the grid covers the SMs, keeping at least 8
+//    k-tiles per split.
 constexpr int64_t kChainTiles = 32;
 
-struct Bf16Choice {
-  int bn, splits;
+struct TcChoice {
+  int bn, bn_max, splits;
   int64_t kps;
 };
 
-Bf16Choice choose_bf16(const Layout& L, int sms) {
-  Bf16Choice c;
+TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force = 0, int split_mult = 1) {
+  TcChoice c;
   const int64_t tm = (L.m + 127) / 128;
   auto waves_eff = [&](int bn) {
     const int64_t t = tm * ((L.n + bn - 1) / bn);
     const int64_t w = (t + sms - 1) / sms;
     return (double)t / (double)(w * sms) * (bn == 256 ? 1.0 : 0.97);
   };
-  c.bn = (L.n > 128 && waves_eff(256) >= waves_eff(128)) ? 256 : 128;
+  if (bn_force > 0) {
+    c.bn = bn_force;
+  } else if (L.n < 128) {
+    c.bn = (int)std::max<int64_t>(16, (L.n + 15) / 16 * 16);
+  } else {
+    c.bn = (pieces == 2 && L.n > 128 && waves_eff(256) >= waves_eff(128)) ? 256 : 128;
+  }
+  c.bn_max = tc_bn_max_for(pieces, c.bn);
   const int64_t tiles = tm * ((L.n + c.bn - 1) / c.bn);
   const int64_t kt = (L.k + 31) / 32;
   const int64_t s_acc = (kt + kChainTiles - 1) / kChainTiles;
   int64_t s_par = 1;
   if (tiles < sms) s_par = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
-  int64_t s = std::max<int64_t>(1, std::max(s_acc, s_par));
+  int64_t s = std::max<int64_t>(1, std::max(s_acc, s_par)) * std::max(1, split_mult);
   s = std::min<int64_t>(s, std::max<int64_t>(kt, 1));
   const int64_t ktps = (kt + s - 1) / s;
   c.kps = ktps * 32;
@@ -105,7 +115,7 @@ struct WsLayout {
   size_t scatter_off, scatter_bytes;
   size_t partial_off, partial_bytes;
   size_t total;
-  Bf16Choice bf;
+  TcChoice tcc;
 };
 
 WsLayout ws_layout(const Planned& p, tc_mode mode) {
@@ -115,11 +125,19 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
   w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
   w.partial_off = w.scatter_bytes;
   w.partial_bytes = 0;
-  w.bf = Bf16Choice{128, 1, 0};
+  w.tcc = TcChoice{128, 128, 1, 0};
   if (mode != TC_MODE_F64 && p.L.k > 0) {
-    w.bf = choose_bf16(p.L, sm_count());
-    if (w.bf.splits > 1)
-      w.partial_bytes = align_up((size_t)w.bf.splits * p.L.m * p.L.n * sizeof(float), 256);
+    // TC_FORCE_BN (16..256, step 16; 256 only with two pieces) pins the tile
+    // width, for tests and tuning experiments
+    int force = 0;
+    if (const char* e = std::getenv("TC_FORCE_BN")) {
+      const int v = std::atoi(e);
+      const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+      if (v >= 16 && v % 16 == 0 && v <= (pieces == 2 ? 256 : 128)) force = v;
+    }
+    w.tcc = choose_tc(p.L, mode == TC_MODE_BF16X6 ? 3 : 2, sm_count(), force);
+    if (w.tcc.splits > 1)
+      w.partial_bytes = align_up((size_t)w.tcc.splits * p.L.m * p.L.n * sizeof(float), 256);
   }
   if (mode == TC_MODE_F64 && p.L.k > 0) {
     const int sms = sm_count();
@@ -153,25 +171,30 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   if (L.k == 0 || alpha == 0.0)
     return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
   if (mode != TC_MODE_F64) {
-    Bf16Launch q;
+    TcLaunch q;
+    std::memset(&q, 0, sizeof q);
+    DevProblem& d = q.single;
+    d.a = p.a;
+    d.b = p.b;
+    d.c = p.c;
+    d.partial = w.tcc.splits > 1 ? static_cast<char*>(ws) + w.partial_off : nullptr;
+    d.sp = sp;
+    d.m = L.m;
+    d.n = L.n;
+    d.k = L.k;
+    d.alpha = alpha;
+    d.beta = beta;
+    d.a_kc = p.info.a_k_contig;
+    d.b_kc = p.info.b_k_contig;
+    d.bn = w.tcc.bn;
+    d.tiles_n = (int32_t)((L.n + d.bn - 1) / d.bn);
+    d.splits = w.tcc.splits;
+    d.kps = w.tcc.kps;
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
-    q.a = p.a;
-    q.b = p.b;
-    q.c = p.c;
-    q.partial = reinterpret_cast<float*>(static_cast<char*>(ws) + w.partial_off);
-    q.sp = sp;
-    q.m = L.m;
-    q.n = L.n;
-    q.k = L.k;
-    q.alpha = alpha;
-    q.beta = beta;
-    q.a_k_contig = p.info.a_k_contig;
-    q.b_k_contig = p.info.b_k_contig;
-    q.bn = w.bf.bn;
-    q.splits = w.bf.splits;
-    q.k_per_split = w.bf.kps;
+    q.bn_max = w.tcc.bn_max;
+    q.ctas = sm_count();
     q.err = err_word();
-    return launch_bf16x3(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+    return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
   }
   F64Launch f;
   f.dtype = dt;

@@ -45,22 +45,47 @@ cudaError_t launch_f64(const F64Launch& p, cudaStream_t s);
 int64_t f64_grid(int64_t m, int64_t n, int64_t k, int64_t max_ctas, bool can_split);
 size_t f64_partial_bytes(int64_t max_ctas);
 
-// K3 + K5 (+ K4 when splits > 1) (bf16x3.cu): tcgen05 BF16x3 mainloop.
-struct Bf16Launch {
+// One planned contraction as the persistent kernels see it: a kernel
+// parameter for a single call, an array in device memory for a batch.
+struct DevProblem {
   const void* a;
   const void* b;
   void* c;
-  float* partial;  // splits * m * n FP32, used when splits > 1
+  void* partial;    // split partial sums, [splits][n][m] (FP32 on the tensor-core
+                    // path, FP64 on the FP64 path); null when splits == 1
   ScatterPtrs sp;
   int64_t m, n, k;
   double alpha, beta;
-  int a_k_contig, b_k_contig;
-  int bn;          // 128 or 256
-  int pieces;      // bf16 pieces per operand: 2 (BF16x3) or 3 (BF16x6)
-  int splits;      // CTAs along the contracted range
-  int64_t k_per_split;  // multiple of 32
+  int32_t a_kc, b_kc;
+  int32_t tiles_n;  // output tiles along n
+  int32_t bn;       // n-width of an output tile (tensor-core path: 16..256, step 16)
+  int32_t splits;   // pieces of the contracted range
+  int32_t pad0;
+  int64_t kps;      // contracted indices per split (a multiple of the k-tile)
+};
+
+// One unit of work of a batch: an output tile of a problem over one k-split.
+struct WorkItem {
+  int32_t prob, tile, split, pad;
+};
+
+// K3 + K5 (tc_mma.cu): tcgen05 mainloop over bf16 pieces (2 -> BF16x3,
+// 3 -> BF16x6), persistent over work items; K4 reduces split partials (two-sum FP32).
+struct TcLaunch {
+  DevProblem single;          // the problem of a single call (probs == null)
+  const DevProblem* probs;    // batch descriptors (device), or null
+  const WorkItem* items;      // batch work list (device), or null
+  int64_t nitems;             // work items in the list (batch)
+  int32_t nprobs;             // problems in the batch
+  int pieces;                 // 2 or 3
+  int bn_max;                 // 128 or 256: shared-memory plan of the kernel
+  int64_t ctas;               // persistent grid size
+  const int32_t* split_probs; // batch: indices of problems with splits > 1 (device)
+  int32_t n_split_probs;
+  int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
   int32_t* err;
 };
-cudaError_t launch_bf16x3(const Bf16Launch& q, cudaStream_t s);
+cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
+int tc_bn_max_for(int pieces, int bn);
 
 }  // namespace tc

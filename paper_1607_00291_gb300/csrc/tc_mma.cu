@@ -1,0 +1,648 @@
+// K3 + K5: the FP32 contraction on the fifth-generation tensor cores (tcgen05),
+// persistent over output tiles (of one problem, or of a batch of problems).
+//
+// Each operand panel is gathered in place through the scatter vectors of
+// Section 6.1 -- 16-byte cp.async copies wherever the block-scatter vectors of
+// Section 6.2 (or the row scatter entries) show a unit-stride run of four,
+// 4-byte copies otherwise, zero-filled past the end of the contracted range --
+// into a raw FP32 stage.  Converter warps split every value into bf16 pieces
+// (x = b0 + b1 [+ b2], each b_i = RN_bf16 of the residual left so far, every
+// residual exact in FP32) and write them in the tensor core's K-major
+// canonical layout.  One elected thread issues, per 16-wide k-slice, a
+// tcgen05.mma for every piece pair (i, j) with i + j < pieces -- three for two
+// pieces (BF16x3), six for three (BF16x6) -- into an FP32 accumulator in
+// Tensor Memory.  The epilogue reads it with tcgen05.ld and applies alpha/beta
+// through rscat(C) + cscat(C), or, when the contracted range is split, stores
+// FP32 partials that K4 sums with compensated FP32 arithmetic.
+//
+// Warp roles (672 threads): warps 0-7 load (cp.async), warps 8-15 convert,
+// warps 16-19 run the epilogue (one per Tensor Memory lane quarter), warp 20
+// owns the Tensor Memory allocation and its lane 0 issues the MMAs.  The
+// accumulator is double-buffered in Tensor Memory, so the epilogue of one tile
+// overlaps the MMAs of the next.  Hand-offs go through mbarriers: raw_full
+// (cp.async completion) / raw_empty, mma_full / mma_empty (tcgen05.commit),
+// acc_full[2] (tcgen05.commit) / acc_empty[2].  Every
+// mbarrier wait is bounded: on expiry the CTA records TC_ERR_DEVICE_TIMEOUT in
+// the device error word and raises a CTA-wide abort flag; the roles leave
+// their loops together (barrier reductions of the flag), the MMA thread waits
+// for its issued MMAs to drain, and Tensor Memory is always released.
+//
+// Rows of a panel beyond the operand's edge are not loaded: a row of A (or B)
+// only reaches the matching row (column) of the accumulator, which the
+// epilogue skips.  Past the end of the contracted range the panels are
+// zero-filled, since those entries reach every output.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "sm100_ptx.cuh"
+
+namespace tc {
+namespace {
+
+using namespace ptx;
+
+constexpr int BM = 128, BK = 32;
+constexpr int NLOAD = 256, NCONV = 256, NEPI = 128;
+constexpr int NT = NLOAD + NCONV + NEPI + 32;
+constexpr int CONV_W0 = NLOAD / 32;
+constexpr int EPI_W0 = (NLOAD + NCONV) / 32;
+constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
+constexpr int BAR_LOAD = 1, BAR_CONV = 2, BAR_EPI = 3;
+constexpr int KRING = 3;
+constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
+
+template <int BNMAX, int NS>
+struct Lay {
+  static constexpr int RS = BNMAX == 256 ? 2 : (NS == 3 ? 3 : 4);  // raw FP32 stages
+  static constexpr int MS = 2;                                   // bf16 MMA stages
+  static constexpr int PA = BM * BK * 2;                        // one bf16 piece of A
+  static constexpr int PB = BNMAX * BK * 2;
+  static constexpr int B_OFF = NS * PA;
+  static constexpr int MMA_STAGE = NS * (PA + PB);
+  static constexpr int RAW_A = BM * BK * 4;
+  static constexpr int RAW_STAGE = RAW_A + BNMAX * BK * 4;
+  static constexpr int MMA0 = 0;
+  static constexpr int RAW0 = MMA0 + MS * MMA_STAGE;
+  static constexpr int SCAT = RAW0 + RS * RAW_STAGE;  // int64 rA[BM] cB[BNMAX] rC[BM] cC[BNMAX]
+  static constexpr int KR = SCAT + (2 * BM + 2 * BNMAX) * 8;  // k ring: KRING x KSLOT int64
+  static constexpr int PROB = KR + KRING * KSLOT * 8;
+  static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
+  static constexpr int NBARS = 2 * RS + 2 * MS + 5;
+  static constexpr int MISC = BARS + NBARS * 8;
+  static constexpr int END = MISC + 16;
+  static constexpr int ALLOC = END + 1024;
+  static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
+  static_assert(BNMAX % NEPI == 0 && BM == NEPI && NLOAD % 32 == 0 && BK % (NLOAD / 32) == 0,
+                "thread maps of the loaders and the epilogue");
+};
+
+// byte offset of (row r, k-chunk q of 8) in an R-row K-major bf16 panel:
+// 8-row x 16-byte core matrices, rows 16 B apart inside one, row groups 128 B
+// apart (SBO), k-chunks R*16 B apart (LBO)
+template <int R>
+__device__ __forceinline__ uint32_t panel_off(int r, int q) {
+  return (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16);
+}
+
+// Split 8 FP32 values into NS bf16 pieces and store one 16-byte core-matrix
+// row per piece (pieces `piece_bytes` apart).
+template <int NS>
+__device__ __forceinline__ void split8_store(float (&v)[8], uint8_t* piece0, int piece_bytes,
+                                             uint32_t off) {
+#pragma unroll
+  for (int sidx = 0; sidx < NS; ++sidx) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      if (sidx + 1 < NS) {
+        const float2 f = __bfloat1622float2(b);
+        v[2 * j] -= f.x;
+        v[2 * j + 1] -= f.y;
+      }
+      w[j] = *reinterpret_cast<uint32_t*>(&b);
+    }
+    *reinterpret_cast<uint4*>(piece0 + sidx * piece_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+struct Args {
+  DevProblem single;
+  const DevProblem* probs;
+  const WorkItem* items;
+  int64_t nitems;
+  int64_t tiles_single;
+  int32_t* err;
+};
+
+__device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err) {
+  *abort = 1;
+  if (err) atomicCAS(err, 0, kDevTimeout);
+}
+
+struct Item {
+  const DevProblem* d;
+  int64_t m0, n0, kbeg, kend, KT;
+  int split;
+  int rows_a, rows_b;
+};
+
+__device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w) {
+  Item it;
+  int64_t tile;
+  if (a.probs) {
+    const WorkItem wi = a.items[w];
+    it.d = a.probs + wi.prob;
+    tile = wi.tile;
+    it.split = wi.split;
+  } else {
+    it.d = single;
+    tile = w % a.tiles_single;
+    it.split = (int)(w / a.tiles_single);
+  }
+  const DevProblem* d = it.d;
+  it.m0 = (tile / d->tiles_n) * BM;
+  it.n0 = (tile % d->tiles_n) * d->bn;
+  it.kbeg = (int64_t)it.split * d->kps;
+  it.kend = it.kbeg + d->kps < d->k ? it.kbeg + d->kps : d->k;
+  it.KT = it.kend > it.kbeg ? (it.kend - it.kbeg + BK - 1) / BK : 0;
+  it.rows_a = (int)(d->m - it.m0 < BM ? d->m - it.m0 : BM);
+  it.rows_b = (int)(d->n - it.n0 < d->bn ? d->n - it.n0 : d->bn);
+  return it;
+}
+
+// ---- loader: one raw FP32 panel of R rows x BK k through cp.async ----------------------
+// Layouts of a raw stage:
+//  * k-contiguous operand: raw[row][BK], the eight 16-byte chunks of a row
+//    stored at position (chunk ^ (row & 7)), so that both the loaders' writes
+//    and the converters' reads touch all 32 banks once per quarter-warp;
+//  * row-contiguous operand: raw[BK][R].
+// The k side of every address comes from a small ring in shared memory that
+// holds, per k-tile, the 32 scatter entries of each operand along k and their
+// 8 block-scatter entries; loader thread i < KSLOT fetches entry i of the
+// k-tile two ahead while the current one is issued, so the latency of the
+// scatter vectors stays off the critical path.  The row side of every address
+// comes from the row scatter entries of the tile, also in shared memory.
+// Consecutive threads walk each operand's unit-stride index.
+__device__ __forceinline__ int64_t kslot_fetch(int i, const DevProblem* d, int64_t k0,
+                                               int64_t kend) {
+  if (i < BK) return k0 + i < kend ? __ldg(d->sp.cA + k0 + i) : 0;
+  if (i < 2 * BK) return k0 + (i - BK) < kend ? __ldg(d->sp.rB + k0 + (i - BK)) : 0;
+  const int b = i - 2 * BK;  // block-scatter entries: k blocks of 4
+  const int64_t kb = (k0 >> 2) + (b & 7);
+  const bool ok = (kb << 2) < kend;
+  if (b < BK / 4) return ok ? __ldg(d->sp.cbsA + kb) : 0;
+  return ok ? __ldg(d->sp.rbsB + kb) : 0;
+}
+
+template <int R>
+__device__ __forceinline__ void load_panel(int t, uint32_t raw, const float* __restrict__ base,
+                                           const int64_t* rowsc, int rows_valid,
+                                           const int64_t* ks, const int64_t* kbs, int64_t k0,
+                                           int64_t kend, bool kcontig) {
+  if (kcontig) {
+    constexpr int RSTEP = NLOAD / 8;  // rows per pass of the loaders
+    const int q4 = t & 7;
+    const int64_t kq = k0 + 4 * q4;
+    const bool vec = kq + 3 < kend && kbs[q4] == 1;
+    int64_t ko[4];
+    uint32_t valid = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ko[j] = ks[4 * q4 + j];
+      valid |= (uint32_t)(kq + j < kend) << j;
+    }
+#pragma unroll
+    for (int i = 0; i < R / RSTEP; ++i) {
+      const int r = (t >> 3) + RSTEP * i;
+      if (r < rows_valid) {
+        const uint32_t dst = raw + (uint32_t)(r * BK * 4 + ((q4 ^ (r & 7)) << 4));
+        const float* rowp = base + rowsc[r];
+        const float* p = rowp + ko[0];
+        if (vec && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+          cp_async16(dst, p, 16);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool ok = (valid >> j) & 1;
+            cp_async4(dst + 4 * j, ok ? rowp + ko[j] : base, ok ? 4u : 0u);
+          }
+        }
+      }
+    }
+  } else {
+    constexpr int KSTEP = NLOAD / 32;  // k positions per pass of the loaders
+    const int kk0 = t >> 5;
+#pragma unroll
+    for (int u = 0; u < R / 128; ++u) {
+      const int r0 = 4 * ((t & 31) + 32 * u);
+      if (r0 >= rows_valid) continue;
+      const int64_t o0 = rowsc[r0];
+      const bool quad = r0 + 3 < rows_valid && rowsc[r0 + 1] == o0 + 1 &&
+                        rowsc[r0 + 2] == o0 + 2 && rowsc[r0 + 3] == o0 + 3;
+#pragma unroll
+      for (int v = 0; v < BK / KSTEP; ++v) {
+        const int kk = kk0 + KSTEP * v;
+        const uint32_t dst = raw + (uint32_t)(kk * R + r0) * 4;
+        const bool ok = k0 + kk < kend;
+        const int64_t ko = ks[kk];
+        const float* p = base + o0 + ko;
+        if (ok && quad && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+          cp_async16(dst, p, 16);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (r0 + i < rows_valid)
+              cp_async4(dst + 4 * i, ok ? base + rowsc[r0 + i] + ko : base, ok ? 4u : 0u);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---- converter: raw panel -> NS bf16 pieces in the canonical layout ------------------
+// Task c = (row r = c % R, k-chunk q = c / R): a warp covers 32 consecutive
+// rows of one k-chunk, so its 16-byte core-matrix row stores are contiguous.
+template <int R, int NS>
+__device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t* piece0,
+                                              bool kcontig) {
+  constexpr int TASKS = R * BK / 8;
+  constexpr int PBY = R * BK * 2;
+  const float* rf = reinterpret_cast<const float*>(raw);
+#pragma unroll
+  for (int i = 0; i < TASKS / NCONV; ++i) {
+    const int c = t + i * NCONV;
+    const int r = c % R, q = c / R;
+    float v[8];
+    if (kcontig) {
+      const float* row = rf + r * BK;
+      const float4 x0 = *reinterpret_cast<const float4*>(row + (((2 * q) ^ (r & 7)) << 2));
+      const float4 x1 = *reinterpret_cast<const float4*>(row + (((2 * q + 1) ^ (r & 7)) << 2));
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = rf[(8 * q + j) * R + r];
+    }
+    split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
+  }
+}
+
+template <int BNMAX, int NS>
+__global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
+  using Ly = Lay<BNMAX, NS>;
+  constexpr int RS = Ly::RS, MS = Ly::MS;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // align to 1 KB by offsetting the shared-memory pointer itself, so that the
+  // compiler keeps every access below in the shared state space
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  int64_t* sRA = reinterpret_cast<int64_t*>(smem + Ly::SCAT);  // loaders' rows
+  int64_t* sCB = sRA + BM;
+  int64_t* sRC = sCB + BNMAX;  // epilogue's rows
+  int64_t* sCC = sRC + BM;
+  int64_t* kring = reinterpret_cast<int64_t*>(smem + Ly::KR);
+  DevProblem* sProb = reinterpret_cast<DevProblem*>(smem + Ly::PROB);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem + Ly::BARS);
+  uint64_t* raw_empty = raw_full + RS;
+  uint64_t* mma_full = raw_empty + RS;
+  uint64_t* mma_empty = mma_full + MS;
+  uint64_t* acc_full = mma_empty + MS;  // [2]
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < RS; ++s) {
+      mbar_init(&raw_full[s], NLOAD);
+      mbar_init(&raw_empty[s], NCONV);
+    }
+    for (int s = 0; s < MS; ++s) {
+      mbar_init(&mma_full[s], NCONV);
+      mbar_init(&mma_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], NEPI);
+    }
+    mbar_init(drain, 1);
+    *abort = 0;
+    *sProb = a.single;
+    fence_mbar_init();
+  }
+  if (warp == MMA_WARP) {
+    tmem_alloc(tmem_slot, 2 * BNMAX);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t nitems = a.nitems;
+  const int64_t w0 = blockIdx.x, dw = gridDim.x;
+
+  if (warp < CONV_W0) {
+    // ---- loaders ----
+    const int t = tid;
+    int64_t g = 0;  // k-tiles staged by this CTA so far
+    // row scatter entries of the next item, fetched one item ahead
+    constexpr int NR = (BM + BNMAX + NLOAD - 1) / NLOAD;  // rows (A then B) per thread
+    int64_t pre[NR];
+    auto fetch_rows = [&](const Item& it) {
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int r = t + i * NLOAD;
+        pre[i] = 0;
+        if (r < BM) {
+          if (r < it.rows_a) pre[i] = __ldg(it.d->sp.rA + it.m0 + r);
+        } else if (r < BM + BNMAX) {
+          if (r - BM < it.rows_b) pre[i] = __ldg(it.d->sp.cB + it.n0 + (r - BM));
+        }
+      }
+    };
+    if (w0 < nitems) fetch_rows(get_item(a, sProb, w0));
+    for (int64_t w = w0; w < nitems; w += dw) {
+      if (bar_or(BAR_LOAD, NLOAD, *abort)) break;  // uniform exit; previous rows consumed
+      const Item it = get_item(a, sProb, w);
+      const DevProblem* d = it.d;
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int r = t + i * NLOAD;
+        if (r < BM + BNMAX) sRA[r] = pre[i];  // sCB follows sRA contiguously
+      }
+      if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
+      const float* A = static_cast<const float*>(d->a);
+      const float* B = static_cast<const float*>(d->b);
+      const bool akc = d->a_kc, bkc = d->b_kc;
+      // k ring: entries of k-tiles 0 and 1 of this item
+      if (t < KSLOT) {
+        for (int64_t kt = 0; kt < 2 && kt < it.KT; ++kt)
+          kring[(kt % KRING) * KSLOT + t] = kslot_fetch(t, d, it.kbeg + kt * BK, it.kend);
+      }
+      bar_sync(BAR_LOAD, NLOAD);
+      for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
+        int64_t ahead = 0;
+        const bool fetch = t < KSLOT && kt + 2 < it.KT;
+        if (fetch) ahead = kslot_fetch(t, d, it.kbeg + (kt + 2) * BK, it.kend);
+        const int s = (int)(g % RS);
+        const bool ok = mbar_wait(&raw_empty[s], (uint32_t)(((g / RS) & 1) ^ 1), abort);
+        if (!ok) record_timeout(abort, a.err);
+        if (ok) {
+          const uint32_t raw = smem_u32(smem + Ly::RAW0 + s * Ly::RAW_STAGE);
+          const int64_t* slot = kring + (kt % KRING) * KSLOT;
+          const int64_t k0 = it.kbeg + kt * BK;
+          load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc);
+          load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sCB, it.rows_b, slot + BK,
+                            slot + 2 * BK + BK / 4, k0, it.kend, bkc);
+          cp_async_arrive(&raw_full[s]);
+        }
+        if (fetch) kring[((kt + 2) % KRING) * KSLOT + t] = ahead;
+        // slot kt+2 now complete and slot kt free for reuse; a timeout anywhere
+        // makes every loader leave together
+        if (bar_or(BAR_LOAD, NLOAD, !ok)) break;
+      }
+    }
+  } else if (warp < EPI_W0) {
+    // ---- converters ----
+    const int t = tid - NLOAD;
+    int64_t g = 0;
+    for (int64_t w = w0; w < nitems; w += dw) {
+      if (bar_or(BAR_CONV, NCONV, *abort)) break;  // uniform exit
+      const Item it = get_item(a, sProb, w);
+      const bool akc = it.d->a_kc, bkc = it.d->b_kc;
+      for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
+        const int rs = (int)(g % RS), ms = (int)(g % MS);
+        if (!mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) ||
+            !mbar_wait(&mma_empty[ms], (uint32_t)(((g / MS) & 1) ^ 1), abort)) {
+          record_timeout(abort, a.err);
+          break;
+        }
+        const uint8_t* raw = smem + Ly::RAW0 + rs * Ly::RAW_STAGE;
+        uint8_t* st = smem + Ly::MMA0 + ms * Ly::MMA_STAGE;
+        convert_panel<BM, NS>(t, raw, st, akc);
+        convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc);
+        fence_proxy_async_smem();
+        mbar_arrive(&mma_full[ms]);
+        mbar_arrive(&raw_empty[rs]);
+      }
+    }
+  } else if (warp < MMA_WARP) {
+    // ---- epilogue: one thread per accumulator row ----
+    const int t = tid - NLOAD - NCONV;
+    const int wq = warp & 3;  // Tensor Memory lane quarter of this warp
+    const int row = 32 * wq + lane;
+    constexpr int NB = BNMAX / NEPI;
+    int64_t pre_r = 0, pre_c[NB];
+    auto fetch_rows = [&](const Item& it) {
+      pre_r = t < it.rows_a ? __ldg(it.d->sp.rC + it.m0 + t) : 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const int c = t + i * NEPI;
+        pre_c[i] = c < it.rows_b ? __ldg(it.d->sp.cC + it.n0 + c) : 0;
+      }
+    };
+    if (w0 < nitems) fetch_rows(get_item(a, sProb, w0));
+    int64_t j = 0;
+    for (int64_t w = w0; w < nitems; w += dw, ++j) {
+      if (bar_or(BAR_EPI, NEPI, *abort)) break;  // uniform exit; previous rows consumed
+      const Item it = get_item(a, sProb, w);
+      const DevProblem* d = it.d;
+      sRC[t] = pre_r;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
+      if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
+      bar_sync(BAR_EPI, NEPI);
+      const int b = (int)(j & 1);
+      const bool have = it.KT > 0;
+      if (have && !*abort) {
+        if (!mbar_wait(&acc_full[b], (uint32_t)((j >> 1) & 1), abort)) record_timeout(abort, a.err);
+      }
+      tc_fence_after();
+      const bool ok = __all_sync(0xffffffffu, !*abort);
+      const bool mv = row < it.rows_a;
+      const int bn = d->bn;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BNMAX);
+      if (ok) {
+        const bool direct = d->splits == 1;
+        const double alpha = d->alpha, beta = d->beta;
+        float* cbase = static_cast<float*>(d->c) + sRC[row];
+        float* pbase = direct ? nullptr
+                              : static_cast<float*>(d->partial) +
+                                    ((int64_t)it.split * d->n + it.n0) * d->m + it.m0 + row;
+        const int64_t m = d->m;
+        for (int cb = 0; cb < bn; cb += 16) {
+          float v[16];
+          if (have) {
+            tmem_ld16(tbase + (uint32_t)cb, v);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = 0.f;
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int col = cb + q;
+            if (mv && col < it.rows_b) {
+              if (direct) {
+                float* cp = cbase + sCC[col];
+                double r = alpha * (double)v[q];
+                if (beta != 0.0) r += beta * (double)*cp;
+                *cp = (float)r;
+              } else {
+                pbase[(int64_t)col * m] = v[q];
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+    }
+  } else if (lane == 0) {
+    // ---- MMA issue ----
+    const uint32_t base = smem_u32(smem + Ly::MMA0);
+    int64_t g = 0, j = 0;
+    for (int64_t w = w0; w < nitems && !*abort; w += dw, ++j) {
+      const Item it = get_item(a, sProb, w);
+      const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
+      const int b = (int)(j & 1);
+      const int64_t u = j >> 1;  // use count of accumulator buffer b
+      if (u > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), abort)) {
+        record_timeout(abort, a.err);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)(b * BNMAX);
+      bool failed = false;
+      for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
+        const int ms = (int)(g % MS);
+        if (!mbar_wait(&mma_full[ms], (uint32_t)((g / MS) & 1), abort)) {
+          record_timeout(abort, a.err);
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + ms * Ly::MMA_STAGE;
+#pragma unroll
+        for (int ksl = 0; ksl < BK / 16; ++ksl) {
+          const uint32_t ao = ksl * 2 * (BM / 8) * 128, bo = ksl * 2 * (BNMAX / 8) * 128;
+          uint64_t dA[NS], dB[NS];
+#pragma unroll
+          for (int i = 0; i < NS; ++i) {
+            dA[i] = smem_desc(st + i * Ly::PA + ao, (BM / 8) * 128, 128);
+            dB[i] = smem_desc(st + Ly::B_OFF + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
+          }
+          mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > 0 || ksl > 0) ? 1u : 0u);
+#pragma unroll
+          for (int ts = 1; ts < NS; ++ts)
+#pragma unroll
+            for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+        }
+        mma_commit(&mma_empty[ms]);
+      }
+      if (failed) break;
+      if (it.KT > 0) mma_commit(&acc_full[b]);
+      else mbar_arrive(&acc_full[b]);  // nothing to accumulate: hand over at once
+    }
+    // every MMA this thread issued has completed once this commit arrives
+    mma_commit(drain);
+    if (!mbar_wait(drain, 0, abort)) {
+      // even on abort, wait for the drain itself (bounded) before releasing TMEM
+      const long long t0 = clock64();
+      while (!mbar_try_wait(drain, 0) && clock64() - t0 < 4000000000LL) {
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * BNMAX);
+  }
+}
+
+
+// K4: C = alpha * (sum of the FP32 partials of the k-splits) + beta * C.
+// The partials are added with error-free transformations (Knuth's two-sum,
+// then the collected errors once: the cascade "Sum2" of Ogita, Rump and
+// Oishi), which yields the sum as if computed in twice FP32's precision
+// before the final rounding -- for S <= 64 FP32 partials as good as an FP64
+// sum -- while running on the FP32 pipes: on GB300 FP64 arithmetic is slow
+// enough (about 1.1 TFLOP/s) that an FP64 reduction of tens of millions of
+// elements costs a large share of the contraction itself.
+// Grid: x over m (plus a stride loop), y over n, z over the split problems of
+// a batch; no integer division per element.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__global__ void k_reduce_partials(const DevProblem single, const DevProblem* probs,
+                                  const int32_t* split_probs) {
+  const DevProblem* dp = probs ? probs + split_probs[blockIdx.z] : nullptr;
+  const int64_t M = dp ? dp->m : single.m, N = dp ? dp->n : single.n;
+  const int S = dp ? dp->splits : single.splits;
+  const float* part = static_cast<const float*>(dp ? dp->partial : single.partial);
+  float* c = static_cast<float*>(dp ? dp->c : single.c);
+  const int64_t* rC = dp ? dp->sp.rC : single.sp.rC;
+  const int64_t* cC = dp ? dp->sp.cC : single.sp.cC;
+  const float alpha = (float)(dp ? dp->alpha : single.alpha);
+  const float beta = (float)(dp ? dp->beta : single.beta);
+  const int64_t plane = M * N;
+  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
+    const int64_t cn = __ldg(cC + n);
+    const float* pn = part + n * M;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+      float hi = __ldg(pn + m), lo = 0.f;
+      for (int ks = 1; ks < S; ++ks) {
+        float e;
+        two_sum(hi, __ldg(pn + ks * plane + m), hi, e);
+        lo = __fadd_rn(lo, e);
+      }
+      float* cp = c + __ldg(rC + m) + cn;
+      // alpha * (hi + lo) [+ beta * C], the small term folded in first
+      float r = __fmaf_rn(alpha, hi, alpha * lo);
+      if (beta != 0.f) r = __fmaf_rn(beta, *cp, r);
+      *cp = r;
+    }
+  }
+}
+
+template <int BNMAX, int NS>
+cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc<BNMAX, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Lay<BNMAX, NS>::ALLOC);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  Args a;
+  a.single = q.single;
+  a.probs = q.probs;
+  a.items = q.items;
+  a.err = q.err;
+  if (q.probs) {
+    a.nitems = q.nitems;
+    a.tiles_single = 1;
+  } else {
+    a.tiles_single = ((q.single.m + BM - 1) / BM) * q.single.tiles_n;
+    a.nitems = a.tiles_single * q.single.splits;
+  }
+  if (a.nitems == 0) return cudaSuccess;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
+  mainloop_event_before(s);
+  k_tc<BNMAX, NS><<<(unsigned)grid, NT, Lay<BNMAX, NS>::ALLOC, s>>>(a);
+  note_launch();
+  const bool single_split = !q.probs && q.single.splits > 1;
+  if (single_split || (q.probs && q.n_split_probs > 0)) {
+    const int64_t mm = single_split ? q.single.m : q.max_m_split;
+    const int64_t nn = single_split ? q.single.n : q.max_n_split;
+    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((mm + 255) / 256, 64));
+    const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nn, 32768));
+    dim3 grid2(bx, by, single_split ? 1u : (unsigned)q.n_split_probs);
+    k_reduce_partials<<<grid2, 256, 0, s>>>(q.single, q.probs, q.split_probs);
+    note_launch();
+  }
+  mainloop_event_after(s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_bn_max_for(int pieces, int bn) { return (pieces == 2 && bn > 128) ? 256 : 128; }
+
+cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
+  if (q.pieces == 3) return launch_cfg<128, 3>(q, s);
+  return q.bn_max == 256 ? launch_cfg<256, 2>(q, s) : launch_cfg<128, 2>(q, s);
+}
+
+}  // namespace tc

@@ -1,4 +1,4 @@
-"""Parity of the tensor-core path (K3, K4 split-K FP64 reduction, K5) with the
+"""Parity of the tensor-core path (K3, K4 split-K reduction, K5) with the
 FP64 CPU oracle, per element, normalised by |alpha| sum|A||B| + |beta||C|.
 
 Bounds, from the arithmetic:
@@ -89,10 +89,24 @@ def test_random_contractions(seed, mode):
     assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
+@pytest.mark.parametrize("mode,bn", [("bf16x3", 16), ("bf16x3", 48), ("bf16x3", 128),
+                                     ("bf16x3", 256), ("bf16x6", 32), ("bf16x6", 128)])
+def test_forced_tile_widths(mode, bn, monkeypatch):
+    # every tile width of the runtime-N tensor-core tile, on a ragged contraction
+    monkeypatch.setenv("TC_FORCE_BN", str(bn))
+    g = torch.Generator().manual_seed(40 + bn)
+    A = f32(torch.rand(37, 150, 11, generator=g, dtype=torch.float64) * 2 - 1)   # a p q
+    B = f32(torch.rand(11, 150, 290, generator=g, dtype=torch.float64) * 2 - 1)  # q p b
+    C0 = f32(torch.rand(290, 37, generator=g, dtype=torch.float64) * 2 - 1)      # b a
+    got = run(1.25, A, "apq", B, "qpb", -0.5, C0, "ba", mode)
+    ref, mag = oracle_ref(1.25, A, "apq", B, "qpb", -0.5, C0, "ba")
+    assert norm_err(got, ref, mag) <= TOLS[mode]
+
+
 @pytest.mark.parametrize("mode", MODES)
-def test_split_k_fp64_reduction(mode):
+def test_split_k_reduction(mode):
     # few output tiles and a long contracted range: the contracted range is
-    # split across CTAs and the FP32 partials are reduced in FP64
+    # split across CTAs and the FP32 partials are summed by K4
     g = torch.Generator().manual_seed(4)
     A = f32(torch.randn(256, 8192, generator=g, dtype=torch.float64))
     B = f32(torch.randn(8192, 100, generator=g, dtype=torch.float64))
