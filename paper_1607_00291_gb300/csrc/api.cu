@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_common.h"
 #include "kernels.h"
 
 namespace tc {
@@ -25,13 +26,12 @@ void mainloop_event_after(cudaStream_t s) {
 }  // namespace tc
 
 namespace {
-
-using namespace tc;
-
 __device__ int32_t g_tc_error;  // device error word (kDevTimeout / kDevBounds), 0 = none
-
 std::mutex g_mu;
 int32_t* g_err_ptr[64] = {};
+}  // namespace
+
+namespace tc {
 
 // Address of the device error word on the current device (set up once per device).
 int32_t* err_word() {
@@ -76,12 +76,7 @@ int sm_count() {
 //    k-tiles per split.
 constexpr int64_t kChainTiles = 32;
 
-struct TcChoice {
-  int bn, bn_max, splits;
-  int64_t kps;
-};
-
-TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force = 0, int split_mult = 1) {
+TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force, int split_mult) {
   TcChoice c;
   const int64_t tm = (L.m + 127) / 128;
   auto waves_eff = [&](int bn) {
@@ -216,16 +211,10 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
-}  // namespace
+}  // namespace tc
 
-struct tc_plan {
-  tc_dtype dtype;
-  tc_mode mode;
-  std::vector<tc_problem> probs;
-  std::vector<Planned> planned;
-  std::vector<size_t> ws_off;
-  size_t ws_total;
-};
+using namespace tc;
+
 
 extern "C" {
 
@@ -278,74 +267,6 @@ int tc_contract(tc_dtype dtype, tc_mode mode, double alpha, const tc_tensor* A,
   if ((rc = plan_checked(dtype, A, B, C, &p)) != TC_OK) return rc;
   return run_planned(dtype, mode, alpha, beta, p, workspace, ws_bytes,
                      static_cast<cudaStream_t>(stream));
-}
-
-int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
-                   tc_plan** out) {
-  if (!out || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
-  int rc = check_modes(dtype, mode);
-  if (rc != TC_OK) return rc;
-  tc_plan* pl = new tc_plan;
-  pl->dtype = dtype;
-  pl->mode = mode;
-  pl->ws_total = 0;
-  pl->planned.resize(count);
-  for (int32_t i = 0; i < count; ++i) {
-    rc = plan_checked(dtype, &probs[i].A, &probs[i].B, &probs[i].C, &pl->planned[i]);
-    if (rc != TC_OK) {
-      delete pl;
-      return rc;
-    }
-    pl->ws_off.push_back(pl->ws_total);
-    const Planned& p = pl->planned[i];
-    if (p.L.m != 0 && p.L.n != 0) pl->ws_total += ws_layout(p, mode).total;
-    pl->probs.push_back(probs[i]);
-  }
-  *out = pl;
-  return TC_OK;
-}
-
-int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes) {
-  if (!plan || !bytes) return TC_ERR_ARG;
-  *bytes = plan->ws_total;
-  return TC_OK;
-}
-
-int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
-  if (!plan) return TC_ERR_ARG;
-  if (ws_bytes < plan->ws_total || (plan->ws_total > 0 && !workspace)) return TC_ERR_WORKSPACE;
-  for (size_t i = 0; i < plan->planned.size(); ++i) {
-    const Planned& p = plan->planned[i];
-    if (p.L.m == 0 || p.L.n == 0) continue;
-    int rc = run_planned(plan->dtype, plan->mode, plan->probs[i].alpha, plan->probs[i].beta, p,
-                         static_cast<char*>(workspace) + plan->ws_off[i],
-                         ws_layout(p, plan->mode).total, static_cast<cudaStream_t>(stream));
-    if (rc != TC_OK) return rc;
-  }
-  return TC_OK;
-}
-
-void tc_plan_destroy(tc_plan* plan) { delete plan; }
-
-int tc_batched_workspace_size(tc_dtype dtype, tc_mode mode, int32_t count,
-                              const tc_problem* probs, size_t* bytes) {
-  if (!bytes) return TC_ERR_ARG;
-  tc_plan* pl = nullptr;
-  int rc = tc_plan_create(dtype, mode, count, probs, &pl);
-  if (rc != TC_OK) return rc;
-  *bytes = pl->ws_total;
-  tc_plan_destroy(pl);
-  return TC_OK;
-}
-
-int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
-                        void* workspace, size_t ws_bytes, void* stream) {
-  tc_plan* pl = nullptr;
-  int rc = tc_plan_create(dtype, mode, count, probs, &pl);
-  if (rc != TC_OK) return rc;
-  rc = tc_plan_execute(pl, workspace, ws_bytes, stream);
-  tc_plan_destroy(pl);
-  return rc;
 }
 
 int tc_scatter_count(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,

@@ -1,0 +1,515 @@
+// K6 + K7: batches of contractions in one persistent launch, with a tile and
+// split-K autotuner.
+//
+// A plan validates and lays out every problem (Sections 4 and 7.3), chooses
+// per problem the tile shape and the split of the contracted range (from the
+// autotune table when TC_AUTOTUNE=1, else from the same rules as a single
+// call), builds one work list -- every output tile x k-split of every
+// problem, sorted by decreasing cost so that a static round-robin over the
+// persistent CTAs stays balanced -- and copies the problem descriptors, the
+// work list and the scatter-vector layouts into one device buffer it owns.
+// tc_plan_execute then only launches kernels: the batched scatter builder
+// (K1 for every problem), the persistent mainloop (FP64: DMMA tiles; FP32:
+// tcgen05 tiles) and, for problems split along k, the reduction -- no host
+// synchronisation and no allocation, so it can be captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host_common.h"
+#include "kernels.h"
+
+using namespace tc;
+
+namespace {
+
+struct ProbCfg {
+  int bn = 0;        // tensor-core tile width (FP64: fixed tile)
+  int splits = 1;
+  int64_t kps = 0;   // k per split
+  int64_t tiles = 0;
+};
+
+// ---- K7: autotuner ------------------------------------------------------------------------
+// Shape class: mode, pieces, rounded log2 of m, n, k, and the two access
+// flags.  Candidates (tensor-core path): tile widths around n and split
+// multipliers 1 and 2; each is timed on the first problem of its class in the
+// batch, writing into a scratch copy of that problem's output (the caller's C
+// is never touched), and the fastest is kept for the rest of the process (and
+// in the file named by TC_AUTOTUNE_CACHE, when set).
+struct TuneKey {
+  int mode, lm, ln, lk, akc, bkc;
+  bool operator<(const TuneKey& o) const {
+    return std::memcmp(this, &o, sizeof o) < 0;
+  }
+};
+struct TuneVal {
+  int bn, split_mult;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+bool g_tune_loaded = false;
+
+int ilog2r(int64_t x) { return x <= 1 ? 0 : (int)std::lround(std::log2((double)x)); }
+
+TuneKey tune_key(tc_mode mode, const Planned& p) {
+  TuneKey k;
+  std::memset(&k, 0, sizeof k);
+  k.mode = (int)mode;
+  k.lm = ilog2r(p.L.m);
+  k.ln = ilog2r(p.L.n);
+  k.lk = ilog2r(p.L.k);
+  k.akc = p.info.a_k_contig;
+  k.bkc = p.info.b_k_contig;
+  return k;
+}
+
+void tune_load_file() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("TC_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneVal v;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.mode, &k.lm, &k.ln, &k.lk, &k.akc, &k.bkc,
+                     &v.bn, &v.split_mult) == 8) {
+    if (v.bn >= 16 && v.bn <= 256 && v.bn % 16 == 0 && v.split_mult >= 1 && v.split_mult <= 8)
+      g_tune[k] = v;  // a corrupt line is skipped; a malformed file stops the read
+  }
+  std::fclose(f);
+}
+
+void tune_save_file() {
+  const char* path = std::getenv("TC_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune)
+    std::fprintf(f, "%d %d %d %d %d %d %d %d\n", kv.first.mode, kv.first.lm, kv.first.ln,
+                 kv.first.lk, kv.first.akc, kv.first.bkc, kv.second.bn, kv.second.split_mult);
+  std::fclose(f);
+}
+
+bool autotune_enabled() {
+  const char* e = std::getenv("TC_AUTOTUNE");
+  return e && e[0] == '1';
+}
+
+// Time one tensor-core configuration of problem p on scratch buffers.
+float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, int bn, int sm,
+                     int64_t* scat, float* partial, void* cscratch, int64_t c_off, cudaStream_t st) {
+  const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+  const TcChoice c = choose_tc(p.L, pieces, sm_count(), bn, sm);
+  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
+  TcLaunch q;
+  std::memset(&q, 0, sizeof q);
+  DevProblem& d = q.single;
+  d.a = p.a;
+  d.b = p.b;
+  d.c = static_cast<float*>(cscratch) + c_off;
+  d.partial = c.splits > 1 ? partial : nullptr;
+  d.sp = scatter_ptrs(scat, o);
+  d.m = p.L.m;
+  d.n = p.L.n;
+  d.k = p.L.k;
+  d.alpha = alpha;
+  d.beta = beta;
+  d.a_kc = p.info.a_k_contig;
+  d.b_kc = p.info.b_k_contig;
+  d.bn = c.bn;
+  d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
+  d.splits = c.splits;
+  d.kps = c.kps;
+  q.pieces = pieces;
+  q.bn_max = c.bn_max;
+  q.ctas = sm_count();
+  q.err = err_word();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int r = 0; r < 4; ++r) {
+    cudaEventRecord(e0, st);
+    if (launch_tc(q, st) != cudaSuccess) {
+      best = 1e30f;
+      break;
+    }
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best = std::min(best, ms);  // first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+TuneVal tune_tc(const Planned& p, tc_mode mode, double alpha, double beta) {
+  const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+  std::vector<int> bns;
+  if (p.L.n < 128) {
+    const int b0 = (int)std::max<int64_t>(16, (p.L.n + 15) / 16 * 16);
+    bns.push_back(b0);
+    if (b0 > 32) bns.push_back((b0 / 2 + 15) / 16 * 16);
+  } else {
+    bns.push_back(128);
+    if (pieces == 2) bns.push_back(256);
+    bns.push_back(64);
+  }
+  // scratch: scatter vectors, partials for the largest split, a copy of C's span
+  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
+  int64_t max_split = 1;
+  for (int bn : bns)
+    for (int sm = 1; sm <= 2; ++sm)
+      max_split = std::max<int64_t>(max_split, choose_tc(p.L, pieces, sm_count(), bn, sm).splits);
+  int64_t cmin = 0, cmax = 0;
+  for (int i = 0; i < p.info.nI; ++i) {
+    const int64_t e = (p.info.I_len[i] - 1) * p.info.I_sC[i];
+    if (e < 0) cmin += e; else cmax += e;
+  }
+  for (int j = 0; j < p.info.nJ; ++j) {
+    const int64_t e = (p.info.J_len[j] - 1) * p.info.J_sC[j];
+    if (e < 0) cmin += e; else cmax += e;
+  }
+  const size_t cbytes = (size_t)(cmax - cmin + 1) * sizeof(float);
+  int64_t* scat = nullptr;
+  float* partial = nullptr;
+  void* cs = nullptr;
+  TuneVal best{bns[0], 1};
+  cudaStream_t st = nullptr;
+  if (cudaMalloc(&scat, (size_t)o.total * 8) != cudaSuccess ||
+      cudaMalloc(&partial, (size_t)max_split * p.L.m * p.L.n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&cs, cbytes) != cudaSuccess || cudaMemset(cs, 0, cbytes) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+  } else if (launch_build_scatter(p.L, kBsBlock, scat, st) == cudaSuccess) {
+    float tbest = 1e30f;
+    for (int bn : bns)
+      for (int sm = 1; sm <= 2; ++sm) {
+        const float t = time_tc_config(p, mode, alpha, beta, bn, sm, scat, partial, cs, -cmin, st);
+        if (t < tbest) {
+          tbest = t;
+          best = TuneVal{bn, sm};
+        }
+      }
+  }
+  if (st) cudaStreamDestroy(st);
+  cudaFree(scat);
+  cudaFree(partial);
+  cudaFree(cs);
+  cudaGetLastError();
+  return best;
+}
+
+}  // namespace
+
+// ---- the plan ----------------------------------------------------------------------------------
+struct tc_plan {
+  tc_dtype dtype;
+  tc_mode mode;
+  int device;
+  std::vector<Planned> planned;   // active problems only
+  std::vector<ProbCfg> cfg;
+  void* dmem = nullptr;
+  Layout* d_layouts = nullptr;
+  int64_t* d_offs = nullptr;
+  int64_t* d_scat = nullptr;
+  DevProblem* d_probs = nullptr;
+  WorkItem* d_items = nullptr;
+  int32_t* d_split = nullptr;
+  int64_t total_scatter = 0, nitems = 0;
+  int32_t n_split = 0;
+  int64_t max_m_split = 0, max_n_split = 0;
+  int pieces = 2, bn_max = 128;
+  int64_t ctas = 152;
+};
+
+namespace {
+
+int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
+  const int sms = sm_count();
+  pl->ctas = sms;
+  const bool f64 = pl->mode == TC_MODE_F64;
+  pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
+  std::vector<double> alpha, beta;
+  for (const tc_problem& pr : probs) {
+    Planned p;
+    int rc = plan_checked(pl->dtype, &pr.A, &pr.B, &pr.C, &p);
+    if (rc != TC_OK) return rc;
+    if (p.L.m == 0 || p.L.n == 0) continue;  // empty output: nothing to do
+    if (pr.alpha == 0.0) p.L.k = 0;          // C := beta * C, A and B not read
+    pl->planned.push_back(p);
+    alpha.push_back(pr.alpha);
+    beta.push_back(pr.beta);
+  }
+  const int np = (int)pl->planned.size();
+  pl->cfg.resize(np);
+
+  // per-problem tiles and k-splits
+  const int tm_f = f64_tile_m(), tn_f = f64_tile_n(), tk_f = f64_tile_k();
+  double total_cost = 0;
+  std::vector<double> cost(np);
+  for (int i = 0; i < np; ++i) {
+    const Layout& L = pl->planned[i].L;
+    ProbCfg& c = pl->cfg[i];
+    if (f64) {
+      c.bn = tn_f;
+      c.tiles = ((L.m + tm_f - 1) / tm_f) * ((L.n + tn_f - 1) / tn_f);
+      cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + tk_f - 1) / tk_f);
+    } else {
+      TuneVal tv{0, 1};
+      if (autotune_enabled() && L.k > 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_file();
+        const TuneKey key = tune_key(pl->mode, pl->planned[i]);
+        auto it = g_tune.find(key);
+        if (it == g_tune.end()) {
+          tv = tune_tc(pl->planned[i], pl->mode, alpha[i], beta[i]);
+          g_tune[key] = tv;
+          tune_save_file();
+        } else {
+          tv = it->second;
+        }
+      }
+      const TcChoice ch = L.k > 0 ? choose_tc(L, pl->pieces, sms, tv.bn, tv.split_mult)
+                                  : TcChoice{std::max(16, (int)std::min<int64_t>(128, (L.n + 15) / 16 * 16)),
+                                             128, 1, 32};
+      c.bn = ch.bn;
+      c.splits = ch.splits;
+      c.kps = ch.kps;
+      c.tiles = ((L.m + 127) / 128) * ((L.n + c.bn - 1) / c.bn);
+      pl->bn_max = std::max(pl->bn_max, tc_bn_max_for(pl->pieces, c.bn));
+      cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + 31) / 32) * c.bn / 128.0;
+    }
+    total_cost += cost[i];
+  }
+  // FP64: split long-k problems so that no item exceeds a quarter of a CTA's
+  // fair share (k-tiles of 16); the tensor-core split already caps chains.
+  if (f64) {
+    const double fair = total_cost / (double)sms;
+    for (int i = 0; i < np; ++i) {
+      const Layout& L = pl->planned[i].L;
+      ProbCfg& c = pl->cfg[i];
+      const int64_t KT = (L.k + tk_f - 1) / tk_f;
+      int64_t s = 1;
+      if (KT > 0 && fair > 0) {
+        const double item = cost[i] / (double)c.tiles;  // k-tiles per tile
+        s = (int64_t)std::ceil(item / std::max(1.0, fair / 4.0));
+        s = std::max<int64_t>(1, std::min<int64_t>(s, KT));
+      }
+      const int64_t ktps = KT > 0 ? (KT + s - 1) / s : 0;
+      c.kps = std::max<int64_t>(1, ktps) * tk_f;
+      c.splits = KT > 0 ? (int)((KT + ktps - 1) / ktps) : 1;
+    }
+  }
+
+  // device buffer: layouts | offsets | scatter | problems | items | split list | partials
+  std::vector<int64_t> offs(np + 1, 0);
+  for (int i = 0; i < np; ++i) offs[i + 1] = offs[i] + scatter_offsets(pl->planned[i].L, kBsBlock).total;
+  pl->total_scatter = offs[np];
+  std::vector<WorkItem> items;
+  std::vector<int32_t> splitp;
+  std::vector<int64_t> part_off(np, -1);
+  int64_t part_elems = 0;
+  for (int i = 0; i < np; ++i) {
+    const ProbCfg& c = pl->cfg[i];
+    for (int s = 0; s < c.splits; ++s)
+      for (int64_t t = 0; t < c.tiles; ++t) items.push_back(WorkItem{i, (int32_t)t, s, 0});
+    if (c.splits > 1) {
+      splitp.push_back(i);
+      part_off[i] = part_elems;
+      part_elems += (int64_t)c.splits * pl->planned[i].L.m * pl->planned[i].L.n;
+      pl->max_m_split = std::max(pl->max_m_split, pl->planned[i].L.m);
+      pl->max_n_split = std::max(pl->max_n_split, pl->planned[i].L.n);
+    }
+  }
+  // longest items first (k-tiles of the item), stable for locality
+  auto item_cost = [&](const WorkItem& w) {
+    const ProbCfg& c = pl->cfg[w.prob];
+    const Layout& L = pl->planned[w.prob].L;
+    const int64_t kb = (int64_t)w.split * c.kps, ke = std::min<int64_t>(L.k, kb + c.kps);
+    return (double)std::max<int64_t>(0, ke - kb) * (f64 ? 1.0 : c.bn / 128.0);
+  };
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const WorkItem& x, const WorkItem& y) { return item_cost(x) > item_cost(y); });
+  pl->nitems = (int64_t)items.size();
+  pl->n_split = (int32_t)splitp.size();
+
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_lay = take(sizeof(Layout) * std::max(np, 1));
+  const size_t o_offs = take(sizeof(int64_t) * (np + 1));
+  const size_t o_scat = take(sizeof(int64_t) * std::max<int64_t>(1, pl->total_scatter));
+  const size_t o_prob = take(sizeof(DevProblem) * std::max(np, 1));
+  const size_t o_item = take(sizeof(WorkItem) * std::max<int64_t>(1, pl->nitems));
+  const size_t o_split = take(sizeof(int32_t) * std::max<int32_t>(1, pl->n_split));
+  const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
+  if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
+    cudaGetLastError();
+    pl->dmem = nullptr;
+    return TC_ERR_CUDA;
+  }
+  char* base = static_cast<char*>(pl->dmem);
+  pl->d_layouts = reinterpret_cast<Layout*>(base + o_lay);
+  pl->d_offs = reinterpret_cast<int64_t*>(base + o_offs);
+  pl->d_scat = reinterpret_cast<int64_t*>(base + o_scat);
+  pl->d_probs = reinterpret_cast<DevProblem*>(base + o_prob);
+  pl->d_items = reinterpret_cast<WorkItem*>(base + o_item);
+  pl->d_split = reinterpret_cast<int32_t*>(base + o_split);
+  char* partial = base + o_part;
+
+  std::vector<Layout> lay(np);
+  std::vector<DevProblem> dp(np);
+  for (int i = 0; i < np; ++i) {
+    const Planned& p = pl->planned[i];
+    const ProbCfg& c = pl->cfg[i];
+    lay[i] = p.L;
+    DevProblem& d = dp[i];
+    std::memset(&d, 0, sizeof d);
+    d.a = p.a;
+    d.b = p.b;
+    d.c = p.c;
+    d.partial = part_off[i] >= 0 ? partial + part_off[i] * es : nullptr;
+    d.sp = scatter_ptrs(pl->d_scat + offs[i], scatter_offsets(p.L, kBsBlock));
+    d.m = p.L.m;
+    d.n = p.L.n;
+    d.k = p.L.k;
+    d.alpha = alpha[i];
+    d.beta = beta[i];
+    d.a_kc = p.info.a_k_contig;
+    d.b_kc = p.info.b_k_contig;
+    d.bn = c.bn;
+    d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
+    d.splits = c.splits;
+    d.kps = c.kps;
+  }
+  auto up = [](void* dst, const void* src, size_t bytes) {
+    return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up(pl->d_layouts, lay.data(), sizeof(Layout) * np) ||
+      !up(pl->d_offs, offs.data(), sizeof(int64_t) * (np + 1)) ||
+      !up(pl->d_probs, dp.data(), sizeof(DevProblem) * np) ||
+      !up(pl->d_items, items.data(), sizeof(WorkItem) * items.size()) ||
+      !up(pl->d_split, splitp.data(), sizeof(int32_t) * splitp.size()))
+    return TC_ERR_CUDA;
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                   tc_plan** out) {
+  if (!out || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  tc_plan* pl = new tc_plan;
+  pl->dtype = dtype;
+  pl->mode = mode;
+  cudaGetDevice(&pl->device);
+  rc = build_plan(pl, std::vector<tc_problem>(probs, probs + count));
+  if (rc != TC_OK) {
+    tc_plan_destroy(pl);
+    return rc;
+  }
+  *out = pl;
+  return TC_OK;
+}
+
+int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return TC_ERR_ARG;
+  *bytes = 0;  // the plan owns its scatter vectors and partials
+  return TC_OK;
+}
+
+int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+  (void)workspace;
+  (void)ws_bytes;
+  if (!plan) return TC_ERR_ARG;
+  const int np = (int)plan->planned.size();
+  if (np == 0) return TC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (launch_build_scatter_batched(plan->d_layouts, plan->d_offs, np, plan->total_scatter,
+                                   kBsBlock, plan->d_scat, s) != cudaSuccess)
+    return TC_ERR_CUDA;
+  cudaError_t e;
+  if (plan->mode == TC_MODE_F64) {
+    F64BatchLaunch q;
+    q.dtype = plan->dtype;
+    q.probs = plan->d_probs;
+    q.items = plan->d_items;
+    q.nitems = plan->nitems;
+    q.ctas = plan->ctas;
+    q.split_probs = plan->d_split;
+    q.n_split_probs = plan->n_split;
+    q.max_m_split = plan->max_m_split;
+    q.max_n_split = plan->max_n_split;
+    e = launch_f64_batched(q, s);
+  } else {
+    TcLaunch q;
+    std::memset(&q, 0, sizeof q);
+    q.probs = plan->d_probs;
+    q.items = plan->d_items;
+    q.nitems = plan->nitems;
+    q.nprobs = np;
+    q.pieces = plan->pieces;
+    q.bn_max = plan->bn_max;
+    q.ctas = plan->ctas;
+    q.split_probs = plan->d_split;
+    q.n_split_probs = plan->n_split;
+    q.max_m_split = plan->max_m_split;
+    q.max_n_split = plan->max_n_split;
+    q.err = err_word();
+    e = launch_tc(q, s);
+  }
+  return e == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+void tc_plan_destroy(tc_plan* plan) {
+  if (!plan) return;
+  if (plan->dmem) cudaFree(plan->dmem);
+  delete plan;
+}
+
+int tc_batched_workspace_size(tc_dtype dtype, tc_mode mode, int32_t count,
+                              const tc_problem* probs, size_t* bytes) {
+  if (!bytes || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  for (int32_t i = 0; i < count; ++i) {
+    Planned p;
+    if ((rc = plan_checked(dtype, &probs[i].A, &probs[i].B, &probs[i].C, &p)) != TC_OK) return rc;
+  }
+  *bytes = 0;
+  return TC_OK;
+}
+
+int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
+                        void* workspace, size_t ws_bytes, void* stream) {
+  tc_plan* pl = nullptr;
+  int rc = tc_plan_create(dtype, mode, count, probs, &pl);
+  if (rc != TC_OK) return rc;
+  rc = tc_plan_execute(pl, workspace, ws_bytes, stream);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && rc == TC_OK)
+    rc = TC_ERR_CUDA;
+  tc_plan_destroy(pl);
+  return rc;
+}
+
+}  // extern "C"

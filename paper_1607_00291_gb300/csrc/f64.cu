@@ -55,144 +55,228 @@ __host__ __device__ __forceinline__ int64_t sk_start(int64_t c, int64_t T, int64
 }
 
 template <typename T>
+struct F64Ctx {
+  const T* a;
+  const T* b;
+  T* c;
+  ScatterPtrs sp;
+  int64_t M, N, K;
+  double alpha, beta;
+  int a_kc, b_kc;
+};
+
+struct F64Smem {
+  double* As;   // [2][BK][LDA]
+  double* Bs;   // [2][BK][LDB]
+  int64_t *sRA, *sRC, *sCB, *sCC;
+};
+
+__device__ __forceinline__ F64Smem f64_smem(unsigned char* smem) {
+  F64Smem S;
+  S.As = reinterpret_cast<double*>(smem);
+  S.Bs = S.As + 2 * BK * LDA;
+  S.sRA = reinterpret_cast<int64_t*>(S.Bs + 2 * BK * LDB);
+  S.sRC = S.sRA + BM;
+  S.sCB = S.sRC + BM;
+  S.sCC = S.sCB + BN;
+  return S;
+}
+
+// One BM x BN output tile at (m0, n0) over k-tiles [kb, ke) (possibly empty).
+// direct: apply the epilogue to C.  Otherwise store the raw FP64 sums at
+// part[nn * ldp + mm] for the tile-local (mm, nn) -- only inside the operand
+// when `bounded`.  All threads of the CTA call it together.
+template <typename T>
+__device__ __forceinline__ void f64_tile(const F64Ctx<T>& P, const F64Smem& S, int64_t m0,
+                                         int64_t n0, int64_t kb, int64_t ke, bool direct,
+                                         double* part, int64_t ldp, bool bounded) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tig = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int64_t M = P.M, N = P.N, K = P.K;
+
+  // element e of a panel -> (row, k) with consecutive threads along the
+  // operand's unit-stride index
+  auto a_coord = [&](int e, int& mm, int& kk) {
+    if (P.a_kc) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+  };
+  auto b_coord = [&](int e, int& nn, int& kk) {
+    if (P.b_kc) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+  };
+
+  __syncthreads();  // the previous tile's epilogue is done with the row tables
+  for (int i = tid; i < BM; i += NT) {
+    const int64_t gm = m0 + i;
+    S.sRA[i] = gm < M ? P.sp.rA[gm] : 0;
+    S.sRC[i] = gm < M ? P.sp.rC[gm] : 0;
+  }
+  for (int i = tid; i < BN; i += NT) {
+    const int64_t gn = n0 + i;
+    S.sCB[i] = gn < N ? P.sp.cB[gn] : 0;
+    S.sCC[i] = gn < N ? P.sp.cC[gn] : 0;
+  }
+  __syncthreads();
+
+  double acc[4][4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+  double ra[A_PER_T], rb[B_PER_T];
+  auto load = [&](int64_t kt) {
+    const int64_t k0 = kt * BK;
+#pragma unroll
+    for (int i = 0; i < A_PER_T; ++i) {
+      int mm, kk;
+      a_coord(tid + i * NT, mm, kk);
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      ra[i] = (gm < M && gk < K) ? (double)P.a[S.sRA[mm] + P.sp.cA[gk]] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER_T; ++i) {
+      int nn, kk;
+      b_coord(tid + i * NT, nn, kk);
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      rb[i] = (gn < N && gk < K) ? (double)P.b[P.sp.rB[gk] + S.sCB[nn]] : 0.0;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < A_PER_T; ++i) {
+      int mm, kk;
+      a_coord(tid + i * NT, mm, kk);
+      S.As[(buf * BK + kk) * LDA + mm] = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < B_PER_T; ++i) {
+      int nn, kk;
+      b_coord(tid + i * NT, nn, kk);
+      S.Bs[(buf * BK + kk) * LDB + nn] = rb[i];
+    }
+  };
+
+  if (kb < ke) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t kt = kb; kt < ke; ++kt) {
+    const int buf = (int)((kt - kb) & 1);
+    if (kt + 1 < ke) load(kt + 1);
+    const double* Ab = S.As + buf * BK * LDA + wm * 32 + g;
+    const double* Bb = S.Bs + buf * BK * LDB + wn * 32 + g;
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) af[i] = Ab[(kk + tig) * LDA + i * 8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bf[j] = Bb[(kk + tig) * LDB + j * 8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+    }
+    if (kt + 1 < ke) store(buf ^ 1);
+    __syncthreads();
+  }
+
+  if (direct) {
+    // K5: scattered epilogue, C[rscat + cscat] = alpha * acc + beta * C
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
+          if (m0 + mm < M && n0 + nn < N) {
+            T* p = P.c + S.sRC[mm] + S.sCC[nn];
+            double v = P.alpha * acc[i][j][q];
+            if (P.beta != 0.0) v += P.beta * (double)*p;
+            *p = (T)v;
+          }
+        }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
+          if (!bounded || (m0 + mm < M && n0 + nn < N)) part[nn * ldp + mm] = acc[i][j][q];
+        }
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(NT, 1)
     k_f64(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ c, const ScatterPtrs sp,
           const int64_t M, const int64_t N, const int64_t K, const double alpha, const double beta,
           const int a_kc, const int b_kc, const SkArgs sk) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* As = reinterpret_cast<double*>(smem);  // [2][BK][LDA]
-  double* Bs = As + 2 * BK * LDA;                // [2][BK][LDB]
-  int64_t* sRA = reinterpret_cast<int64_t*>(Bs + 2 * BK * LDB);
-  int64_t* sRC = sRA + BM;
-  int64_t* sCB = sRC + BM;
-  int64_t* sCC = sCB + BN;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, tig = lane & 3;
-  const int wm = warp >> 1, wn = warp & 1;
+  const F64Smem S = f64_smem(smem);
+  F64Ctx<T> P{a, b, c, sp, M, N, K, alpha, beta, a_kc, b_kc};
   const int64_t Tt = sk.tiles * sk.KT;
   const int64_t start = sk_start(blockIdx.x, Tt, sk.G), end = sk_start(blockIdx.x + 1, Tt, sk.G);
-
-  // element e of a panel -> (row, k) with consecutive threads along the
-  // operand's unit-stride index
-  auto a_coord = [&](int e, int& mm, int& kk) {
-    if (a_kc) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
-  };
-  auto b_coord = [&](int e, int& nn, int& kk) {
-    if (b_kc) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
-  };
-
   for (int64_t it = start; it < end;) {
     const int64_t tile = it / sk.KT;
     const int64_t kb = it - tile * sk.KT;
     const int64_t ke = (end - tile * sk.KT) < sk.KT ? (end - tile * sk.KT) : sk.KT;
     const int64_t m0 = (tile / sk.tiles_n) * BM, n0 = (tile % sk.tiles_n) * BN;
-
-    __syncthreads();  // the previous tile's epilogue is done with sRC/sCC
-    for (int i = tid; i < BM; i += NT) {
-      const int64_t gm = m0 + i;
-      sRA[i] = gm < M ? sp.rA[gm] : 0;
-      sRC[i] = gm < M ? sp.rC[gm] : 0;
-    }
-    for (int i = tid; i < BN; i += NT) {
-      const int64_t gn = n0 + i;
-      sCB[i] = gn < N ? sp.cB[gn] : 0;
-      sCC[i] = gn < N ? sp.cC[gn] : 0;
-    }
-    __syncthreads();
-
-    double acc[4][4][2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-
-    double ra[A_PER_T], rb[B_PER_T];
-    auto load = [&](int64_t kt) {
-      const int64_t k0 = kt * BK;
-#pragma unroll
-      for (int i = 0; i < A_PER_T; ++i) {
-        int mm, kk;
-        a_coord(tid + i * NT, mm, kk);
-        const int64_t gm = m0 + mm, gk = k0 + kk;
-        ra[i] = (gm < M && gk < K) ? (double)a[sRA[mm] + sp.cA[gk]] : 0.0;
-      }
-#pragma unroll
-      for (int i = 0; i < B_PER_T; ++i) {
-        int nn, kk;
-        b_coord(tid + i * NT, nn, kk);
-        const int64_t gn = n0 + nn, gk = k0 + kk;
-        rb[i] = (gn < N && gk < K) ? (double)b[sp.rB[gk] + sCB[nn]] : 0.0;
-      }
-    };
-    auto store = [&](int buf) {
-#pragma unroll
-      for (int i = 0; i < A_PER_T; ++i) {
-        int mm, kk;
-        a_coord(tid + i * NT, mm, kk);
-        As[(buf * BK + kk) * LDA + mm] = ra[i];
-      }
-#pragma unroll
-      for (int i = 0; i < B_PER_T; ++i) {
-        int nn, kk;
-        b_coord(tid + i * NT, nn, kk);
-        Bs[(buf * BK + kk) * LDB + nn] = rb[i];
-      }
-    };
-
-    load(kb);
-    store(0);
-    __syncthreads();
-    for (int64_t kt = kb; kt < ke; ++kt) {
-      const int buf = (int)((kt - kb) & 1);
-      if (kt + 1 < ke) load(kt + 1);
-      const double* Ab = As + buf * BK * LDA + wm * 32 + g;
-      const double* Bb = Bs + buf * BK * LDB + wn * 32 + g;
-#pragma unroll
-      for (int kk = 0; kk < BK; kk += 4) {
-        double af[4], bf[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) af[i] = Ab[(kk + tig) * LDA + i * 8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bf[j] = Bb[(kk + tig) * LDB + j * 8];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
-      }
-      if (kt + 1 < ke) store(buf ^ 1);
-      __syncthreads();
-    }
-
-    if (kb == 0 && ke == sk.KT) {
-      // K5: scattered epilogue, C[rscat + cscat] = alpha * acc + beta * C
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
-            if (m0 + mm < M && n0 + nn < N) {
-              T* p = c + sRC[mm] + sCC[nn];
-              double v = alpha * acc[i][j][q];
-              if (beta != 0.0) v += beta * (double)*p;
-              *p = (T)v;
-            }
-          }
-    } else {
-      double* slot = sk.partial + ((int64_t)blockIdx.x * 2 + (it == start ? 0 : 1)) * (BM * BN);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int mm = wm * 32 + i * 8 + g, nn = wn * 32 + j * 8 + 2 * tig + q;
-            slot[nn * BM + mm] = acc[i][j][q];
-          }
-    }
+    const bool whole = kb == 0 && ke == sk.KT;
+    double* slot = sk.partial + ((int64_t)blockIdx.x * 2 + (it == start ? 0 : 1)) * (BM * BN);
+    f64_tile<T>(P, S, m0, n0, kb, ke, whole, slot, BM, false);
     it = tile * sk.KT + ke;
+  }
+}
+
+// Batched FP64 contractions: a persistent grid walks the work list (output
+// tile x k-split of every problem, sorted by decreasing cost).  Unsplit tiles
+// finish in place; split ones leave FP64 partials in [split][n][m] for
+// k_f64_batched_reduce.
+template <typename T>
+__global__ void __launch_bounds__(NT, 1)
+    k_f64_batched(const DevProblem* __restrict__ probs, const WorkItem* __restrict__ items,
+                  int64_t nitems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const F64Smem S = f64_smem(smem);
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const WorkItem wi = items[w];
+    const DevProblem& d = probs[wi.prob];
+    F64Ctx<T> P{static_cast<const T*>(d.a), static_cast<const T*>(d.b), static_cast<T*>(d.c),
+                d.sp, d.m, d.n, d.k, d.alpha, d.beta, d.a_kc, d.b_kc};
+    const int64_t m0 = (int64_t)(wi.tile / d.tiles_n) * BM, n0 = (int64_t)(wi.tile % d.tiles_n) * BN;
+    const int64_t KT = (d.k + BK - 1) / BK, kpt = d.kps / BK;
+    const int64_t kb = (int64_t)wi.split * kpt;
+    const int64_t ke = kb + kpt < KT ? kb + kpt : KT;
+    double* part = d.splits > 1 ? static_cast<double*>(d.partial) +
+                                      (int64_t)wi.split * d.m * d.n + n0 * d.m + m0
+                                : nullptr;
+    f64_tile<T>(P, S, m0, n0, kb, ke, d.splits == 1, part, d.m, true);
+  }
+}
+
+template <typename T>
+__global__ void k_f64_batched_reduce(const DevProblem* __restrict__ probs,
+                                     const int32_t* __restrict__ split_probs) {
+  const DevProblem& d = probs[split_probs[blockIdx.z]];
+  const int64_t M = d.m, N = d.n, plane = M * N;
+  const double* part = static_cast<const double*>(d.partial);
+  T* c = static_cast<T*>(d.c);
+  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
+    const int64_t cn = d.sp.cC[n];
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+      double s = 0.0;
+      for (int ks = 0; ks < d.splits; ++ks) s += part[ks * plane + n * M + m];
+      T* p = c + d.sp.rC[m] + cn;
+      double v = d.alpha * s;
+      if (d.beta != 0.0) v += d.beta * (double)*p;
+      *p = (T)v;
+    }
   }
 }
 
@@ -262,7 +346,43 @@ cudaError_t launch_t(const F64Launch& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_f64_batched<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  if (q.nitems > 0) {
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, q.nitems));
+    mainloop_event_before(s);
+    k_f64_batched<T><<<(unsigned)grid, NT, kSmem, s>>>(q.probs, q.items, q.nitems);
+    note_launch();
+    if (q.n_split_probs > 0) {
+      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 64));
+      const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q.max_n_split, 32768));
+      k_f64_batched_reduce<T><<<dim3(bx, by, (unsigned)q.n_split_probs), 256, 0, s>>>(q.probs,
+                                                                                     q.split_probs);
+      note_launch();
+    }
+    mainloop_event_after(s);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s) {
+  return q.dtype == TC_F64 ? launch_batched_t<double>(q, s) : launch_batched_t<float>(q, s);
+}
+
+int f64_tile_m() { return BM; }
+int f64_tile_n() { return BN; }
+int f64_tile_k() { return BK; }
 
 // CTAs for the FP64 mainloop: plain tiling (one CTA per tile) when the tiles
 // fill whole waves of `max_ctas` (or no partial workspace is available),

@@ -1,0 +1,29 @@
+// Host helpers shared by the single-contraction (api.cu) and batch (batch.cu)
+// entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+// Device error word of the current device (looked up once per device).
+int32_t* err_word();
+size_t elem_size(tc_dtype dt);
+// Valid dtype/mode combination?  TC_OK or an error code.
+int check_modes(tc_dtype dt, tc_mode mode);
+// SMs of the current device (152 when no device can be queried).
+int sm_count();
+// plan_problem + the C-aliases-A/B check.
+int plan_checked(tc_dtype dt, const tc_tensor* A, const tc_tensor* B, const tc_tensor* C,
+                 Planned* p);
+
+// Tile width, shared-memory plan and k-split of the tensor-core mainloop.
+struct TcChoice {
+  int bn, bn_max, splits;
+  int64_t kps;
+};
+TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force = 0, int split_mult = 1);
+
+}  // namespace tc

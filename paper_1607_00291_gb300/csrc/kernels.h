@@ -44,6 +44,9 @@ struct F64Launch {
 cudaError_t launch_f64(const F64Launch& p, cudaStream_t s);
 int64_t f64_grid(int64_t m, int64_t n, int64_t k, int64_t max_ctas, bool can_split);
 size_t f64_partial_bytes(int64_t max_ctas);
+int f64_tile_m();
+int f64_tile_n();
+int f64_tile_k();
 
 // One planned contraction as the persistent kernels see it: a kernel
 // parameter for a single call, an array in device memory for a batch.
@@ -86,6 +89,26 @@ struct TcLaunch {
   int32_t* err;
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
+
+// K6 on the FP64 path (f64.cu): persistent batched mainloop + FP64 reduction
+// of split problems.
+struct F64BatchLaunch {
+  tc_dtype dtype;
+  const DevProblem* probs;
+  const WorkItem* items;
+  int64_t nitems;
+  int64_t ctas;
+  const int32_t* split_probs;
+  int32_t n_split_probs;
+  int64_t max_m_split, max_n_split;
+};
+cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s);
+
+// K1 for a batch (scatter.cu): every problem's vectors in one launch.
+// layouts[count], offsets[count + 1] (prefix sums of scatter_offsets().total).
+cudaError_t launch_build_scatter_batched(const Layout* layouts, const int64_t* offsets,
+                                         int32_t count, int64_t total, int32_t b, int64_t* out,
+                                         cudaStream_t s);
 int tc_bn_max_for(int pieces, int bn);
 
 }  // namespace tc

@@ -255,25 +255,6 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
   return TC_OK;
 }
 
-ScatterOffsets scatter_offsets(const Layout& L, int32_t b) {
-  ScatterOffsets o;
-  auto nb = [b](int64_t l) { return (l + b - 1) / b; };
-  int64_t p = 0;
-  o.rA = p; p += L.m;
-  o.cA = p; p += L.k;
-  o.rB = p; p += L.k;
-  o.cB = p; p += L.n;
-  o.rC = p; p += L.m;
-  o.cC = p; p += L.n;
-  o.rbsA = p; p += nb(L.m);
-  o.cbsA = p; p += nb(L.k);
-  o.rbsB = p; p += nb(L.k);
-  o.cbsB = p; p += nb(L.n);
-  o.rbsC = p; p += nb(L.m);
-  o.cbsC = p; p += nb(L.n);
-  o.total = p;
-  return o;
-}
 
 // Exposed for the API layer.
 int aliases(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, size_t es) {

@@ -46,39 +46,55 @@ __device__ __forceinline__ Section section(const Layout& L, int which) {
   }
 }
 
-__global__ void k_build_scatter(const Layout L, const int32_t b, const ScatterOffsets o,
-                                int64_t* __restrict__ out) {
+// Entry t of the concatenated vectors of one problem (layout of tc.h).
+__device__ __forceinline__ int64_t scatter_entry(const Layout& L, const ScatterOffsets& o,
+                                                 int32_t b, int64_t t) {
   const int64_t starts[12] = {o.rA, o.cA, o.rB, o.cB, o.rC, o.cC,
                               o.rbsA, o.cbsA, o.rbsB, o.cbsB, o.rbsC, o.cbsC};
+  int sec = 0;
+  while (sec < 11 && t >= starts[sec + 1]) ++sec;
+  const int64_t x = t - starts[sec];
+  if (sec < 6) {
+    Section S = section(L, sec);
+    return scat_at(S.len, S.s, S.nd, x);
+  }
+  Section S = section(L, sec - 6);
+  const int64_t lo = x * b;
+  const int64_t hi = lo + b < S.l ? lo + b : S.l;
+  if (hi - lo <= 1) return 1;
+  int64_t prev = scat_at(S.len, S.s, S.nd, lo);
+  int64_t cur = scat_at(S.len, S.s, S.nd, lo + 1);
+  const int64_t st = cur - prev;
+  bool ok = st > 0;
+  for (int64_t j = lo + 2; j < hi && ok; ++j) {
+    prev = cur;
+    cur = scat_at(S.len, S.s, S.nd, j);
+    ok = (cur - prev) == st;
+  }
+  return ok ? st : 0;
+}
+
+__global__ void k_build_scatter(const Layout L, const int32_t b, const ScatterOffsets o,
+                                int64_t* __restrict__ out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < o.total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = scatter_entry(L, o, b, t);
+}
+
+// All problems of a batch: entry t belongs to the problem p with
+// offsets[p] <= t < offsets[p + 1] (binary search).
+__global__ void k_build_scatter_batched(const Layout* __restrict__ layouts,
+                                        const int64_t* __restrict__ offsets, int32_t count,
+                                        int64_t total, int32_t b, int64_t* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int sec = 0;
-    while (sec < 11 && t >= starts[sec + 1]) ++sec;
-    const int64_t x = t - starts[sec];
-    if (sec < 6) {
-      Section S = section(L, sec);
-      out[t] = scat_at(S.len, S.s, S.nd, x);
-    } else {
-      Section S = section(L, sec - 6);
-      const int64_t lo = x * b;
-      const int64_t hi = lo + b < S.l ? lo + b : S.l;
-      int64_t v;
-      if (hi - lo <= 1) {
-        v = 1;
-      } else {
-        int64_t prev = scat_at(S.len, S.s, S.nd, lo);
-        int64_t cur = scat_at(S.len, S.s, S.nd, lo + 1);
-        const int64_t st = cur - prev;
-        bool ok = st > 0;
-        for (int64_t j = lo + 2; j < hi && ok; ++j) {
-          prev = cur;
-          cur = scat_at(S.len, S.s, S.nd, j);
-          ok = (cur - prev) == st;
-        }
-        v = ok ? st : 0;
-      }
-      out[t] = v;
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= t) lo = mid; else hi = mid;
     }
+    const Layout& L = layouts[lo];
+    out[t] = scatter_entry(L, scatter_offsets(L, b), b, t - offsets[lo]);
   }
 }
 
@@ -119,6 +135,17 @@ cudaError_t launch_build_scatter(const Layout& L, int32_t b, int64_t* out, cudaS
   int64_t blocks = (o.total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_build_scatter<<<(int)blocks, 256, 0, s>>>(L, b, o, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_scatter_batched(const Layout* layouts, const int64_t* offsets,
+                                         int32_t count, int64_t total, int32_t b, int64_t* out,
+                                         cudaStream_t s) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_build_scatter_batched<<<(int)blocks, 256, 0, s>>>(layouts, offsets, count, total, b, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -48,7 +48,32 @@ struct ScatterOffsets {
   int64_t rbsA, cbsA, rbsB, cbsB, rbsC, cbsC;  // block-scatter vectors
   int64_t total;                           // entries
 };
-ScatterOffsets scatter_offsets(const Layout& L, int32_t b);
+#if defined(__CUDACC__)
+#define TC_HD __host__ __device__
+#else
+#define TC_HD
+#endif
+
+TC_HD inline ScatterOffsets scatter_offsets(const Layout& L, int32_t b) {
+  ScatterOffsets o;
+  const int64_t m = L.m, n = L.n, k = L.k;
+  const int64_t nm = (m + b - 1) / b, nn = (n + b - 1) / b, nk = (k + b - 1) / b;
+  int64_t p = 0;
+  o.rA = p; p += m;
+  o.cA = p; p += k;
+  o.rB = p; p += k;
+  o.cB = p; p += n;
+  o.rC = p; p += m;
+  o.cC = p; p += n;
+  o.rbsA = p; p += nm;
+  o.cbsA = p; p += nk;
+  o.rbsB = p; p += nk;
+  o.cbsB = p; p += nn;
+  o.rbsC = p; p += nm;
+  o.cbsC = p; p += nn;
+  o.total = p;
+  return o;
+}
 
 // Block size of the block-scatter vectors the mainloops consult.
 constexpr int32_t kBsBlock = 4;

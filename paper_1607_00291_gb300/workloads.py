@@ -172,3 +172,16 @@ def make_random_inputs(p: RandomProblem, seed: int, dtype=torch.float64, dist: s
         flat = _draw(g, n, dist).to(dtype).to(torch.float64)
         out[name] = dense_permuted(flat, lab, order or lab, p.ext)
     return out
+
+
+# ---- the batch workload: 512 independent contractions ---------------------------------
+
+def batch_problems(seed: int = 1004, count: int = 512):
+    """Random contractions of the paper's random-contraction generator shape:
+    1-3 contracted indices, ranks 2-6 per operand (d_I + d_P <= 6,
+    d_P + d_J <= 6, d_I, d_J >= 1), extents uniform in 8..64, random label
+    orders and randomly permuted dense layouts; a draw whose operand exceeds
+    2^22 elements or whose flop count exceeds 2^34 is redrawn."""
+    rng = np.random.default_rng(seed)
+    return [random_problem(rng, dI=(1, 5), dJ=(1, 5), dP=(1, 3), ext=(8, 64), max_rank=6,
+                           max_elems=1 << 22, max_flops=2.0 ** 34) for _ in range(count)]

@@ -1,0 +1,141 @@
+"""Batched contractions (K6 persistent launch, K7 autotuner, graph replay)
+against the CPU oracle, problem by problem, in every mode."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1607_00291_gb300 as tc
+from paper_1607_00291_gb300 import workloads as W
+
+from helpers import norm_err, oracle_ref, to_device
+
+pytestmark = pytest.mark.gpu
+TOLS = {"f64": 1e-12, "bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24, "bf16x6": 1e-5}
+
+
+def make_batch(seed, count, ext=(1, 30), mode="f64"):
+    rng = np.random.default_rng(seed)
+    dt = torch.float64 if mode == "f64" else torch.float32
+    host, dev = [], []
+    for i in range(count):
+        p = W.random_problem(rng, dI=(1, 3), dJ=(1, 3), dP=(1, 3), ext=ext, max_elems=1 << 16,
+                             max_flops=2.0 ** 24)
+        h = W.make_random_inputs(p, seed=seed * 1000 + i, dtype=dt)
+        alpha = float(rng.uniform(-2, 2))
+        beta = float(rng.choice([0.0, 1.0, rng.uniform(-2, 2)]))
+        host.append((p, h, alpha, beta))
+        dev.append((to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB,
+                    to_device(h["C"], dt), p.labC, alpha, beta))
+    return host, dev
+
+
+def check_batch(host, dev, mode):
+    worst = 0.0
+    for (p, h, alpha, beta), d in zip(host, dev):
+        ref, mag = oracle_ref(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
+        e = norm_err(d[4].cpu().double().numpy(), ref, mag)
+        worst = max(worst, e)
+    assert worst <= TOLS[mode], worst
+    return worst
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3", "bf16x6"])
+def test_batch_matches_oracle(mode):
+    host, dev = make_batch(11, 40, mode=mode)
+    tc.contract_batched(dev, mode=mode)
+    assert tc.device_error() == 0
+    check_batch(host, dev, mode)
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3"])
+def test_plan_graph_capture_and_replay(mode):
+    host, dev = make_batch(12, 24, mode=mode)
+    C0 = [d[4].clone() for d in dev]
+    plan = tc.Plan(dev, mode=mode)
+    plan.execute()  # first run outside capture (one-time per-device set-up)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.execute()
+    # capture does not run the kernels; each replay performs the batch once
+    for d, c0 in zip(dev, C0):
+        d[4].copy_(c0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    check_batch(host, dev, mode)
+    for d, c0 in zip(dev, C0):
+        d[4].copy_(c0)
+    g.replay()
+    torch.cuda.synchronize()
+    check_batch(host, dev, mode)
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x6"])
+def test_batch_degenerate_members(mode):
+    dt = torch.float64 if mode == "f64" else torch.float32
+    g = torch.Generator().manual_seed(13)
+    r = lambda *s: (torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1).to(dt).double()
+    cases = [
+        (0.0, torch.full((9, 7), float("nan"), dtype=torch.float64), "ip", r(7, 5), "pj", 2.0, r(9, 5), "ij"),
+        (1.0, torch.zeros(9, 0, dtype=torch.float64), "ip", torch.zeros(0, 5, dtype=torch.float64), "pj", 0.5, r(9, 5), "ij"),
+        (1.0, r(0, 4), "ip", r(4, 5), "pj", 1.0, torch.zeros(0, 5, dtype=torch.float64), "ij"),
+        (1.0, r(33), "p", r(33, 70), "pj", 0.0, torch.full((70,), float("nan"), dtype=torch.float64), "j"),
+        (1.0, r(130), "i", r(70), "j", 0.0, torch.zeros(70, 130, dtype=torch.float64), "ji"),
+        (1.5, r(7, 9), "ab", r(9, 7), "ba", -1.0, r(()), ""),
+    ]
+    dev = [(to_device(A, dt), la, to_device(B, dt), lb, to_device(C, dt), lc, al, be)
+           for (al, A, la, B, lb, be, C, lc) in cases]
+    tc.contract_batched(dev, mode=mode)
+    assert tc.device_error() == 0
+    for (al, A, la, B, lb, be, C, lc), d in zip(cases, dev):
+        got = d[4].cpu().double().numpy()
+        if al == 0.0:
+            assert np.array_equal(got, (be * C).to(dt).double().numpy())
+            continue
+        ref, mag = oracle_ref(al, A, la, B, lb, be, C, lc)
+        assert norm_err(got, ref, mag) <= TOLS[mode]
+
+
+def test_autotuned_batch(monkeypatch, tmp_path):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TC_AUTOTUNE", "1")
+    monkeypatch.setenv("TC_AUTOTUNE_CACHE", str(cache))
+    host, dev = make_batch(14, 12, ext=(8, 40), mode="bf16x3")
+    tc.contract_batched(dev, mode="bf16x3")
+    assert tc.device_error() == 0
+    check_batch(host, dev, "bf16x3")
+    lines = cache.read_text().strip().splitlines()
+    assert lines and all(len(l.split()) == 8 for l in lines)
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3"])
+def test_batch512_workload_sampled(mode):
+    # the 512-problem workload at full size: every problem checked on its first
+    # 48 output elements (colexicographic order of C)
+    import oracle
+    dt = torch.float64 if mode == "f64" else torch.float32
+    probs = W.batch_problems(seed=1004)
+    host, dev = [], []
+    for i, p in enumerate(probs):
+        h = W.make_random_inputs(p, seed=5000 + i, dtype=dt)
+        host.append((p, h))
+        dev.append((to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB,
+                    to_device(h["C"], dt), p.labC, 1.0, 0.0))
+    tc.contract_batched(dev, mode=mode)
+    assert tc.device_error() == 0
+    worst = 0.0
+    for (p, h), d in zip(host, dev):
+        got = d[4].cpu().double().numpy().ravel(order="F")
+        c = np.array(h["C"].numpy(), copy=True)
+        w = min(48, got.size)
+        mag = oracle.contract_(1.0, h["A"].numpy(), p.labA, h["B"].numpy(), p.labB, 0.0, c, p.labC,
+                               begin=0, end=w)
+        worst = max(worst, norm_err(got[:w], np.asarray(c).ravel(order="F")[:w],
+                                    mag.ravel(order="F")[:w]))
+    assert worst <= TOLS[mode], worst
