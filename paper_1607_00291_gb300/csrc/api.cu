@@ -65,44 +65,28 @@ int sm_count() {
   return n;
 }
 
-// Tile shape and split of the contracted range for the tensor-core mainloop.
-//  * tile width bn: the next multiple of 16 above n when n < 128; otherwise
-//    128, or 256 (two-piece mode only) when that fills the SMs' waves as well;
-//  * split count S, from two constraints: accuracy -- the tensor core
-//    accumulates in FP32 with unspecified rounding, so each CTA's chain is
-//    capped at kChainTiles k-tiles of 32 (1024 terms) and the FP32 partials are
-//    summed with compensated FP32 arithmetic (K4); parallelism -- when the output alone has fewer tiles
-//    than SMs, split further so the grid covers the SMs, keeping at least 8
-//    k-tiles per split.
-constexpr int64_t kChainTiles = 32;
-
+// Tile shape and split of the contracted range for the tensor-core mainloop:
+//  * tile width bn: the next multiple of 16 above n, at most 128;
+//  * split count S: when the output alone has fewer tiles than SMs, split the
+//    contracted range so the grid covers the SMs, keeping at least 8 k-tiles
+//    of 32 per split (the kernel itself bounds every FP32 accumulation chain
+//    to 1024 terms, so accuracy needs no split).
 TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force, int split_mult) {
+  (void)pieces;
   TcChoice c;
   const int64_t tm = (L.m + 127) / 128;
-  auto waves_eff = [&](int bn) {
-    const int64_t t = tm * ((L.n + bn - 1) / bn);
-    const int64_t w = (t + sms - 1) / sms;
-    return (double)t / (double)(w * sms) * (bn == 256 ? 1.0 : 0.97);
-  };
-  if (bn_force > 0) {
-    c.bn = bn_force;
-  } else if (L.n < 128) {
-    c.bn = (int)std::max<int64_t>(16, (L.n + 15) / 16 * 16);
-  } else {
-    c.bn = (pieces == 2 && L.n > 128 && waves_eff(256) >= waves_eff(128)) ? 256 : 128;
-  }
-  c.bn_max = tc_bn_max_for(pieces, c.bn);
+  const int bmax = tc_bn_max();
+  c.bn = bn_force > 0 ? std::min(bn_force, bmax)
+                      : (int)std::min<int64_t>(bmax, std::max<int64_t>(16, (L.n + 15) / 16 * 16));
   const int64_t tiles = tm * ((L.n + c.bn - 1) / c.bn);
   const int64_t kt = (L.k + 31) / 32;
-  const int64_t s_acc = (kt + kChainTiles - 1) / kChainTiles;
-  int64_t s_par = 1;
-  if (tiles < sms) s_par = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
-  int64_t s = std::max<int64_t>(1, std::max(s_acc, s_par)) * std::max(1, split_mult);
+  int64_t s = 1;
+  if (tiles < sms) s = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
+  s = std::max<int64_t>(1, s) * std::max(1, split_mult);
   s = std::min<int64_t>(s, std::max<int64_t>(kt, 1));
   const int64_t ktps = (kt + s - 1) / s;
-  c.kps = ktps * 32;
-  c.splits = (int)((L.k + c.kps - 1) / c.kps);
-  if (c.splits < 1) c.splits = 1;
+  c.kps = std::max<int64_t>(1, ktps) * 32;
+  c.splits = (int)std::max<int64_t>(1, (L.k + c.kps - 1) / c.kps);
   return c;
 }
 
@@ -120,15 +104,14 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
   w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
   w.partial_off = w.scatter_bytes;
   w.partial_bytes = 0;
-  w.tcc = TcChoice{128, 128, 1, 0};
+  w.tcc = TcChoice{128, 1, 0};
   if (mode != TC_MODE_F64 && p.L.k > 0) {
-    // TC_FORCE_BN (16..256, step 16; 256 only with two pieces) pins the tile
-    // width, for tests and tuning experiments
+    // TC_FORCE_BN (16..128, step 16) pins the tile width, for tests and
+    // tuning experiments
     int force = 0;
     if (const char* e = std::getenv("TC_FORCE_BN")) {
       const int v = std::atoi(e);
-      const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
-      if (v >= 16 && v % 16 == 0 && v <= (pieces == 2 ? 256 : 128)) force = v;
+      if (v >= 16 && v % 16 == 0 && v <= tc_bn_max()) force = v;
     }
     w.tcc = choose_tc(p.L, mode == TC_MODE_BF16X6 ? 3 : 2, sm_count(), force);
     if (w.tcc.splits > 1)
@@ -186,7 +169,6 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     d.splits = w.tcc.splits;
     d.kps = w.tcc.kps;
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
-    q.bn_max = w.tcc.bn_max;
     q.ctas = sm_count();
     q.err = err_word();
     return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;

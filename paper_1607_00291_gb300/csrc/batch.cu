@@ -37,12 +37,14 @@ struct ProbCfg {
 };
 
 // ---- K7: autotuner ------------------------------------------------------------------------
-// Shape class: mode, pieces, rounded log2 of m, n, k, and the two access
-// flags.  Candidates (tensor-core path): tile widths around n and split
-// multipliers 1 and 2; each is timed on the first problem of its class in the
-// batch, writing into a scratch copy of that problem's output (the caller's C
-// is never touched), and the fastest is kept for the rest of the process (and
-// in the file named by TC_AUTOTUNE_CACHE, when set).
+// Shape class: mode, rounded log2 of m, n, k, and the two access flags.
+// Candidates (tensor-core path): tile widths around n.  Each is timed on the
+// first problem of its class in the batch running on ONE persistent CTA --
+// in a batch the other problems keep the other SMs busy, so the SM-time a
+// problem costs is what the choice should minimise -- writing into a scratch
+// copy of that problem's output (the caller's C is never touched).  The
+// fastest is kept for the rest of the process (and in the file named by
+// TC_AUTOTUNE_CACHE, when set).
 struct TuneKey {
   int mode, lm, ln, lk, akc, bkc;
   bool operator<(const TuneKey& o) const {
@@ -108,7 +110,7 @@ bool autotune_enabled() {
 float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, int bn, int sm,
                      int64_t* scat, float* partial, void* cscratch, int64_t c_off, cudaStream_t st) {
   const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
-  const TcChoice c = choose_tc(p.L, pieces, sm_count(), bn, sm);
+  const TcChoice c = choose_tc(p.L, pieces, 1, bn, sm);
   const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
   TcLaunch q;
   std::memset(&q, 0, sizeof q);
@@ -130,8 +132,7 @@ float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, 
   d.splits = c.splits;
   d.kps = c.kps;
   q.pieces = pieces;
-  q.bn_max = c.bn_max;
-  q.ctas = sm_count();
+  q.ctas = 1;
   q.err = err_word();
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -163,15 +164,12 @@ TuneVal tune_tc(const Planned& p, tc_mode mode, double alpha, double beta) {
     if (b0 > 32) bns.push_back((b0 / 2 + 15) / 16 * 16);
   } else {
     bns.push_back(128);
-    if (pieces == 2) bns.push_back(256);
     bns.push_back(64);
   }
   // scratch: scatter vectors, partials for the largest split, a copy of C's span
   const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
   int64_t max_split = 1;
-  for (int bn : bns)
-    for (int sm = 1; sm <= 2; ++sm)
-      max_split = std::max<int64_t>(max_split, choose_tc(p.L, pieces, sm_count(), bn, sm).splits);
+  for (int bn : bns) max_split = std::max<int64_t>(max_split, choose_tc(p.L, pieces, 1, bn, 1).splits);
   int64_t cmin = 0, cmax = 0;
   for (int i = 0; i < p.info.nI; ++i) {
     const int64_t e = (p.info.I_len[i] - 1) * p.info.I_sC[i];
@@ -194,14 +192,13 @@ TuneVal tune_tc(const Planned& p, tc_mode mode, double alpha, double beta) {
     cudaGetLastError();
   } else if (launch_build_scatter(p.L, kBsBlock, scat, st) == cudaSuccess) {
     float tbest = 1e30f;
-    for (int bn : bns)
-      for (int sm = 1; sm <= 2; ++sm) {
-        const float t = time_tc_config(p, mode, alpha, beta, bn, sm, scat, partial, cs, -cmin, st);
-        if (t < tbest) {
-          tbest = t;
-          best = TuneVal{bn, sm};
-        }
+    for (int bn : bns) {
+      const float t = time_tc_config(p, mode, alpha, beta, bn, 1, scat, partial, cs, -cmin, st);
+      if (t < tbest) {
+        tbest = t;
+        best = TuneVal{bn, 1};
       }
+    }
   }
   if (st) cudaStreamDestroy(st);
   cudaFree(scat);
@@ -227,10 +224,12 @@ struct tc_plan {
   DevProblem* d_probs = nullptr;
   WorkItem* d_items = nullptr;
   int32_t* d_split = nullptr;
+  int64_t* d_split_cols = nullptr;
+  int64_t split_cols = 0;
   int64_t total_scatter = 0, nitems = 0;
   int32_t n_split = 0;
   int64_t max_m_split = 0, max_n_split = 0;
-  int pieces = 2, bn_max = 128;
+  int pieces = 2;
   int64_t ctas = 152;
 };
 
@@ -268,7 +267,9 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + tk_f - 1) / tk_f);
     } else {
       TuneVal tv{0, 1};
-      if (autotune_enabled() && L.k > 0) {
+      // tuning times one CTA: skip problems too large to time quickly that way
+      const double sm_work = (double)((L.m + 127) / 128) * ((L.n + 127) / 128) * ((L.k + 31) / 32);
+      if (autotune_enabled() && L.k > 0 && sm_work <= 4096) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_file();
         const TuneKey key = tune_key(pl->mode, pl->planned[i]);
@@ -281,20 +282,36 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
           tv = it->second;
         }
       }
-      const TcChoice ch = L.k > 0 ? choose_tc(L, pl->pieces, sms, tv.bn, tv.split_mult)
-                                  : TcChoice{std::max(16, (int)std::min<int64_t>(128, (L.n + 15) / 16 * 16)),
-                                             128, 1, 32};
+      // in a batch the other problems keep the SMs busy: no parallelism split
+      // here (long items are split below, for balance)
+      const TcChoice ch = choose_tc(L, pl->pieces, 1, tv.bn, tv.split_mult);
       c.bn = ch.bn;
       c.splits = ch.splits;
       c.kps = ch.kps;
       c.tiles = ((L.m + 127) / 128) * ((L.n + c.bn - 1) / c.bn);
-      pl->bn_max = std::max(pl->bn_max, tc_bn_max_for(pl->pieces, c.bn));
-      cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + 31) / 32) * c.bn / 128.0;
+      cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + 31) / 32 / c.splits) * c.splits;
     }
     total_cost += cost[i];
   }
-  // FP64: split long-k problems so that no item exceeds a quarter of a CTA's
-  // fair share (k-tiles of 16); the tensor-core split already caps chains.
+  // Split long-k problems so that no item exceeds a quarter of a CTA's fair
+  // share of the batch (in k-tiles: 16 on the FP64 path, 32 on the tensor
+  // cores).
+  if (!f64) {
+    const double fair = total_cost / (double)sms;
+    for (int i = 0; i < np; ++i) {
+      const Layout& L = pl->planned[i].L;
+      ProbCfg& c = pl->cfg[i];
+      const int64_t KT = (L.k + 31) / 32;
+      if (KT == 0) continue;
+      const double item = (double)KT / c.splits;
+      if (item <= std::max(8.0, fair / 4.0)) continue;
+      int64_t s = (int64_t)std::ceil((double)KT / std::max(8.0, fair / 4.0));
+      s = std::max<int64_t>(c.splits, std::min<int64_t>(s, KT));
+      const int64_t ktps = (KT + s - 1) / s;
+      c.kps = ktps * 32;
+      c.splits = (int)((KT + ktps - 1) / ktps);
+    }
+  }
   if (f64) {
     const double fair = total_cost / (double)sms;
     for (int i = 0; i < np; ++i) {
@@ -344,6 +361,19 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
                    [&](const WorkItem& x, const WorkItem& y) { return item_cost(x) > item_cost(y); });
   pl->nitems = (int64_t)items.size();
   pl->n_split = (int32_t)splitp.size();
+  if (const char* lg = std::getenv("TC_LOG")) {
+    if (lg[0] == '1') {
+      std::map<int, int> bns;
+      double ksteps = 0;
+      for (const WorkItem& w : items) ksteps += item_cost(w);
+      for (int i = 0; i < np; ++i) bns[pl->cfg[i].bn]++;
+      std::fprintf(stderr, "[libtc] batch plan: %d problems, %lld work items, %d split, "
+                   "%.3g k-index-units of work; tile widths:", np, (long long)pl->nitems,
+                   pl->n_split, ksteps);
+      for (const auto& kv : bns) std::fprintf(stderr, " %d x%d", kv.first, kv.second);
+      std::fprintf(stderr, "\n");
+    }
+  }
 
   const size_t es = f64 ? sizeof(double) : sizeof(float);
   size_t off = 0;
@@ -358,6 +388,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const size_t o_prob = take(sizeof(DevProblem) * std::max(np, 1));
   const size_t o_item = take(sizeof(WorkItem) * std::max<int64_t>(1, pl->nitems));
   const size_t o_split = take(sizeof(int32_t) * std::max<int32_t>(1, pl->n_split));
+  const size_t o_scols = take(sizeof(int64_t) * (pl->n_split + 1));
   const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
@@ -371,6 +402,10 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->d_probs = reinterpret_cast<DevProblem*>(base + o_prob);
   pl->d_items = reinterpret_cast<WorkItem*>(base + o_item);
   pl->d_split = reinterpret_cast<int32_t*>(base + o_split);
+  pl->d_split_cols = reinterpret_cast<int64_t*>(base + o_scols);
+  std::vector<int64_t> scols(pl->n_split + 1, 0);
+  for (int i = 0; i < pl->n_split; ++i) scols[i + 1] = scols[i] + pl->planned[splitp[i]].L.n;
+  pl->split_cols = scols[pl->n_split];
   char* partial = base + o_part;
 
   std::vector<Layout> lay(np);
@@ -405,7 +440,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       !up(pl->d_offs, offs.data(), sizeof(int64_t) * (np + 1)) ||
       !up(pl->d_probs, dp.data(), sizeof(DevProblem) * np) ||
       !up(pl->d_items, items.data(), sizeof(WorkItem) * items.size()) ||
-      !up(pl->d_split, splitp.data(), sizeof(int32_t) * splitp.size()))
+      !up(pl->d_split, splitp.data(), sizeof(int32_t) * splitp.size()) ||
+      !up(pl->d_split_cols, scols.data(), sizeof(int64_t) * scols.size()))
     return TC_ERR_CUDA;
   return TC_OK;
 }
@@ -457,6 +493,8 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.nitems = plan->nitems;
     q.ctas = plan->ctas;
     q.split_probs = plan->d_split;
+    q.split_col_prefix = plan->d_split_cols;
+    q.split_cols = plan->split_cols;
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
@@ -469,9 +507,10 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.nitems = plan->nitems;
     q.nprobs = np;
     q.pieces = plan->pieces;
-    q.bn_max = plan->bn_max;
     q.ctas = plan->ctas;
     q.split_probs = plan->d_split;
+    q.split_col_prefix = plan->d_split_cols;
+    q.split_cols = plan->split_cols;
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;

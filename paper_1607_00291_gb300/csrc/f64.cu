@@ -261,12 +261,20 @@ __global__ void __launch_bounds__(NT, 1)
 
 template <typename T>
 __global__ void k_f64_batched_reduce(const DevProblem* __restrict__ probs,
-                                     const int32_t* __restrict__ split_probs) {
-  const DevProblem& d = probs[split_probs[blockIdx.z]];
-  const int64_t M = d.m, N = d.n, plane = M * N;
-  const double* part = static_cast<const double*>(d.partial);
-  T* c = static_cast<T*>(d.c);
-  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
+                                     const int32_t* __restrict__ split_probs,
+                                     const int64_t* __restrict__ col_prefix, int32_t n_split) {
+  const int64_t total = col_prefix[n_split];
+  for (int64_t r = blockIdx.y; r < total; r += gridDim.y) {
+    int lo = 0, hi = n_split;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (col_prefix[mid] <= r) lo = mid; else hi = mid;
+    }
+    const DevProblem& d = probs[split_probs[lo]];
+    const int64_t n = r - col_prefix[lo];
+    const int64_t M = d.m, plane = M * d.n;
+    const double* part = static_cast<const double*>(d.partial);
+    T* c = static_cast<T*>(d.c);
     const int64_t cn = d.sp.cC[n];
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
@@ -363,10 +371,10 @@ cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
     k_f64_batched<T><<<(unsigned)grid, NT, kSmem, s>>>(q.probs, q.items, q.nitems);
     note_launch();
     if (q.n_split_probs > 0) {
-      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 64));
-      const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q.max_n_split, 32768));
-      k_f64_batched_reduce<T><<<dim3(bx, by, (unsigned)q.n_split_probs), 256, 0, s>>>(q.probs,
-                                                                                     q.split_probs);
+      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 16));
+      const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q.split_cols, 16384));
+      k_f64_batched_reduce<T><<<dim3(bx, by), 256, 0, s>>>(q.probs, q.split_probs,
+                                                           q.split_col_prefix, q.n_split_probs);
       note_launch();
     }
     mainloop_event_after(s);

@@ -19,9 +19,9 @@ int sm_count();
 int plan_checked(tc_dtype dt, const tc_tensor* A, const tc_tensor* B, const tc_tensor* C,
                  Planned* p);
 
-// Tile width, shared-memory plan and k-split of the tensor-core mainloop.
+// Tile width and k-split of the tensor-core mainloop.
 struct TcChoice {
-  int bn, bn_max, splits;
+  int bn, splits;
   int64_t kps;
 };
 TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force = 0, int split_mult = 1);

@@ -73,7 +73,8 @@ struct WorkItem {
 };
 
 // K3 + K5 (tc_mma.cu): tcgen05 mainloop over bf16 pieces (2 -> BF16x3,
-// 3 -> BF16x6), persistent over work items; K4 reduces split partials (two-sum FP32).
+// 3 -> BF16x6), persistent over work items, chunked FP32 accumulation summed
+// in float-float; K4 reduces the partials of k-splits (two-sum FP32).
 struct TcLaunch {
   DevProblem single;          // the problem of a single call (probs == null)
   const DevProblem* probs;    // batch descriptors (device), or null
@@ -81,9 +82,10 @@ struct TcLaunch {
   int64_t nitems;             // work items in the list (batch)
   int32_t nprobs;             // problems in the batch
   int pieces;                 // 2 or 3
-  int bn_max;                 // 128 or 256: shared-memory plan of the kernel
   int64_t ctas;               // persistent grid size
   const int32_t* split_probs; // batch: indices of problems with splits > 1 (device)
+  const int64_t* split_col_prefix;  // batch: prefix sums of their n (device, n_split + 1)
+  int64_t split_cols;         // batch: total columns of the split problems
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
   int32_t* err;
@@ -99,6 +101,8 @@ struct F64BatchLaunch {
   int64_t nitems;
   int64_t ctas;
   const int32_t* split_probs;
+  const int64_t* split_col_prefix;
+  int64_t split_cols;
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;
 };
@@ -109,6 +113,6 @@ cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s);
 cudaError_t launch_build_scatter_batched(const Layout* layouts, const int64_t* offsets,
                                          int32_t count, int64_t total, int32_t b, int64_t* out,
                                          cudaStream_t s);
-int tc_bn_max_for(int pieces, int bn);
+int tc_bn_max();  // widest output tile of the tensor-core mainloop (columns)
 
 }  // namespace tc

@@ -11,17 +11,25 @@
 // canonical layout.  One elected thread issues, per 16-wide k-slice, a
 // tcgen05.mma for every piece pair (i, j) with i + j < pieces -- three for two
 // pieces (BF16x3), six for three (BF16x6) -- into an FP32 accumulator in
-// Tensor Memory.  The epilogue reads it with tcgen05.ld and applies alpha/beta
-// through rscat(C) + cscat(C), or, when the contracted range is split, stores
-// FP32 partials that K4 sums with compensated FP32 arithmetic.
+// Tensor Memory.
+//
+// Accumulation: the tensor core adds in FP32 with unspecified rounding, and
+// over thousands of terms that alone exceeds 1e-5 of sum|a||b| (measured on
+// the spiky 4096^3 workload: 2.25e-5 with 4096-term chains).  So a tile's
+// contracted range is processed in chunks of at most 1024 terms, each into a
+// fresh accumulator (two buffers, alternating), and the epilogue warps add the
+// finished chunks into a running float-float sum (Knuth's two-sum) that stays
+// in Tensor Memory.  After the last chunk they apply alpha/beta through
+// rscat(C) + cscat(C), or -- when a tile's range is also split across CTAs for
+// parallelism -- store the FP32 partial that K4 sums the same compensated way.
 //
 // Warp roles (672 threads): warps 0-7 load (cp.async), warps 8-15 convert,
 // warps 16-19 run the epilogue (one per Tensor Memory lane quarter), warp 20
-// owns the Tensor Memory allocation and its lane 0 issues the MMAs.  The
-// accumulator is double-buffered in Tensor Memory, so the epilogue of one tile
-// overlaps the MMAs of the next.  Hand-offs go through mbarriers: raw_full
-// (cp.async completion) / raw_empty, mma_full / mma_empty (tcgen05.commit),
-// acc_full[2] (tcgen05.commit) / acc_empty[2].  Every
+// owns the Tensor Memory allocation (512 columns: two accumulators, the hi and
+// lo words of the running sum) and its lane 0 issues the MMAs.  The epilogue
+// of one chunk overlaps the MMAs of the next.  Hand-offs go through mbarriers:
+// raw_full (cp.async completion) / raw_empty, mma_full / mma_empty
+// (tcgen05.commit), acc_full[2] (tcgen05.commit) / acc_empty[2].  Every
 // mbarrier wait is bounded: on expiry the CTA records TC_ERR_DEVICE_TIMEOUT in
 // the device error word and raises a CTA-wide abort flag; the roles leave
 // their loops together (barrier reductions of the flag), the MMA thread waits
@@ -52,12 +60,15 @@ constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
 constexpr int BAR_LOAD = 1, BAR_CONV = 2, BAR_EPI = 3;
 constexpr int KRING = 3;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
+constexpr int BNMAX = 128;        // widest output tile (columns)
+constexpr int CHUNK_KT = 32;      // k-tiles per accumulation chunk (1024 terms)
+constexpr uint32_t TM_ACC = 0, TM_HI = 2 * BNMAX, TM_LO = 3 * BNMAX, TM_COLS = 4 * BNMAX;
 
-template <int BNMAX, int NS>
+template <int NS>
 struct Lay {
-  static constexpr int RS = BNMAX == 256 ? 2 : (NS == 3 ? 3 : 4);  // raw FP32 stages
-  static constexpr int MS = 2;                                   // bf16 MMA stages
-  static constexpr int PA = BM * BK * 2;                        // one bf16 piece of A
+  static constexpr int RS = NS == 3 ? 3 : 4;  // raw FP32 stages
+  static constexpr int MS = 2;                 // bf16 MMA stages
+  static constexpr int PA = BM * BK * 2;       // one bf16 piece of A
   static constexpr int PB = BNMAX * BK * 2;
   static constexpr int B_OFF = NS * PA;
   static constexpr int MMA_STAGE = NS * (PA + PB);
@@ -127,6 +138,7 @@ struct Item {
   int64_t m0, n0, kbeg, kend, KT;
   int split;
   int rows_a, rows_b;
+  int nchunks;
 };
 
 __device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w) {
@@ -150,7 +162,14 @@ __device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single
   it.KT = it.kend > it.kbeg ? (it.kend - it.kbeg + BK - 1) / BK : 0;
   it.rows_a = (int)(d->m - it.m0 < BM ? d->m - it.m0 : BM);
   it.rows_b = (int)(d->n - it.n0 < d->bn ? d->n - it.n0 : d->bn);
+  it.nchunks = it.KT > 0 ? (int)((it.KT + CHUNK_KT - 1) / CHUNK_KT) : 1;
   return it;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // ---- loader: one raw FP32 panel of R rows x BK k through cp.async ----------------------
@@ -270,18 +289,16 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
     split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
   }
 }
-
-template <int BNMAX, int NS>
+template <int NS>
 __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
-  using Ly = Lay<BNMAX, NS>;
+  using Ly = Lay<NS>;
   constexpr int RS = Ly::RS, MS = Ly::MS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align to 1 KB by offsetting the shared-memory pointer itself, so that the
   // compiler keeps every access below in the shared state space
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   int64_t* sRA = reinterpret_cast<int64_t*>(smem + Ly::SCAT);  // loaders' rows
-  int64_t* sCB = sRA + BM;
-  int64_t* sRC = sCB + BNMAX;  // epilogue's rows
+  int64_t* sRC = sRA + BM + BNMAX;                            // epilogue's rows
   int64_t* sCC = sRC + BM;
   int64_t* kring = reinterpret_cast<int64_t*>(smem + Ly::KR);
   DevProblem* sProb = reinterpret_cast<DevProblem*>(smem + Ly::PROB);
@@ -315,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
     fence_mbar_init();
   }
   if (warp == MMA_WARP) {
-    tmem_alloc(tmem_slot, 2 * BNMAX);
+    tmem_alloc(tmem_slot, TM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -329,8 +346,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
     // ---- loaders ----
     const int t = tid;
     int64_t g = 0;  // k-tiles staged by this CTA so far
-    // row scatter entries of the next item, fetched one item ahead
-    constexpr int NR = (BM + BNMAX + NLOAD - 1) / NLOAD;  // rows (A then B) per thread
+    // row scatter entries (A rows then B rows) of the next item, fetched one item ahead
+    constexpr int NR = (BM + BNMAX + NLOAD - 1) / NLOAD;
     int64_t pre[NR];
     auto fetch_rows = [&](const Item& it) {
 #pragma unroll
@@ -352,14 +369,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
         const int r = t + i * NLOAD;
-        if (r < BM + BNMAX) sRA[r] = pre[i];  // sCB follows sRA contiguously
+        if (r < BM + BNMAX) sRA[r] = pre[i];  // B rows follow A rows
       }
       if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
-      // k ring: entries of k-tiles 0 and 1 of this item
-      if (t < KSLOT) {
+      if (t < KSLOT) {  // k ring: entries of k-tiles 0 and 1 of this item
         for (int64_t kt = 0; kt < 2 && kt < it.KT; ++kt)
           kring[(kt % KRING) * KSLOT + t] = kslot_fetch(t, d, it.kbeg + kt * BK, it.kend);
       }
@@ -376,7 +392,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
           const int64_t* slot = kring + (kt % KRING) * KSLOT;
           const int64_t k0 = it.kbeg + kt * BK;
           load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc);
-          load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sCB, it.rows_b, slot + BK,
+          load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
                             slot + 2 * BK + BK / 4, k0, it.kend, bkc);
           cp_async_arrive(&raw_full[s]);
         }
@@ -415,6 +431,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
     const int t = tid - NLOAD - NCONV;
     const int wq = warp & 3;  // Tensor Memory lane quarter of this warp
     const int row = 32 * wq + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
     constexpr int NB = BNMAX / NEPI;
     int64_t pre_r = 0, pre_c[NB];
     auto fetch_rows = [&](const Item& it) {
@@ -426,8 +443,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
       }
     };
     if (w0 < nitems) fetch_rows(get_item(a, sProb, w0));
-    int64_t j = 0;
-    for (int64_t w = w0; w < nitems; w += dw, ++j) {
+    int64_t gc = 0;  // chunks finished by this CTA
+    for (int64_t w = w0; w < nitems; w += dw) {
       if (bar_or(BAR_EPI, NEPI, *abort)) break;  // uniform exit; previous rows consumed
       const Item it = get_item(a, sProb, w);
       const DevProblem* d = it.d;
@@ -436,96 +453,140 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
       if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
       bar_sync(BAR_EPI, NEPI);
-      const int b = (int)(j & 1);
       const bool have = it.KT > 0;
-      if (have && !*abort) {
-        if (!mbar_wait(&acc_full[b], (uint32_t)((j >> 1) & 1), abort)) record_timeout(abort, a.err);
-      }
-      tc_fence_after();
-      const bool ok = __all_sync(0xffffffffu, !*abort);
-      const bool mv = row < it.rows_a;
+      // descriptor fields in registers: the stores below could alias them as
+      // far as the compiler knows, which would reload them per element
       const int bn = d->bn;
-      const uint32_t tbase = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BNMAX);
-      if (ok) {
-        const bool direct = d->splits == 1;
-        const double alpha = d->alpha, beta = d->beta;
-        float* cbase = static_cast<float*>(d->c) + sRC[row];
-        float* pbase = direct ? nullptr
-                              : static_cast<float*>(d->partial) +
-                                    ((int64_t)it.split * d->n + it.n0) * d->m + it.m0 + row;
-        const int64_t m = d->m;
-        for (int cb = 0; cb < bn; cb += 16) {
-          float v[16];
-          if (have) {
-            tmem_ld16(tbase + (uint32_t)cb, v);
-          } else {
+      const bool direct = d->splits == 1;
+      const float al = (float)d->alpha, be = (float)d->beta;
+      float* const crow = static_cast<float*>(d->c) + sRC[row];
+      float* const prow = direct ? nullptr
+                                 : static_cast<float*>(d->partial) +
+                                       ((int64_t)it.split * d->n + it.n0) * d->m + it.m0 + row;
+      const int64_t pm = d->m;
+      const bool mv = row < it.rows_a;
+      const int cols = it.rows_b;
+      bool ok = true;
+      for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
+        const int b = (int)(gc & 1);
+        const bool first = ch == 0, last = ch + 1 == it.nchunks;
+        if (have && !*abort) {
+          if (!mbar_wait(&acc_full[b], (uint32_t)((gc >> 1) & 1), abort)) record_timeout(abort, a.err);
+        }
+        tc_fence_after();
+        ok = __all_sync(0xffffffffu, !*abort);
+        if (ok) {
+          const uint32_t acc = lane_base + TM_ACC + (uint32_t)(b * BNMAX);
+          for (int cb = 0; cb < bn; cb += 8) {
+            float v[8], hi[8], lo[8];
+            if (have) {
+              tmem_ld8(acc + (uint32_t)cb, v);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = 0.f;
-          }
+              for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            }
+            if (first) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int col = cb + q;
-            if (mv && col < it.rows_b) {
-              if (direct) {
-                float* cp = cbase + sCC[col];
-                double r = alpha * (double)v[q];
-                if (beta != 0.0) r += beta * (double)*cp;
-                *cp = (float)r;
+              for (int q = 0; q < 8; ++q) {
+                hi[q] = v[q];
+                lo[q] = 0.f;
+              }
+            } else {
+              tmem_ld8(lane_base + TM_HI + (uint32_t)cb, hi);
+              tmem_ld8(lane_base + TM_LO + (uint32_t)cb, lo);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float e;
+                two_sum(hi[q], v[q], hi[q], e);
+                lo[q] = __fadd_rn(lo[q], e);
+              }
+            }
+            if (!last) {
+              tmem_st8(lane_base + TM_HI + (uint32_t)cb, hi);
+              tmem_st8(lane_base + TM_LO + (uint32_t)cb, lo);
+              continue;
+            }
+            // output of the tile: alpha * (hi + lo) [+ beta * C], or the partial.
+            // The three cases are separate loops so that no load of C is ever
+            // issued when beta == 0 (C is then only written), and the loads of
+            // C for beta != 0 are all in flight before the first store.
+            if (mv) {
+              if (!direct) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
+              } else if (be == 0.f) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
               } else {
-                pbase[(int64_t)col * m] = v[q];
+                float old[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if (cb + q < cols)
+                    crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
               }
             }
           }
+          if (!last) tmem_st_wait();
         }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+        if (!ok) break;
       }
-      tc_fence_before();
-      mbar_arrive(&acc_empty[b]);
     }
   } else if (lane == 0) {
     // ---- MMA issue ----
     const uint32_t base = smem_u32(smem + Ly::MMA0);
-    int64_t g = 0, j = 0;
-    for (int64_t w = w0; w < nitems && !*abort; w += dw, ++j) {
+    int64_t g = 0, gc = 0;
+    bool failed = false;
+    for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
       const Item it = get_item(a, sProb, w);
       const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
-      const int b = (int)(j & 1);
-      const int64_t u = j >> 1;  // use count of accumulator buffer b
-      if (u > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), abort)) {
-        record_timeout(abort, a.err);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t acc = tmem + (uint32_t)(b * BNMAX);
-      bool failed = false;
-      for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
-        const int ms = (int)(g % MS);
-        if (!mbar_wait(&mma_full[ms], (uint32_t)((g / MS) & 1), abort)) {
+      for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
+        const int b = (int)(gc & 1);
+        const int64_t u = gc >> 1;  // use count of accumulator buffer b
+        if (u > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), abort)) {
           record_timeout(abort, a.err);
           failed = true;
           break;
         }
         tc_fence_after();
-        const uint32_t st = base + ms * Ly::MMA_STAGE;
-#pragma unroll
-        for (int ksl = 0; ksl < BK / 16; ++ksl) {
-          const uint32_t ao = ksl * 2 * (BM / 8) * 128, bo = ksl * 2 * (BNMAX / 8) * 128;
-          uint64_t dA[NS], dB[NS];
-#pragma unroll
-          for (int i = 0; i < NS; ++i) {
-            dA[i] = smem_desc(st + i * Ly::PA + ao, (BM / 8) * 128, 128);
-            dB[i] = smem_desc(st + Ly::B_OFF + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
+        const uint32_t acc = tmem + TM_ACC + (uint32_t)(b * BNMAX);
+        const int64_t kt0 = (int64_t)ch * CHUNK_KT;
+        const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
+        for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
+          const int ms = (int)(g % MS);
+          if (!mbar_wait(&mma_full[ms], (uint32_t)((g / MS) & 1), abort)) {
+            record_timeout(abort, a.err);
+            failed = true;
+            break;
           }
-          mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > 0 || ksl > 0) ? 1u : 0u);
+          tc_fence_after();
+          const uint32_t st = base + ms * Ly::MMA_STAGE;
 #pragma unroll
-          for (int ts = 1; ts < NS; ++ts)
+          for (int ksl = 0; ksl < BK / 16; ++ksl) {
+            const uint32_t ao = ksl * 2 * (BM / 8) * 128, bo = ksl * 2 * (BNMAX / 8) * 128;
+            uint64_t dA[NS], dB[NS];
 #pragma unroll
-            for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+            for (int i = 0; i < NS; ++i) {
+              dA[i] = smem_desc(st + i * Ly::PA + ao, (BM / 8) * 128, 128);
+              dB[i] = smem_desc(st + Ly::B_OFF + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
+            }
+            mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
+#pragma unroll
+            for (int ts = 1; ts < NS; ++ts)
+#pragma unroll
+              for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+          }
+          mma_commit(&mma_empty[ms]);
         }
-        mma_commit(&mma_empty[ms]);
+        if (failed) break;
+        if (kt1 > kt0) mma_commit(&acc_full[b]);
+        else mbar_arrive(&acc_full[b]);  // nothing to accumulate: hand over at once
       }
-      if (failed) break;
-      if (it.KT > 0) mma_commit(&acc_full[b]);
-      else mbar_arrive(&acc_full[b]);  // nothing to accumulate: hand over at once
     }
     // every MMA this thread issued has completed once this commit arrives
     mma_commit(drain);
@@ -541,10 +602,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
   __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * BNMAX);
+    tmem_dealloc(tmem, TM_COLS);
   }
 }
-
 
 // K4: C = alpha * (sum of the FP32 partials of the k-splits) + beta * C.
 // The partials are added with error-free transformations (Knuth's two-sum,
@@ -554,28 +614,20 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
 // sum -- while running on the FP32 pipes: on GB300 FP64 arithmetic is slow
 // enough (about 1.1 TFLOP/s) that an FP64 reduction of tens of millions of
 // elements costs a large share of the contraction itself.
-// Grid: x over m (plus a stride loop), y over n, z over the split problems of
-// a batch; no integer division per element.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
+// Grid: x over m, y over n, both with stride loops; no integer division per
+// element.
 
-__global__ void k_reduce_partials(const DevProblem single, const DevProblem* probs,
-                                  const int32_t* split_probs) {
-  const DevProblem* dp = probs ? probs + split_probs[blockIdx.z] : nullptr;
-  const int64_t M = dp ? dp->m : single.m, N = dp ? dp->n : single.n;
-  const int S = dp ? dp->splits : single.splits;
-  const float* part = static_cast<const float*>(dp ? dp->partial : single.partial);
-  float* c = static_cast<float*>(dp ? dp->c : single.c);
-  const int64_t* rC = dp ? dp->sp.rC : single.sp.rC;
-  const int64_t* cC = dp ? dp->sp.cC : single.sp.cC;
-  const float alpha = (float)(dp ? dp->alpha : single.alpha);
-  const float beta = (float)(dp ? dp->beta : single.beta);
-  const int64_t plane = M * N;
-  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
-    const int64_t cn = __ldg(cC + n);
+// Columns [n0, n1) of one problem (the single-problem launch strides its
+// block rows over all columns; the batched one hands each block row one).
+__device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int64_t n1) {
+  const int64_t M = d.m, plane = M * d.n;
+  const int S = d.splits;
+  const float* part = static_cast<const float*>(d.partial);
+  float* c = static_cast<float*>(d.c);
+  const float alpha = (float)d.alpha, beta = (float)d.beta;
+  const bool stride_y = n1 - n0 > 1;
+  for (int64_t n = n0 + (stride_y ? blockIdx.y : 0); n < n1; n += stride_y ? gridDim.y : 1) {
+    const int64_t cn = __ldg(d.sp.cC + n);
     const float* pn = part + n * M;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
@@ -585,23 +637,46 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
         two_sum(hi, __ldg(pn + ks * plane + m), hi, e);
         lo = __fadd_rn(lo, e);
       }
-      float* cp = c + __ldg(rC + m) + cn;
-      // alpha * (hi + lo) [+ beta * C], the small term folded in first
-      float r = __fmaf_rn(alpha, hi, alpha * lo);
-      if (beta != 0.f) r = __fmaf_rn(beta, *cp, r);
-      *cp = r;
+      float* cp = c + __ldg(d.sp.rC + m) + cn;
+      // alpha * (hi + lo) [+ beta * C], the small term folded in first; C is
+      // only read when beta != 0
+      const float r = __fmaf_rn(alpha, hi, alpha * lo);
+      if (beta == 0.f) *cp = r;
+      else *cp = __fmaf_rn(beta, *cp, r);
     }
   }
 }
 
-template <int BNMAX, int NS>
+// One launch for the single problem, or for every split problem of a batch:
+// block row y walks the flattened list of (problem, column) pairs, found from
+// the prefix sums of the problems' column counts.
+__global__ void k_reduce_partials(const DevProblem single, const DevProblem* probs,
+                                  const int32_t* split_probs, const int64_t* col_prefix,
+                                  int32_t n_split) {
+  if (!probs) {
+    reduce_one(single, 0, single.n);
+    return;
+  }
+  const int64_t total = col_prefix[n_split];
+  for (int64_t r = blockIdx.y; r < total; r += gridDim.y) {
+    int lo = 0, hi = n_split;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (col_prefix[mid] <= r) lo = mid; else hi = mid;
+    }
+    const int64_t n = r - col_prefix[lo];
+    reduce_one(probs[split_probs[lo]], n, n + 1);
+  }
+}
+
+template <int NS>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc<BNMAX, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Lay<BNMAX, NS>::ALLOC);
+    cudaError_t e = cudaFuncSetAttribute(k_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Lay<NS>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -620,16 +695,18 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   mainloop_event_before(s);
-  k_tc<BNMAX, NS><<<(unsigned)grid, NT, Lay<BNMAX, NS>::ALLOC, s>>>(a);
+  k_tc<NS><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
     const int64_t mm = single_split ? q.single.m : q.max_m_split;
     const int64_t nn = single_split ? q.single.n : q.max_n_split;
-    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((mm + 255) / 256, 64));
-    const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nn, 32768));
-    dim3 grid2(bx, by, single_split ? 1u : (unsigned)q.n_split_probs);
-    k_reduce_partials<<<grid2, 256, 0, s>>>(q.single, q.probs, q.split_probs);
+    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((mm + 255) / 256, 16));
+    const unsigned by = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(single_split ? nn : q.split_cols, single_split ? 8192 : 16384));
+    k_reduce_partials<<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
+                                                   q.split_col_prefix,
+                                                   single_split ? 0 : q.n_split_probs);
     note_launch();
   }
   mainloop_event_after(s);
@@ -638,11 +715,10 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
 
 }  // namespace
 
-int tc_bn_max_for(int pieces, int bn) { return (pieces == 2 && bn > 128) ? 256 : 128; }
+int tc_bn_max() { return BNMAX; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
-  if (q.pieces == 3) return launch_cfg<128, 3>(q, s);
-  return q.bn_max == 256 ? launch_cfg<256, 2>(q, s) : launch_cfg<128, 2>(q, s);
+  return q.pieces == 3 ? launch_cfg<3>(q, s) : launch_cfg<2>(q, s);
 }
 
 }  // namespace tc

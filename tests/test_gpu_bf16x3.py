@@ -40,6 +40,7 @@ def f32(t):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n", [128, 256])
 def test_single_tile_integers_exact(mode, n):
+    # one tile (n = 128) and two (n = 256) with exactly representable sums
     g = torch.Generator().manual_seed(1)
     A = f32(torch.randint(-8, 9, (128, 32), generator=g).double())
     B = f32(torch.randint(-8, 9, (32, n), generator=g).double())
@@ -89,8 +90,8 @@ def test_random_contractions(seed, mode):
     assert norm_err(got, ref, mag) <= TOLS[mode]
 
 
-@pytest.mark.parametrize("mode,bn", [("bf16x3", 16), ("bf16x3", 48), ("bf16x3", 128),
-                                     ("bf16x3", 256), ("bf16x6", 32), ("bf16x6", 128)])
+@pytest.mark.parametrize("mode,bn", [("bf16x3", 16), ("bf16x3", 48), ("bf16x3", 112),
+                                     ("bf16x3", 128), ("bf16x6", 32), ("bf16x6", 128)])
 def test_forced_tile_widths(mode, bn, monkeypatch):
     # every tile width of the runtime-N tensor-core tile, on a ragged contraction
     monkeypatch.setenv("TC_FORCE_BN", str(bn))
@@ -171,3 +172,16 @@ def test_spiky_f32_full_size_sampled(mode):
 @pytest.mark.parametrize("mode", MODES)
 def test_grad_f32_forward_full_size_sampled(mode):
     sampled_check(W.SPECS["grad_f32"], seed=1003, mode=mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_long_contracted_range_chunked_accumulation(mode):
+    # k = 5000 runs as five accumulation chunks per tile, combined in float-float;
+    # integer data below 2^4 keeps every chunk sum exact, so the result is too
+    g = torch.Generator().manual_seed(21)
+    A = f32(torch.randint(-4, 5, (200, 5000), generator=g).double())
+    B = f32(torch.randint(-4, 5, (5000, 160), generator=g).double())
+    C0 = torch.zeros(200, 160, dtype=torch.float64)
+    got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij", mode)
+    ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+    assert np.array_equal(got, ref)
