@@ -450,7 +450,7 @@ def run_ours(args, ws, rank, local):
         peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
         prods = 3 if spec.mode == "bf16x3" else 6
         bound, unit, ach = "tensor", "TFLOP/s", prods * flops / (kms_max * 1e-3) / 1e12
-        kname = "k_bf16x3"
+        kname = "k_tc"
     value = ws * flops / (ms_max * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": ws, "steps": K,
