@@ -8,12 +8,14 @@ exactly two tensors with one extent.  d_I, d_J, d_P then satisfy
 d_P = (d(A)+d(B)-d(C))/2 and its two companions.
 
 ``normalize`` applies the five steps of Section 7.3 in the paper's order:
-  1. drop dimensions of length one;
-  2. fold dimensions of a bundle that are sequentially contiguous in every
-     tensor holding the bundle;
-  3. sort I and J by increasing stride in C;
-  4. if the first J dimension has stride 1 in C, swap A with B and I with J;
-  5. sort P by increasing stride in A.
+  1. every dimension whose length is 1 is discarded;
+  2. within a bundle, two dimensions merge into one when, in both tensors that
+     carry the bundle, the second one's stride equals the first one's stride
+     times its length;
+  3. the I dims and the J dims are ordered by their stride in C, smallest first;
+  4. when the first J dim then has unit stride in C, the roles of A and B are
+     exchanged, and with them those of I and J;
+  5. the P dims are ordered by their stride in A, smallest first.
 Readings (the paper does not say): sorting uses |stride| and is stable in the
 order the labels appear in C (I, J) or A (P); folding merges a pair (x, y)
 whenever s_y(T) == s_x(T) * n_x in both tensors of the bundle, scanning pairs
@@ -22,7 +24,7 @@ in label order and repeating until no pair merges.  The steps move no data.
 ``normalize(..., gpu_p_order=True)`` adds one step that is not the paper's:
 6. when A's smallest stride lies outside P (A is then read along its rows and
    the P order does not affect its access) but B's smallest stride lies in P,
-   re-sort P by increasing |stride| in B, so that B is read along its own unit
+   order P by |stride| in B instead (smallest first), so that B is read along its own unit
    stride.  Step 5's aim -- stride-1 access for A -- is unaffected.
 """
 from dataclasses import dataclass, field
@@ -129,13 +131,13 @@ def normalize(A, B, C, gpu_p_order: bool = False) -> Bundles:
     the five steps of Section 7.3 (names 'A' and 'B' in Dim.s refer to the
     tensors *after* any swap), plus step 6 above when ``gpu_p_order``."""
     I, J, P = _dims(A, B, C)
-    # 1. remove dimensions of length one
+    # 1. discard length-1 dims
     I = [d for d in I if d.n != 1]
     J = [d for d in J if d.n != 1]
     P = [d for d in P if d.n != 1]
-    # 2. fold sequentially contiguous dimensions
+    # 2. merge dims that are sequentially contiguous in both tensors
     I, J, P = _fold(I), _fold(J), _fold(P)
-    # 3. sort I and J by increasing stride in C
+    # 3. order I and J by stride in C
     I = sorted(I, key=lambda d: abs(d.s["C"]))
     J = sorted(J, key=lambda d: abs(d.s["C"]))
     # 4. swap A with B and I with J if the first J dimension has unit stride in C
@@ -146,7 +148,7 @@ def normalize(A, B, C, gpu_p_order: bool = False) -> Bundles:
         I = [Dim(d.labels, d.n, {"A": d.s["B"], "C": d.s["C"]}) for d in I]
         J = [Dim(d.labels, d.n, {"B": d.s["A"], "C": d.s["C"]}) for d in J]
         P = [Dim(d.labels, d.n, {"A": d.s["B"], "B": d.s["A"]}) for d in P]
-    # 5. sort P by increasing stride in A
+    # 5. order P by stride in A
     P = sorted(P, key=lambda d: abs(d.s["A"]))
     # 6. (not in the paper) let B's unit stride order P when A's lies outside P
     if gpu_p_order and P:

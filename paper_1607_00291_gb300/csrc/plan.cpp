@@ -3,13 +3,15 @@
 // Section 4 defines the bundles: labels of A and C form I, of B and C form J,
 // of A and B form P; each label lies in exactly two tensors with one length.
 // Section 7.3 gives the purely logical reordering applied here, in order:
-//   1. drop dims of length one;
-//   2. fold dims that are sequentially contiguous in every tensor of the bundle
-//      (x, y fold when s_y(T) == s_x(T) * n_x for both tensors T);
-//   3. sort I and J by increasing |stride| in C (stable in C's label order);
-//   4. if the first J dim has stride 1 in C, exchange A and B (and I and J),
-//      i.e. compute C^T = B^T A^T so that C's unit stride runs along M;
-//   5. sort P by increasing |stride| in A (stable in the original A's order).
+//   1. length-1 dims are discarded;
+//   2. dims x, y of a bundle merge when s_y(T) == s_x(T) * n_x in both tensors
+//      T carrying the bundle;
+//   3. I and J dims are ordered by |stride| in C, smallest first (stable in
+//      C's label order);
+//   4. when the first J dim has unit stride in C, A and B (and I and J) trade
+//      roles, i.e. C^T = B^T A^T is computed, so C's unit stride runs along M;
+//   5. P dims are ordered by |stride| in A, smallest first (stable in the
+//      original A's label order).
 // No data moves; the result only fixes the iteration order of the kernels.
 // One GPU-specific step follows the paper's five:
 //   6. if A's smallest |stride| lies outside P (A is read along its rows, so
@@ -176,7 +178,7 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
   drop1(I, nI);
   drop1(J, nJ);
   drop1(P, nP);
-  // step 2: fold sequentially contiguous dims
+  // step 2: merge sequentially contiguous dims
   fold(I, nI);
   fold(J, nJ);
   fold(P, nP);
