@@ -171,6 +171,8 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.ctas = sm_count();
     q.err = err_word();
+    // TC_FAULT=timeout: test hook that makes the kernel's first wait expire
+    if (const char* f = std::getenv("TC_FAULT")) q.fault = std::strcmp(f, "timeout") == 0 ? 1 : 0;
     return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
   }
   F64Launch f;

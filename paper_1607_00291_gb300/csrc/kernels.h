@@ -89,6 +89,8 @@ struct TcLaunch {
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
   int32_t* err;
+  int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
+              // expire (bounded), exercising the timeout and unwind path
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
 

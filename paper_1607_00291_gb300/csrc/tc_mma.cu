@@ -58,7 +58,7 @@ constexpr int CONV_W0 = NLOAD / 32;
 constexpr int EPI_W0 = (NLOAD + NCONV) / 32;
 constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
 constexpr int BAR_LOAD = 1, BAR_CONV = 2, BAR_EPI = 3;
-constexpr int KRING = 3;
+constexpr int KRING = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
 constexpr int BNMAX = 128;        // widest output tile (columns)
 constexpr int CHUNK_KT = 32;      // k-tiles per accumulation chunk (1024 terms)
@@ -126,6 +126,7 @@ struct Args {
   int64_t nitems;
   int64_t tiles_single;
   int32_t* err;
+  int fault;  // 1: injected timeout (see TcLaunch::fault)
 };
 
 __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err) {
@@ -180,20 +181,32 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 //  * row-contiguous operand: raw[BK][R].
 // The k side of every address comes from a small ring in shared memory that
 // holds, per k-tile, the 32 scatter entries of each operand along k and their
-// 8 block-scatter entries; loader thread i < KSLOT fetches entry i of the
-// k-tile two ahead while the current one is issued, so the latency of the
-// scatter vectors stays off the critical path.  The row side of every address
+// 8 block-scatter entries; loader thread i < KSLOT owns entry i: it keeps the
+// entries of the next four k-tiles in flight in registers and stores one
+// per k-tile into the ring, so the latency of the scatter vectors stays off
+// the critical path.  The row side of every address
 // comes from the row scatter entries of the tile, also in shared memory.
 // Consecutive threads walk each operand's unit-stride index.
-__device__ __forceinline__ int64_t kslot_fetch(int i, const DevProblem* d, int64_t k0,
-                                               int64_t kend) {
-  if (i < BK) return k0 + i < kend ? __ldg(d->sp.cA + k0 + i) : 0;
-  if (i < 2 * BK) return k0 + (i - BK) < kend ? __ldg(d->sp.rB + k0 + (i - BK)) : 0;
-  const int b = i - 2 * BK;  // block-scatter entries: k blocks of 4
-  const int64_t kb = (k0 >> 2) + (b & 7);
-  const bool ok = (kb << 2) < kend;
-  if (b < BK / 4) return ok ? __ldg(d->sp.cbsA + kb) : 0;
-  return ok ? __ldg(d->sp.rbsB + kb) : 0;
+// Entry `i` (< KSLOT) of the k-side ring: which vector it reads and where.
+struct KSlotSrc {
+  const int64_t* vec;
+  int off;
+  bool block;  // a block-scatter entry (k blocks of 4) rather than a scatter entry
+};
+
+__device__ __forceinline__ KSlotSrc kslot_src(int i, const DevProblem* d) {
+  if (i < BK) return {d->sp.cA, i, false};
+  if (i < 2 * BK) return {d->sp.rB, i - BK, false};
+  if (i < 2 * BK + BK / 4) return {d->sp.cbsA, i - 2 * BK, true};
+  return {d->sp.rbsB, i - 2 * BK - BK / 4, true};
+}
+
+__device__ __forceinline__ int64_t kslot_fetch(const KSlotSrc& src, int64_t k0, int64_t kend) {
+  if (src.block) {
+    const int64_t kb = (k0 >> 2) + src.off;
+    return (kb << 2) < kend ? __ldg(src.vec + kb) : 0;
+  }
+  return k0 + src.off < kend ? __ldg(src.vec + k0 + src.off) : 0;
 }
 
 template <int R>
@@ -375,15 +388,28 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
-      if (t < KSLOT) {  // k ring: entries of k-tiles 0 and 1 of this item
-        for (int64_t kt = 0; kt < 2 && kt < it.KT; ++kt)
-          kring[(kt % KRING) * KSLOT + t] = kslot_fetch(t, d, it.kbeg + kt * BK, it.kend);
+      // k ring: entry t of k-tile 0 now, of k-tiles 1..4 in flight in p0..p3
+      KSlotSrc src{nullptr, 0, false};
+      int64_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+      if (t < KSLOT) {
+        src = kslot_src(t, d);
+        auto kf = [&](int64_t kt) { return kt < it.KT ? kslot_fetch(src, it.kbeg + kt * BK, it.kend) : 0; };
+        const int64_t v0 = kf(0);
+        p0 = kf(1);
+        p1 = kf(2);
+        p2 = kf(3);
+        p3 = kf(4);
+        if (it.KT > 0) kring[t] = v0;
       }
       bar_sync(BAR_LOAD, NLOAD);
       for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
-        int64_t ahead = 0;
-        const bool fetch = t < KSLOT && kt + 2 < it.KT;
-        if (fetch) ahead = kslot_fetch(t, d, it.kbeg + (kt + 2) * BK, it.kend);
+        if (t < KSLOT) {  // publish k-tile kt+1, fetch k-tile kt+5
+          if (kt + 1 < it.KT) kring[((kt + 1) % KRING) * KSLOT + t] = p0;
+          p0 = p1;
+          p1 = p2;
+          p2 = p3;
+          p3 = kt + 5 < it.KT ? kslot_fetch(src, it.kbeg + (kt + 5) * BK, it.kend) : 0;
+        }
         const int s = (int)(g % RS);
         const bool ok = mbar_wait(&raw_empty[s], (uint32_t)(((g / RS) & 1) ^ 1), abort);
         if (!ok) record_timeout(abort, a.err);
@@ -396,12 +422,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
                             slot + 2 * BK + BK / 4, k0, it.kend, bkc);
           cp_async_arrive(&raw_full[s]);
         }
-        if (fetch) kring[((kt + 2) % KRING) * KSLOT + t] = ahead;
-        // slot kt+2 now complete and slot kt free for reuse; a timeout anywhere
+        // slot kt+1 now complete and slot kt free for reuse; a timeout anywhere
         // makes every loader leave together
         if (bar_or(BAR_LOAD, NLOAD, !ok)) break;
       }
     }
+    // no copy into shared memory may outlive the CTA (matters only after an abort)
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
   } else if (warp < EPI_W0) {
     // ---- converters ----
     const int t = tid - NLOAD;
@@ -542,6 +569,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
     const uint32_t base = smem_u32(smem + Ly::MMA0);
     int64_t g = 0, gc = 0;
     bool failed = false;
+    if (a.fault == 1) {
+      // injected failure: a bounded wait (about 10 ms) on a barrier nothing
+      // arrives on yet; it expires, and the CTA unwinds through the abort path
+      if (!mbar_wait(drain, 0, abort, 20000000LL)) {
+        record_timeout(abort, a.err);
+        failed = true;
+      }
+    }
     for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
       const Item it = get_item(a, sProb, w);
       const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
@@ -685,6 +720,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   a.probs = q.probs;
   a.items = q.items;
   a.err = q.err;
+  a.fault = q.fault;
   if (q.probs) {
     a.nitems = q.nitems;
     a.tiles_single = 1;
