@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--workload", default="cc4x4_f64", choices=sorted(W.SPECS) + ["batch512"])
     ap.add_argument("--mode", choices=["f64", "bf16x3", "bf16x6"], default=None,
                     help="override the workload's arithmetic")
+    ap.add_argument("--access", choices=["block", "scatter", "box"], default="block",
+                    help="tensor-core operand access: block-scatter gathers (block), element "
+                         "gathers (scatter) or TMA boxes where tiles are boxes (box)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -452,15 +455,20 @@ def run_ours(args, ws, rank, local):
         bound, unit, ach = "tensor", "TFLOP/s", prods * flops / (kms_max * 1e-3) / 1e12
         kname = "k_tc"
     value = ws * flops / (ms_max * 1e-3) / 1e12
+    extra = {"l2": f"inputs larger than L2 (A = {host_bytes(spec)[0] / 1e6:.1f} MB > {L2_BYTES / 1e6:.0f} MB)",
+             "parallelism": f"replicas x{ws}"}
+    if spec.mode != "f64":
+        fa, fb = tc.box_access(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.mode)
+        how = {"block": "block-scatter gather", "scatter": "element gather", "box": "block-scatter gather"}
+        extra["operand_access"] = (f"{args.access}: A {'TMA box' if fa else how[args.access]}, "
+                                   f"B {'TMA box' if fb else how[args.access]}")
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": ws, "steps": K,
         "warmup": warm, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if spec.mode == "f64" else f"f32 data, {spec.mode} products, f32 accumulate",
         "data": "synthetic (seeded uniform[-1,1], column-major; shapes of the paper's CC-style contractions)",
-        "config": workload_config(spec, {
-            "l2": f"inputs larger than L2 (A = {host_bytes(spec)[0] / 1e6:.1f} MB > {L2_BYTES / 1e6:.0f} MB)",
-            "parallelism": f"replicas x{ws}"}),
+        "config": workload_config(spec, extra),
         "clocks": clk,
         "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -534,6 +542,7 @@ def main():
     else:
         if not torch.cuda.is_available():
             raise SystemExit("bench.py --impl ours needs a GPU")
+        tc.set_access(args.access)
         run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist

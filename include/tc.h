@@ -170,6 +170,41 @@ TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);
 TC_API int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream);
 TC_API void tc_plan_destroy(tc_plan* plan);
 
+/* ---- operand access of the tensor-core mainloop ------------------------------- */
+
+/* How the tensor-core mainloop (BF16X3 / BF16X6 modes) reads A and B into
+ * shared memory.  Results are identical, bit for bit, in every setting; only
+ * the speed differs.
+ * TC_ACCESS_BLOCK (default): gathers through the scatter vectors (Section
+ * 6.1), 16 bytes at a time wherever the block-scatter vectors (Section 6.2)
+ * show four consecutive elements at unit stride: the paper's block-scatter
+ * form.
+ * TC_ACCESS_SCATTER: the same gathers one element at a time, ignoring the
+ * block-scatter vectors: the paper's plain scatter-matrix form, kept for
+ * comparison.
+ * TC_ACCESS_BOX: an operand whose tile rows and k-tile form one box in its
+ * own dims -- its unit-stride dim leads the row or the k bundle, the bundle
+ * dims before the one a tile ends in are covered whole, and that dim's tile
+ * extent divides its length (the last dim of a bundle may run past its end),
+ * at most 5 dims, FP32 strides that are multiples of 4 elements, 16-byte
+ * aligned data -- is loaded with one TMA box per tile (a regular block in the
+ * sense of Section 6.2, in several dims at once, read along the unit stride
+ * as Section 7.3 prefers, with no scatter entry); other operands as BLOCK.
+ * The FP64 mode always uses the BLOCK form.  The setting is process-wide and
+ * read when a contraction is issued or a plan is created.  Returns the
+ * previous setting, or TC_ERR_ARG for an unknown value. */
+typedef enum { TC_ACCESS_BLOCK = 0, TC_ACCESS_SCATTER = 1, TC_ACCESS_BOX = 2 } tc_access;
+TC_API int tc_set_access(int access);
+
+/* Report how tc_contract would read A and B (matrix roles, as in
+ * tc_plan_describe) in tensor-core mode `mode` with the current setting:
+ * *a_box, *b_box = 1 for a TMA box per tile, 0 for the scatter gather.  Host
+ * only; without a CUDA driver it reports the eligibility rules alone (the
+ * driver may still refuse a tensor map, and the operand is then gathered).
+ * TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
+TC_API int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                         const tc_tensor* C, int32_t* a_box, int32_t* b_box);
+
 /* ---- scatter vectors (K1 on its own; used by the tests) ------------------------ */
 
 /* Number of int64 entries tc_build_scatter writes for this problem and block

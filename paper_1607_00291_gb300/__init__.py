@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import TcError  # noqa: F401
 
 __all__ = ["contract", "workspace_size", "plan_describe", "build_scatter", "device_error",
-           "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
+           "set_access", "access", "box_access", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
 
 _MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3, "bf16x6": L.TC_MODE_BF16X6}
 
@@ -106,6 +106,57 @@ def plan_describe(A, labA, B, labB, C, labC) -> dict:
                 P=bundle(info.nP, info.P_len, info.P_sA, info.P_sB, info.P_labels),
                 a_k_contig=bool(info.a_k_contig), b_k_contig=bool(info.b_k_contig),
                 c_m_contig=bool(info.c_m_contig))
+
+
+_ACCESS = {"block": L.TC_ACCESS_BLOCK, "scatter": L.TC_ACCESS_SCATTER, "box": L.TC_ACCESS_BOX}
+
+
+def set_access(access: str) -> str:
+    """Operand access of the tensor-core mainloop, process-wide (results are
+    identical in every setting): "block" (default) gathers through the
+    scatter vectors, 16 bytes at a time where the block-scatter vectors allow;
+    "scatter" gathers element by element (the plain scatter-matrix form);
+    "box" loads every operand whose tiles are boxes in its own dims with TMA
+    and block-gathers the rest.  Returns the previous setting."""
+    if access not in _ACCESS:
+        raise ValueError(f"access must be one of {sorted(_ACCESS)}")
+    prev = L.lib().tc_set_access(_ACCESS[access])
+    if prev < 0:
+        L.check(prev, "tc_set_access")
+    return {v: k for k, v in _ACCESS.items()}[prev]
+
+
+class access:
+    """Context manager: ``with access("box"): ...`` restores the previous setting."""
+
+    def __init__(self, mode: str):
+        self.mode = mode
+
+    def __enter__(self):
+        self.prev = set_access(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        set_access(self.prev)
+        return False
+
+
+def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):
+    """(a_box, b_box): whether tc_contract in tensor-core `mode` loads the
+    matrix-role operands A and B as TMA boxes (True) or gathers them (False)
+    under the current access setting (only "box" takes boxes).  Host only; A, B, C are tensors or
+    (shape, strides) pairs (pairs are taken as 16-byte aligned)."""
+    keep = []
+
+    def d(x, lab):
+        if isinstance(x, torch.Tensor):
+            return L.make_tensor(tuple(x.shape), x.stride(), lab, x.data_ptr(), keep)
+        return L.make_tensor(x[0], x[1], lab, 0, keep)
+
+    a, b = L.c_i32(0), L.c_i32(0)
+    L.check(L.lib().tc_box_access(L.TC_F32, _mode_code(mode), d(A, labA), d(B, labB), d(C, labC),
+                                  a, b), "tc_box_access")
+    return bool(a.value), bool(b.value)
 
 
 def build_scatter(A, labA, B, labB, C, labC, b: int = 4):

@@ -168,6 +168,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     d.tiles_n = (int32_t)((L.n + d.bn - 1) / d.bn);
     d.splits = w.tcc.splits;
     d.kps = w.tcc.kps;
+    plan_access(L, d, q.tm);
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.ctas = sm_count();
     q.err = err_word();
@@ -251,6 +252,28 @@ int tc_contract(tc_dtype dtype, tc_mode mode, double alpha, const tc_tensor* A,
   if ((rc = plan_checked(dtype, A, B, C, &p)) != TC_OK) return rc;
   return run_planned(dtype, mode, alpha, beta, p, workspace, ws_bytes,
                      static_cast<cudaStream_t>(stream));
+}
+
+int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                  const tc_tensor* C, int32_t* a_box, int32_t* b_box) {
+  if (!a_box || !b_box) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  if (mode == TC_MODE_F64) return TC_ERR_UNSUPPORTED;
+  Planned p;
+  if ((rc = plan_problem(A, B, C, &p)) != TC_OK) return rc;
+  DevProblem d;
+  std::memset(&d, 0, sizeof d);
+  d.a = p.a;
+  d.b = p.b;
+  d.a_kc = p.info.a_k_contig;
+  d.b_kc = p.info.b_k_contig;
+  d.bn = ws_layout(p, mode).tcc.bn;
+  CUtensorMap maps[2];
+  plan_access(p.L, d, box_encoder_available() ? maps : nullptr);
+  *a_box = d.boxA.rank > 0;
+  *b_box = d.boxB.rank > 0;
+  return TC_OK;
 }
 
 int tc_scatter_count(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, int32_t b,

@@ -131,6 +131,7 @@ float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, 
   d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
   d.splits = c.splits;
   d.kps = c.kps;
+  plan_access(p.L, d, q.tm);
   q.pieces = pieces;
   q.ctas = 1;
   q.err = err_word();
@@ -231,6 +232,7 @@ struct tc_plan {
   int64_t max_m_split = 0, max_n_split = 0;
   int pieces = 2;
   int64_t ctas = 152;
+  bool any_box = false;  // some problem loads an operand as TMA boxes
 };
 
 namespace {
@@ -390,6 +392,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const size_t o_split = take(sizeof(int32_t) * std::max<int32_t>(1, pl->n_split));
   const size_t o_scols = take(sizeof(int64_t) * (pl->n_split + 1));
   const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
+  const size_t o_tmap = take(sizeof(CUtensorMap) * 2 * std::max(np, 1));
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -410,6 +413,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
 
   std::vector<Layout> lay(np);
   std::vector<DevProblem> dp(np);
+  std::vector<CUtensorMap> maps(2 * (size_t)np);
+  const CUtensorMap* d_maps = reinterpret_cast<const CUtensorMap*>(base + o_tmap);
   for (int i = 0; i < np; ++i) {
     const Planned& p = pl->planned[i];
     const ProbCfg& c = pl->cfg[i];
@@ -432,6 +437,11 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
     d.splits = c.splits;
     d.kps = c.kps;
+    if (!f64) {
+      plan_access(p.L, d, &maps[2 * (size_t)i]);
+      d.tmaps = d_maps + 2 * (size_t)i;
+      pl->any_box = pl->any_box || d.boxA.rank > 0 || d.boxB.rank > 0;
+    }
   }
   auto up = [](void* dst, const void* src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -441,7 +451,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       !up(pl->d_probs, dp.data(), sizeof(DevProblem) * np) ||
       !up(pl->d_items, items.data(), sizeof(WorkItem) * items.size()) ||
       !up(pl->d_split, splitp.data(), sizeof(int32_t) * splitp.size()) ||
-      !up(pl->d_split_cols, scols.data(), sizeof(int64_t) * scols.size()))
+      !up(pl->d_split_cols, scols.data(), sizeof(int64_t) * scols.size()) ||
+      !up(base + o_tmap, maps.data(), sizeof(CUtensorMap) * maps.size()))
     return TC_ERR_CUDA;
   return TC_OK;
 }
@@ -514,6 +525,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
+    q.any_box = plan->any_box ? 1 : 0;
     q.err = err_word();
     e = launch_tc(q, s);
   }

@@ -1,6 +1,7 @@
 // Launch wrappers of the device kernels (one translation unit each).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
 #include "tc_internal.h"
@@ -48,6 +49,35 @@ int f64_tile_m();
 int f64_tile_n();
 int f64_tile_k();
 
+// Access plan of one operand of the tensor-core mainloop (Section 7.3's
+// preference for unit-stride access, in the GPU's terms).  When the rows of a
+// tile and a k-tile of the operand form a box in the operand's own dims -- its
+// unit-stride dim leads one bundle, every bundle dim before the one the tile
+// ends in is covered whole, and that dim's tile extent divides its length (the
+// bundle's last dim may run past its end: the box reads zeros there) -- the
+// tile is one TMA box load: like a regular block of Section 6.2, but in
+// several dims at once, every address follows from the box's corner and the
+// operand's own strides, so no scatter entry is read.  Otherwise (rank == 0)
+// the loaders gather it through its scatter vectors.
+struct BoxAccess {
+  int32_t rank;     // dims of the tensor map, 2..5 (0: gather)
+  int32_t nfirst;   // dims of the bundle that leads the map (the one holding the unit stride)
+  int32_t kfirst;   // that bundle is the k bundle (else the row bundle)
+  int32_t bytes;    // bytes one box delivers
+  int32_t len[5];   // extents in map order: each bundle fastest dim first
+  int32_t klast;    // map index of the k bundle's last dim
+  int32_t kstep_dim, kstep;  // the next k-tile's box: coordinate kstep_dim + kstep,
+                             // then carries (the dims before it are covered whole)
+};
+// Fill d.boxA / d.boxB / d.elem_gather for the tensor-core mainloop from the
+// process-wide access setting (tc_set_access) and the problem's layout,
+// operands, access flags and tile width, and encode the tensor maps of the
+// operands that take boxes into maps[0] (A) and maps[1] (B); with maps ==
+// null only the eligibility is decided.  Defined in access.cu.
+struct DevProblem;
+void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps);
+bool box_encoder_available();  // the driver's tensor-map encoder could be found
+
 // One planned contraction as the persistent kernels see it: a kernel
 // parameter for a single call, an array in device memory for a batch.
 struct DevProblem {
@@ -63,8 +93,12 @@ struct DevProblem {
   int32_t tiles_n;  // output tiles along n
   int32_t bn;       // n-width of an output tile (tensor-core path: 16..256, step 16)
   int32_t splits;   // pieces of the contracted range
-  int32_t pad0;
+  int32_t elem_gather;  // tensor-core path: gather element by element, ignoring the
+                        // block-scatter vectors (the plain scatter-matrix form)
   int64_t kps;      // contracted indices per split (a multiple of the k-tile)
+  BoxAccess boxA, boxB;       // tensor-core path: TMA boxes or gathers per operand
+  const CUtensorMap* tmaps;   // batch: the two tensor maps in device memory (a single
+                              // call passes them as kernel parameters instead)
 };
 
 // One unit of work of a batch: an output tile of a problem over one k-split.
@@ -76,6 +110,7 @@ struct WorkItem {
 // 3 -> BF16x6), persistent over work items, chunked FP32 accumulation summed
 // in float-float; K4 reduces the partials of k-splits (two-sum FP32).
 struct TcLaunch {
+  CUtensorMap tm[2];          // tensor maps of the single problem's box operands
   DevProblem single;          // the problem of a single call (probs == null)
   const DevProblem* probs;    // batch descriptors (device), or null
   const WorkItem* items;      // batch work list (device), or null
@@ -88,6 +123,7 @@ struct TcLaunch {
   int64_t split_cols;         // batch: total columns of the split problems
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
+  int32_t any_box;            // batch: some problem loads an operand as TMA boxes
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path

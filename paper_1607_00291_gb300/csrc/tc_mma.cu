@@ -82,7 +82,8 @@ struct Lay {
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
   static constexpr int NBARS = 2 * RS + 2 * MS + 5;
   static constexpr int MISC = BARS + NBARS * 8;
-  static constexpr int END = MISC + 16;
+  static constexpr int BOXS = MISC + 16;  // BoxState of the loaders' thread 0
+  static constexpr int END = BOXS + 64;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
   static_assert(BNMAX % NEPI == 0 && BM == NEPI && NLOAD % 32 == 0 && BK % (NLOAD / 32) == 0,
@@ -120,6 +121,7 @@ __device__ __forceinline__ void split8_store(float (&v)[8], uint8_t* piece0, int
 }
 
 struct Args {
+  CUtensorMap tm[2];  // tensor maps of the single problem's box operands (A, B)
   DevProblem single;
   const DevProblem* probs;
   const WorkItem* items;
@@ -209,16 +211,72 @@ __device__ __forceinline__ int64_t kslot_fetch(const KSlotSrc& src, int64_t k0, 
   return k0 + src.off < kend ? __ldg(src.vec + k0 + src.off) : 0;
 }
 
+// ---- box loads (operands whose tiles are TMA boxes) ------------------------------
+// Thread 0 of the loaders issues them; its state lives in shared memory so
+// that it takes no registers from the gather loop of the other loaders.
+struct BoxState {
+  int32_t c[2][5];  // coordinates of the next box of A and of B (map order)
+  int32_t pad[2];
+  long long g_box;  // the last k-tile box loads were issued for (-1: none)
+  long long g_iss;  // the last k-tile thread 0 issued any loads for
+};
+static_assert(sizeof(BoxState) <= 64, "box state slot");
+
+// Coordinates of the box whose rows start at linear row r0 and whose k-tile
+// starts at linear k index k0: the mixed-radix digits of r0 and k0 over the
+// two bundles' extents (the last dim of each bundle keeps the quotient, which
+// may point past its end: the box reads zeros there).  Once per work item.
+__device__ __noinline__ void box_coords(const BoxAccess* x, uint32_t r0, uint32_t k0, int32_t* c) {
+  uint32_t v1 = x->kfirst ? k0 : r0, v2 = x->kfirst ? r0 : k0;
+  const int rank = x->rank, nf = x->nfirst;
+  for (int i = 0; i < rank; ++i) {
+    const bool first = i < nf;
+    const bool lastdim = i == nf - 1 || i == rank - 1;
+    const uint32_t v = first ? v1 : v2;
+    const uint32_t len = (uint32_t)x->len[i];
+    c[i] = (int32_t)(lastdim ? v : v % len);
+    const uint32_t q = lastdim ? 0u : v / len;
+    if (first) v1 = q; else v2 = q;
+  }
+}
+
+// The box loads of one k-tile into the raw stage whose barrier is `bar`, then
+// the coordinates of the next k-tile's boxes (one step along the dim the
+// k-tile ends in, carried into the k bundle's higher dims; the step divides
+// that dim's extent, so a wrap lands exactly on 0).  The transaction count
+// goes up before thread 0's own arrival on `bar`, so the phase cannot
+// complete before the boxes have landed.
+__device__ __noinline__ void box_issue(const DevProblem* d, const CUtensorMap* maps,
+                                       uint32_t rawA, uint32_t rawB, uint64_t* bar,
+                                       BoxState* bs) {
+  const BoxAccess* x[2] = {&d->boxA, &d->boxB};
+  const uint32_t ra = (uint32_t)x[0]->rank, rb = (uint32_t)x[1]->rank;
+  mbar_expect_tx(bar, (ra ? (uint32_t)x[0]->bytes : 0u) + (rb ? (uint32_t)x[1]->bytes : 0u));
+  for (int o = 0; o < 2; ++o) {
+    const BoxAccess* b = x[o];
+    if (b->rank == 0) continue;
+    int32_t* c = bs->c[o];
+    tma_load(o ? rawB : rawA, maps + o, c, b->rank, bar);
+    int i = b->kstep_dim;
+    c[i] += b->kstep;
+    while (i < b->klast && c[i] >= b->len[i]) {
+      c[i] = 0;
+      ++i;
+      c[i] += 1;
+    }
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void load_panel(int t, uint32_t raw, const float* __restrict__ base,
                                            const int64_t* rowsc, int rows_valid,
                                            const int64_t* ks, const int64_t* kbs, int64_t k0,
-                                           int64_t kend, bool kcontig) {
+                                           int64_t kend, bool kcontig, bool vec_ok) {
   if (kcontig) {
     constexpr int RSTEP = NLOAD / 8;  // rows per pass of the loaders
     const int q4 = t & 7;
     const int64_t kq = k0 + 4 * q4;
-    const bool vec = kq + 3 < kend && kbs[q4] == 1;
+    const bool vec = vec_ok && kq + 3 < kend && kbs[q4] == 1;
     int64_t ko[4];
     uint32_t valid = 0;
 #pragma unroll
@@ -252,7 +310,7 @@ __device__ __forceinline__ void load_panel(int t, uint32_t raw, const float* __r
       const int r0 = 4 * ((t & 31) + 32 * u);
       if (r0 >= rows_valid) continue;
       const int64_t o0 = rowsc[r0];
-      const bool quad = r0 + 3 < rows_valid && rowsc[r0 + 1] == o0 + 1 &&
+      const bool quad = vec_ok && r0 + 3 < rows_valid && rowsc[r0 + 1] == o0 + 1 &&
                         rowsc[r0 + 2] == o0 + 2 && rowsc[r0 + 3] == o0 + 3;
 #pragma unroll
       for (int v = 0; v < BK / KSTEP; ++v) {
@@ -280,7 +338,7 @@ __device__ __forceinline__ void load_panel(int t, uint32_t raw, const float* __r
 // rows of one k-chunk, so its 16-byte core-matrix row stores are contiguous.
 template <int R, int NS>
 __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t* piece0,
-                                              bool kcontig) {
+                                              bool kcontig, int rstride) {
   constexpr int TASKS = R * BK / 8;
   constexpr int PBY = R * BK * 2;
   const float* rf = reinterpret_cast<const float*>(raw);
@@ -297,13 +355,15 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
       v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = rf[(8 * q + j) * R + r];
+      for (int j = 0; j < 8; ++j) v[j] = rf[(8 * q + j) * rstride + r];
     }
     split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
   }
 }
-template <int NS>
-__global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
+// BOX: some operand of some work item is loaded as TMA boxes (a separate
+// instantiation, so that the gather-only kernel carries none of that code).
+template <int NS, bool BOX>
+__global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   using Ly = Lay<NS>;
   constexpr int RS = Ly::RS, MS = Ly::MS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -359,6 +419,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
     // ---- loaders ----
     const int t = tid;
     int64_t g = 0;  // k-tiles staged by this CTA so far
+    BoxState* bst = reinterpret_cast<BoxState*>(smem + Ly::BOXS);
+    if (BOX && t == 0) {
+      bst->g_box = -1;
+      bst->g_iss = -1;
+    }
     // row scatter entries (A rows then B rows) of the next item, fetched one item ahead
     constexpr int NR = (BM + BNMAX + NLOAD - 1) / NLOAD;
     int64_t pre[NR];
@@ -388,6 +453,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
+      const bool boxA = BOX && d->boxA.rank > 0, boxB = BOX && d->boxB.rank > 0;
+      const bool vec_ok = d->elem_gather == 0;
+      if (BOX && t == 0) {
+        if (boxA) box_coords(&d->boxA, (uint32_t)it.m0, (uint32_t)it.kbeg, bst->c[0]);
+        if (boxB) box_coords(&d->boxB, (uint32_t)it.n0, (uint32_t)it.kbeg, bst->c[1]);
+      }
       // k ring: entry t of k-tile 0 now, of k-tiles 1..4 in flight in p0..p3
       KSlotSrc src{nullptr, 0, false};
       int64_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
@@ -417,18 +488,50 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
           const uint32_t raw = smem_u32(smem + Ly::RAW0 + s * Ly::RAW_STAGE);
           const int64_t* slot = kring + (kt % KRING) * KSLOT;
           const int64_t k0 = it.kbeg + kt * BK;
-          load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc);
-          load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
-                            slot + 2 * BK + BK / 4, k0, it.kend, bkc);
+          if (!(boxA || boxB)) {  // both gathered: one block, so the two panels interleave
+            load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
+                           vec_ok);
+            load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
+                              slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
+          } else if constexpr (BOX) {
+            if (t == 0) {
+              box_issue(d, a.probs ? d->tmaps : a.tm, raw, raw + Ly::RAW_A, &raw_full[s], bst);
+              bst->g_box = g;
+            }
+            if (!boxA)
+              load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
+                             vec_ok);
+            if (!boxB)
+              load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
+                                slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
+          }
           cp_async_arrive(&raw_full[s]);
+          if (BOX && t == 0) bst->g_iss = g;
         }
         // slot kt+1 now complete and slot kt free for reuse; a timeout anywhere
         // makes every loader leave together
         if (bar_or(BAR_LOAD, NLOAD, !ok)) break;
       }
     }
-    // no copy into shared memory may outlive the CTA (matters only after an abort)
+    // no copy into shared memory may outlive the CTA (matters only after an
+    // abort): the cp.async gathers, and the box loads of the stages still
+    // filling.  Thread 0 issued every k-tile up to g_iss; a fill that a later
+    // issued fill of the same stage followed was consumed before that one
+    // began, so only the k-tiles after g_iss - RS can be in flight, and
+    // thread 0 waits for the phases of those up to its last box.  A box load
+    // lands within microseconds of its issue whatever the other roles do; the
+    // wait is bounded (about 10 ms per stage) because after an abort a phase
+    // can miss the arrival of a loader that gave up on that k-tile.
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const long long g_box = BOX ? bst->g_box : -1, g_iss = BOX ? bst->g_iss : -1;
+    if (BOX && t == 0 && g_box >= 0 && g_box > g_iss - RS) {
+      for (long long gi = g_iss - RS + 1 > 0 ? g_iss - RS + 1 : 0; gi <= g_box; ++gi) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&raw_full[gi % RS], (uint32_t)((gi / RS) & 1)) &&
+               clock64() - t0 < 20000000LL) {
+        }
+      }
+    }
   } else if (warp < EPI_W0) {
     // ---- converters ----
     const int t = tid - NLOAD;
@@ -437,6 +540,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
       if (bar_or(BAR_CONV, NCONV, *abort)) break;  // uniform exit
       const Item it = get_item(a, sProb, w);
       const bool akc = it.d->a_kc, bkc = it.d->b_kc;
+      // a row-contiguous B box holds k-rows of bn floats; the gather's k-rows hold BNMAX
+      const int rsB = BOX && it.d->boxB.rank > 0 ? it.d->bn : BNMAX;
       for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
         const int rs = (int)(g % RS), ms = (int)(g % MS);
         if (!mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) ||
@@ -446,8 +551,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const Args a) {
         }
         const uint8_t* raw = smem + Ly::RAW0 + rs * Ly::RAW_STAGE;
         uint8_t* st = smem + Ly::MMA0 + ms * Ly::MMA_STAGE;
-        convert_panel<BM, NS>(t, raw, st, akc);
-        convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc);
+        convert_panel<BM, NS>(t, raw, st, akc, BM);
+        if (!BOX || rsB == BNMAX)  // the common k-row pitch as a constant: immediate offsets
+          convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, BNMAX);
+        else
+          convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, rsB);
         fence_proxy_async_smem();
         mbar_arrive(&mma_full[ms]);
         mbar_arrive(&raw_empty[rs]);
@@ -704,18 +812,20 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
   }
 }
 
-template <int NS>
+template <int NS, bool BOX>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Lay<NS>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   Args a;
+  a.tm[0] = q.tm[0];
+  a.tm[1] = q.tm[1];
   a.single = q.single;
   a.probs = q.probs;
   a.items = q.items;
@@ -731,7 +841,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   mainloop_event_before(s);
-  k_tc<NS><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
+  k_tc<NS, BOX><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
@@ -754,7 +864,9 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
 int tc_bn_max() { return BNMAX; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
-  return q.pieces == 3 ? launch_cfg<3>(q, s) : launch_cfg<2>(q, s);
+  const bool box = q.probs ? q.any_box != 0 : (q.single.boxA.rank > 0 || q.single.boxB.rank > 0);
+  if (q.pieces == 3) return box ? launch_cfg<3, true>(q, s) : launch_cfg<3, false>(q, s);
+  return box ? launch_cfg<2, true>(q, s) : launch_cfg<2, false>(q, s);
 }
 
 }  // namespace tc

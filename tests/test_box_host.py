@@ -1,0 +1,110 @@
+"""Host-side access plan of the tensor-core mainloop (no GPU needed): which
+operands take one TMA box per tile and which are gathered through scatter
+vectors.  A tile of T consecutive linear indices of a bundle is a box when it
+covers the bundle's leading dims whole and a divisor-sized run of the next
+one (the bundle's last dim may run past its end); the operand's unit-stride
+dim must lead the bundle the access flag names; at most 5 dims; FP32 strides
+multiples of 4 elements."""
+import pytest
+
+import paper_1607_00291_gb300 as tc
+from paper_1607_00291_gb300 import _lib as L
+from paper_1607_00291_gb300 import workloads as W
+
+
+def cm(shape):
+    st, s = [], 1
+    for n in shape:
+        st.append(s)
+        s *= n
+    return tuple(shape), tuple(st)
+
+
+def boxes(labA, labB, labC, ext, mode="bf16x3"):
+    sh = lambda lab: [ext[c] for c in lab]  # noqa: E731
+    with tc.access("box"):
+        return tc.box_access(cm(sh(labA)), labA, cm(sh(labB)), labB, cm(sh(labC)), labC, mode)
+
+
+def test_benchmark_workloads_take_boxes():
+    for name in ("spiky_f32", "grad_f32"):
+        sp = W.SPECS[name]
+        assert boxes(sp.labA, sp.labB, sp.labC, sp.ext) == (True, True), name
+
+
+def test_gradient_contractions():
+    sp = W.SPECS["grad_f32"]
+    # dA = dC x_J B: B's unit-stride dim m is not the first of its bundle
+    # (J is sorted by dA's strides: l before m), so B is gathered
+    assert boxes(sp.labC, sp.labB, sp.labA, sp.ext) == (True, False)
+    # dB = A x_I dC
+    assert boxes(sp.labA, sp.labC, sp.labB, sp.ext) == (True, True)
+
+
+def test_only_the_box_setting_takes_boxes():
+    sp = W.SPECS["spiky_f32"]
+    sh = lambda lab: cm([sp.ext[c] for c in lab])  # noqa: E731
+    args = (sh(sp.labA), sp.labA, sh(sp.labB), sp.labB, sh(sp.labC), sp.labC)
+    assert tc.set_access("block") == "block"  # the default
+    for acc in ("block", "scatter"):
+        with tc.access(acc):
+            assert tc.box_access(*args) == (False, False)
+    with tc.access("box"):
+        assert tc.box_access(*args) == (True, True)
+    assert tc.set_access("block") == "block"
+
+
+def test_tile_structure_rules():
+    # C keeps j between the row dims, so the planner cannot fold them
+    # rows: I = (a, b) with a = 24 does not tile 128 rows into a box
+    ext = dict(a=24, b=16, p=64, j=128)
+    assert boxes("pab", "pj", "ajb", ext)[0] is False
+    # a = 32 and b divisible by 128 / 32 = 4: a box (32 x 4)
+    ext = dict(a=32, b=8, p=64, j=128)
+    assert boxes("pab", "pj", "ajb", ext)[0] is True
+    # b = 6 is not a multiple of 4 and not the last row dim (c follows)
+    ext = dict(a=32, b=6, c=2, p=64, j=64)
+    assert boxes("pacb", "pj", "ajbc", ext)[0] is False
+    # ... but as the last row dim it may run past its end
+    ext = dict(a=32, b=6, p=64, j=64)
+    assert boxes("pab", "pj", "ajb", ext)[0] is True
+
+
+def test_k_tile_rules():
+    # k-contiguous A needs the unit-stride k dim to fill the 32-wide k-tile:
+    # a multiple of 32, or the only k dim (its end read as zeros)
+    assert boxes("pi", "pj", "ij", dict(p=48, i=128, j=64))[0] is True
+    # (B's order qp keeps p and q from being folded into one dim)
+    assert boxes("pqi", "qpj", "ij", dict(p=48, q=2, i=128, j=64))[0] is False
+    assert boxes("pqi", "qpj", "ij", dict(p=64, q=3, i=128, j=64))[0] is True
+    assert boxes("pqi", "qpj", "ij", dict(p=16, q=4, i=128, j=64))[0] is False
+
+
+def test_rank_and_stride_rules():
+    # six dims in A: more than a tensor map holds
+    ext = dict(a=32, b=2, c=2, p=32, q=2, r=2, j=16)
+    assert boxes("apbqcr", "pqrj", "acbj", ext)[0] is False
+    # a stride that is not a multiple of 4 FP32 elements (16 bytes)
+    B = ((64, 64), (1, 64))
+    C = ((128, 64), (1, 128))
+    with tc.access("box"):
+        A = ((128, 64), (1, 130))
+        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is False
+        A = ((128, 64), (1, 132))
+        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is True
+        # negative or zero strides are gathered
+        A = ((128, 64), (1, -128))
+        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is False
+
+
+def test_fp64_mode_has_no_box_plan():
+    keep = []
+    t = L.make_tensor((8, 8), (1, 8), "ip", 0, keep)
+    u = L.make_tensor((8, 8), (1, 8), "pj", 0, keep)
+    v = L.make_tensor((8, 8), (1, 8), "ij", 0, keep)
+    a, b = L.c_i32(0), L.c_i32(0)
+    assert L.lib().tc_box_access(L.TC_F32, L.TC_MODE_F64, t, u, v, a, b) == -8
+    assert L.lib().tc_box_access(L.TC_F64, L.TC_MODE_BF16X3, t, u, v, a, b) == -8
+    with pytest.raises(ValueError):
+        tc.set_access("tma")
+    assert L.lib().tc_set_access(7) == -1

@@ -16,23 +16,31 @@ from helpers import norm_err, oracle_ref, to_device
 pytestmark = pytest.mark.gpu
 
 
-def test_injected_timeout_is_reported_and_context_survives(monkeypatch):
+@pytest.mark.parametrize("access", ["block", "box"])
+def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access):
+    # "box": the box loads still in flight when the CTA unwinds are waited
+    # for (bounded) before it exits
     g = torch.Generator().manual_seed(3)
     A = (torch.rand(200, 96, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     B = (torch.rand(96, 150, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     C0 = torch.zeros(200, 150, dtype=torch.float64)
     dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
     assert tc.device_error() == 0
-    monkeypatch.setenv("TC_FAULT", "timeout")
-    dC = to_device(C0, torch.float32)
-    tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
-    torch.cuda.synchronize()
-    assert tc.device_error() == -7  # TC_ERR_DEVICE_TIMEOUT, then cleared
-    assert tc.device_error() == 0
-    monkeypatch.delenv("TC_FAULT")
-    dC = to_device(C0, torch.float32)
-    tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
-    torch.cuda.synchronize()
-    assert tc.device_error() == 0
+    with tc.access(access):
+        dC = to_device(C0, torch.float32)
+        # C is row-major, so the planner swaps the operands: the matrix-role A
+        # is the caller's B (stride 150, not a multiple of 4: gathered) and the
+        # matrix-role B the caller's A (boxed)
+        assert tc.box_access(dA, "ip", dB, "pj", dC, "ij") == (False, access == "box")
+        monkeypatch.setenv("TC_FAULT", "timeout")
+        tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
+        torch.cuda.synchronize()
+        assert tc.device_error() == -7  # TC_ERR_DEVICE_TIMEOUT, then cleared
+        assert tc.device_error() == 0
+        monkeypatch.delenv("TC_FAULT")
+        dC = to_device(C0, torch.float32)
+        tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
     ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
     assert norm_err(dC.cpu().double().numpy(), ref, mag) <= 3 * 2.0 ** -16 + 8 * 2.0 ** -24
