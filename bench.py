@@ -41,13 +41,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cc4x4_f64", choices=sorted(W.SPECS) + ["batch512"])
+    ap.add_argument("--workload", default="cc4x4_f64",
+                    choices=sorted(W.SPECS) + ["batch512"] + sorted(W.PAPER_SHAPES))
     ap.add_argument("--mode", choices=["f64", "bf16x3", "bf16x6"], default=None,
                     help="override the workload's arithmetic")
     ap.add_argument("--access", choices=["block", "scatter", "box"], default="block",
                     help="tensor-core operand access: block-scatter gathers (block), element "
                          "gathers (scatter) or TMA boxes where tiles are boxes (box)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttgt", action="store_true", help="skip the TTGT comparison leg")
     return ap.parse_args()
 
 
@@ -200,6 +202,55 @@ def host_bytes(spec):
     es = torch.tensor([], dtype=spec.dtype).element_size()
     n = lambda lab: int(np.prod(spec.shape(lab)))
     return es * n(spec.labA), es * n(spec.labB), es * n(spec.labC)
+
+
+# ---- TTGT comparison (transpose-transpose-GEMM-transpose, Section 3) ----------------------
+
+def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta):
+    """The contraction the way the paper's TTGT baseline computes it: copy A
+    and B into matrix order (I, P) and (P, J), one library GEMM (cuBLAS via
+    torch.matmul), then a strided copy of the product back into C's layout.
+    Returns the bytes of the temporary matrices."""
+    I = [x for x in labC if x in labA]
+    J = [x for x in labC if x in labB]
+    P = [x for x in labA if x in labB]
+    ext = {x: n for lab, T in ((labA, A), (labB, B), (labC, C)) for x, n in zip(lab, T.shape)}
+    size = lambda xs: int(np.prod([ext[x] for x in xs])) if xs else 1  # noqa: E731
+    At = A.permute(*[labA.index(x) for x in I + P]).contiguous().reshape(size(I), size(P))
+    Bt = B.permute(*[labB.index(x) for x in P + J]).contiguous().reshape(size(P), size(J))
+    Ct = torch.matmul(At, Bt)
+    back = Ct.reshape([ext[x] for x in I + J]).permute(*[(I + J).index(x) for x in labC])
+    if beta == 0.0:
+        C.copy_(back).mul_(alpha)
+    else:
+        C.mul_(beta).add_(back, alpha=alpha)
+    return (At.numel() + Bt.numel() + Ct.numel()) * At.element_size()
+
+
+def time_ttgt(problems, warm: int, K: int, flops: float, ws: int):
+    """Device time of the TTGT form of one step (all `problems`), with the
+    temporaries' bytes; FP32 GEMMs in full FP32 (no TF32)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        extra = 0
+        for _ in range(warm):
+            extra = sum(ttgt_contract(*p) for p in problems)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            for p in problems:
+                ttgt_contract(*p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return {"value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
+            "ms_per_step": round(ms, 4), "temporary_bytes": int(extra),
+            "what": "torch permute().contiguous() + torch.matmul (cuBLAS, FP64 or full FP32) + "
+                    "strided copy back, same inputs, device time"}
 
 
 # ---- CPU oracle baseline -----------------------------------------------------------------
@@ -359,9 +410,164 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_paper(args, ws, rank, local):
+    """Section 9's randomly generated contractions of one matrix shape (square
+    m = n = k, or rank-k m = n >> k): three seeded contractions, 1-3 dims per
+    bundle, random label and storage orders; one step = the three tc_contract
+    calls.  Effective lengths from the flops actually performed."""
+    shape = W.PAPER_SHAPES[args.workload]
+    mode = args.mode or "f64"
+    dt = torch.float64 if mode == "f64" else torch.float32
+    warm, K = max(3, args.warmup), max(1, args.steps)
+    probs = W.paper_problems(args.workload)
+    host = [W.make_random_inputs(p, seed=shape["seed"] * 10 + i, dtype=dt) for i, p in enumerate(probs)]
+    dev = [(to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB, to_device(h["C"], dt),
+            p.labC, 1.0, 0.0) for p, h in zip(probs, host)]
+    C0 = [d[4].clone() for d in dev]
+    works = [torch.empty(max(1, tc.workspace_size(d[0], d[1], d[2], d[3], d[4], d[5], mode=mode)),
+                         dtype=torch.uint8, device="cuda") for d in dev]
+    flops = sum(p.flops() for p in probs)
+    lib = L.lib()
+
+    def step():
+        for d, w in zip(dev, works):
+            tc.contract(d[0], d[1], d[2], d[3], d[4], d[5], alpha=d[6], beta=d[7], mode=mode, workspace=w)
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in dev]
+           for _ in range(K)]
+    for row in kev:
+        for a, b in row:
+            a.record()
+            b.record()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.tc_launch_count()
+    e0.record()
+    for i in range(K):
+        for (d, w), (ka, kb) in zip(zip(dev, works), kev[i]):
+            lib.tc_set_mainloop_events(L.c_vp(ka.cuda_event), L.c_vp(kb.cuda_event))
+            tc.contract(d[0], d[1], d[2], d[3], d[4], d[5], alpha=d[6], beta=d[7], mode=mode, workspace=w)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = lib.tc_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+    kms = max_over_ranks(float(np.mean([sum(a.elapsed_time(b) for a, b in row) for row in kev])), ws)
+    err_code = tc.device_error()
+
+    # end to end through the public API with host buffers
+    pins = [tuple(torch.empty_strided(h[x].shape, h[x].stride(), dtype=dt).pin_memory().copy_(h[x])
+                  for x in "ABC") for h in host]
+    outs = [torch.empty_strided(h["C"].shape, h["C"].stride(), dtype=dt).pin_memory() for h in host]
+    bi = sum(sum(t.numel() * t.element_size() for t in pp) for pp in pins)
+    bo = sum(t.numel() * t.element_size() for t in outs)
+
+    def e2e_step():
+        for d, pp in zip(dev, pins):
+            d[0].copy_(pp[0], non_blocking=True)
+            d[2].copy_(pp[1], non_blocking=True)
+            d[4].copy_(pp[2], non_blocking=True)
+        step()
+        for d, o in zip(dev, outs):
+            o.copy_(d[4], non_blocking=True)
+
+    for _ in range(warm):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(K):
+        e2e_step()
+    f1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / K, ws)
+
+    square = shape["m"] == shape["n"] == shape["k"]
+    eff = [round(W.effective_square(p.flops()) if square
+                 else W.effective_rank_k(p.flops(), shape["m"], shape["n"]), 1) for p in probs]
+    if mode == "f64":
+        peak_v = fp64_peak_tflops()
+        peak_src = "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
+        prods, kname = 1, "k_f64"
+    else:
+        mp = measured_peaks()
+        peak_v = mp.get("bf16_tflops", 1900.0)
+        peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
+        prods, kname = (3 if mode == "bf16x3" else 6), "k_tc"
+    ach = prods * flops / (kms * 1e-3) / 1e12
+    desc = (f"{args.workload}: {len(probs)} random contractions shaped like m={shape['m']}, "
+            f"n={shape['n']}, k={shape['k']} (1-3 dims per bundle, random label and storage "
+            f"orders, seed {shape['seed']}): " + "; ".join(
+                f"{p.labC} <- {p.labA}.{p.labB}" for p in probs)
+            + f"; mode={mode}")
+    line = {
+        "metric": METRIC, "value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": K, "warmup": warm, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if mode == "f64" else f"f32 data, {mode} products, f32 accumulate",
+        "data": "synthetic (seeded uniform[-1,1], randomly permuted dense layouts)",
+        "config": {"workload": desc, "effective_lengths": eff,
+                   "extents": [{str(k): v for k, v in p.ext.items()} for p in probs],
+                   "l2": "operands larger than L2" if max(d[0].numel() * d[0].element_size() for d in dev)
+                         > L2_BYTES else "operands smaller than L2",
+                   "parallelism": f"replicas x{ws}"},
+        "clocks": clk,
+        "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "tensor", "kernel": kname, "achieved": round(ach, 5), "peak": round(peak_v, 5),
+                     "unit": "TFLOP/s", "frac": round(ach / peak_v, 4), "peak_source": peak_src,
+                     "kernel_ms": round(kms, 4), "traffic": None,
+                     "algorithmic": f"{flops:.4g} flops per step over {len(probs)} launches"
+                                    + (f" (x{prods} bf16 products)" if mode != "f64" else "")},
+        "device_error": err_code,
+    }
+    if not args.no_ttgt:
+        for d, c in zip(dev, C0):
+            d[4].copy_(c)
+        tt = time_ttgt(dev, warm, K, flops, ws)
+        tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms, 3)
+        tt["ours_workspace_bytes"] = int(sum(w.numel() for w in works))
+        line["ttgt"] = tt
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        for d, c in zip(dev, C0):
+            d[4].copy_(c)
+        step()
+        torch.cuda.synchronize()
+        p0, h0 = probs[0], host[0]
+        spec0 = W.Spec(args.workload, p0.labA, p0.labB, p0.labC, {str(k): v for k, v in p0.ext.items()},
+                       dt, 1.0, 0.0)
+        fl, sec, S, cores, cref, mag = oracle_sample(spec0, h0, seconds=12.0)
+        got = dev[0][4].cpu().to(torch.float64).numpy()
+        # the oracle's first S elements: colexicographic over C's own dims
+        g = got.ravel(order="F")[:S]
+        r = cref.ravel(order="F")[:S]
+        m = mag.ravel(order="F")[:S]
+        err = float(np.max(np.abs(g - r) / np.maximum(m, 1e-300)))
+        line["cpu_baseline"] = {"value": round(fl / sec / 1e12, 8), "unit": "TFLOP/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {S} output elements of the first contraction "
+                                          f"(all k terms each), {sec:.1f} s on {cores} host threads",
+                                "max_normalised_err_gpu_vs_oracle": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, ws, rank, local):
     if args.workload == "batch512":
         return run_batch(args, ws, rank, local)
+    if args.workload in W.PAPER_SHAPES:
+        return run_paper(args, ws, rank, local)
     spec = W.SPECS[args.workload]
     if args.mode:
         import dataclasses
@@ -481,6 +687,15 @@ def run_ours(args, ws, rank, local):
                                     + (f" (x{prods} bf16 products)" if spec.mode != "f64" else "")},
         "device_error": err_code,
     }
+
+    # the TTGT form of the same step (cuBLAS GEMM between transposition copies)
+    if not args.no_ttgt:
+        dC.copy_(C0)
+        tt = time_ttgt([(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.alpha, spec.beta)],
+                       warm, K, flops, ws)
+        tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms_max, 3)
+        tt["ours_workspace_bytes"] = int(wsz)
+        line["ttgt"] = tt
 
     # CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

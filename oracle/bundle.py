@@ -26,6 +26,11 @@ in label order and repeating until no pair merges.  The steps move no data.
    the P order does not affect its access) but B's smallest stride lies in P,
    order P by |stride| in B instead (smallest first), so that B is read along its own unit
    stride.  Step 5's aim -- stride-1 access for A -- is unaffected.
+``normalize(..., gpu_row_order=True)`` adds a second one:
+7. when A's smallest stride lies in I (A is read along its rows), order I by
+   |stride| in A instead of C (smallest first); likewise J by |stride| in B
+   when B's smallest stride lies in J.  C, which step 3 serves, is written
+   once, while A and B are read once per output tile across from them.
 """
 from dataclasses import dataclass, field
 from typing import Dict, List, Tuple
@@ -126,10 +131,11 @@ def _fold(dims: List[Dim]) -> List[Dim]:
     return dims
 
 
-def normalize(A, B, C, gpu_p_order: bool = False) -> Bundles:
+def normalize(A, B, C, gpu_p_order: bool = False, gpu_row_order: bool = False) -> Bundles:
     """A, B, C are (labels, lens, strides) triples.  Returns the bundles after
     the five steps of Section 7.3 (names 'A' and 'B' in Dim.s refer to the
-    tensors *after* any swap), plus step 6 above when ``gpu_p_order``."""
+    tensors *after* any swap), plus step 6 above when ``gpu_p_order`` and
+    step 7 when ``gpu_row_order``."""
     I, J, P = _dims(A, B, C)
     # 1. discard length-1 dims
     I = [d for d in I if d.n != 1]
@@ -160,4 +166,13 @@ def normalize(A, B, C, gpu_p_order: bool = False) -> Bundles:
         b_k = minB_J is None or minB_P < minB_J
         if a_rows and b_k:
             P = sorted(P, key=lambda d: abs(d.s["B"]))
+    # 7. (not in the paper) an operand whose smallest stride lies in its row
+    #    bundle orders that bundle by its own strides
+    if gpu_row_order:
+        minA_P = min((abs(d.s["A"]) for d in P), default=None)
+        minB_P = min((abs(d.s["B"]) for d in P), default=None)
+        if I and (minA_P is None or min(abs(d.s["A"]) for d in I) <= minA_P):
+            I = sorted(I, key=lambda d: abs(d.s["A"]))
+        if J and (minB_P is None or min(abs(d.s["B"]) for d in J) <= minB_P):
+            J = sorted(J, key=lambda d: abs(d.s["B"]))
     return Bundles(I, J, P, swapped)

@@ -185,3 +185,63 @@ def batch_problems(seed: int = 1004, count: int = 512):
     rng = np.random.default_rng(seed)
     return [random_problem(rng, dI=(1, 5), dJ=(1, 5), dP=(1, 3), ext=(8, 64), max_rank=6,
                            max_elems=1 << 22, max_flops=2.0 ** 34) for _ in range(count)]
+
+
+# ---- contractions shaped like a given matrix multiplication ---------------------------
+# Section 9's randomly generated contractions: for a matrix shape (m, n, k),
+# each of the bundles I, J, P gets one to three tensor dims whose extents
+# multiply to about m, n and k; the label order inside each tensor and each
+# tensor's storage order are random permutations.  Results are reported
+# against "effective" matrix lengths derived from the flops f actually
+# performed: m = n = k = (f / 2)^(1/3) for square shapes, k = f / (2 m n)
+# for rank-k updates with the prescribed m and n.
+
+def split_extent(rng: np.random.Generator, target: int, nd: int, min_ext: int = 2) -> List[int]:
+    """`nd` extents (each >= min_ext) whose product is close to `target`: the
+    first nd - 1 drawn within +-25 % of target^(1/nd), the last making up the
+    rest."""
+    if nd == 1:
+        return [max(min_ext, int(target))]
+    base = float(target) ** (1.0 / nd)
+    ext = [max(min_ext, int(round(base * rng.uniform(0.75, 1.25)))) for _ in range(nd - 1)]
+    ext.append(max(min_ext, int(round(target / float(np.prod(ext))))))
+    return ext
+
+
+def shaped_problem(rng: np.random.Generator, m: int, n: int, k: int,
+                   dims=(1, 3)) -> RandomProblem:
+    """One random contraction shaped like an m x n x k matrix multiplication."""
+    nd = [int(rng.integers(dims[0], dims[1] + 1)) for _ in range(3)]
+    labs = [str(x) for x in rng.permutation(list(LETTERS[:sum(nd)]))]
+    I, J, P = labs[:nd[0]], labs[nd[0]:nd[0] + nd[1]], labs[nd[0] + nd[1]:]
+    e = {}
+    for bundle, target in ((I, m), (J, n), (P, k)):
+        for x, v in zip(bundle, split_extent(rng, target, len(bundle))):
+            e[x] = v
+    perm = lambda xs: "".join(str(x) for x in rng.permutation(list(xs)))  # noqa: E731
+    A, B, C = perm(I + P), perm(P + J), perm(I + J)
+    return RandomProblem(A, B, C, e, perm(A), perm(B), perm(C))
+
+
+def effective_square(flops: float) -> float:
+    """Effective m = n = k of a square-shaped contraction: (f / 2)^(1/3)."""
+    return (flops / 2.0) ** (1.0 / 3.0)
+
+
+def effective_rank_k(flops: float, m: int, n: int) -> float:
+    """Effective k of a rank-k-shaped contraction with prescribed m and n: f / (2 m n)."""
+    return flops / (2.0 * m * n)
+
+
+# The two shape families of the paper's random-contraction experiments at
+# GB300-sized lengths: three contractions per shape (seeded).
+PAPER_SHAPES = {
+    "paper_square_f64": dict(m=4096, n=4096, k=4096, seed=1101, count=3),
+    "paper_rankk_f64": dict(m=16000, n=16000, k=256, seed=1102, count=3),
+}
+
+
+def paper_problems(name: str) -> List[RandomProblem]:
+    s = PAPER_SHAPES[name]
+    rng = np.random.default_rng(s["seed"])
+    return [shaped_problem(rng, s["m"], s["n"], s["k"]) for _ in range(s["count"])]

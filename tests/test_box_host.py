@@ -34,9 +34,9 @@ def test_benchmark_workloads_take_boxes():
 
 def test_gradient_contractions():
     sp = W.SPECS["grad_f32"]
-    # dA = dC x_J B: B's unit-stride dim m is not the first of its bundle
-    # (J is sorted by dA's strides: l before m), so B is gathered
-    assert boxes(sp.labC, sp.labB, sp.labA, sp.ext) == (True, False)
+    # dA = dC x_J B: B's unit stride lies in J, so the planner orders J by
+    # B's strides (m before l, not dA's l before m) and B's tiles are boxes
+    assert boxes(sp.labC, sp.labB, sp.labA, sp.ext) == (True, True)
     # dB = A x_I dC
     assert boxes(sp.labA, sp.labC, sp.labB, sp.ext) == (True, True)
 

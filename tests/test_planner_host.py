@@ -19,7 +19,7 @@ def cm(lab, ext):
 
 def compare(labA, sA, labB, sB, labC, sC):
     got = tc.plan_describe(sA, labA, sB, labB, sC, labC)
-    ref = ob.normalize((labA, *sA), (labB, *sB), (labC, *sC), gpu_p_order=True)
+    ref = ob.normalize((labA, *sA), (labB, *sB), (labC, *sC), gpu_p_order=True, gpu_row_order=True)
     assert got["swapped"] == ref.swapped
     assert (got["m"], got["n"], got["k"]) == (ref.m, ref.n, ref.k)
     for name, rb, key in (("I", ref.I, ("A", "C")), ("J", ref.J, ("B", "C")), ("P", ref.P, ("A", "B"))):
@@ -102,6 +102,29 @@ def test_gpu_p_order_step():
     paper = ob.normalize((s.labA, *cm(s.labA, s.ext)), (s.labB, *cm(s.labB, s.ext)),
                          (s.labC, *cm(s.labC, s.ext)))
     assert ["".join(d.labels) for d in paper.P] == ["l", "m"]  # the paper's step 5 alone
+
+
+def test_gpu_row_order_step():
+    # A's unit stride (a) lies in I but C orders I as (gd, a) (g and d fold):
+    # the planner orders I by A's strides instead, B likewise for J
+    ext = dict(a=13, b=73, c=68, d=17, e=56, f=60, g=19)
+    A = ("bgdea", *stride_of("bgdea", "abegd", ext))
+    B = ("fbec", *stride_of("fbec", "febc", ext))
+    C = ("gadcf", *stride_of("gadcf", "gdfac", ext))
+    g = compare(A[0], A[1:], B[0], B[1:], C[0], C[1:])
+    assert [d["labels"] for d in g["I"]][0] == "a"
+    paper = ob.normalize(A, B, C)
+    assert ["".join(d.labels) for d in paper.I][0] == "gd"  # the paper's step 3 alone
+
+
+def stride_of(labels, order, ext):
+    """Lengths and strides of a tensor indexed by `labels`, stored column-major
+    in the label order `order`."""
+    st, acc = {}, 1
+    for x in order:
+        st[x] = acc
+        acc *= ext[x]
+    return tuple(ext[x] for x in labels), tuple(st[x] for x in labels)
 
 
 def test_workspace_is_vector_sized_not_operand_sized():

@@ -1,0 +1,51 @@
+"""The seeded workload generators (no GPU): Section 9's contractions shaped
+like a given matrix multiplication, and the effective lengths the paper
+reports them at."""
+import numpy as np
+import pytest
+
+from paper_1607_00291_gb300 import workloads as W
+
+
+def bundles(p):
+    I = [x for x in p.labC if x in p.labA]
+    J = [x for x in p.labC if x in p.labB]
+    P = [x for x in p.labA if x in p.labB]
+    return I, J, P
+
+
+def size(p, xs):
+    return int(np.prod([p.ext[x] for x in xs])) if xs else 1
+
+
+@pytest.mark.parametrize("mnk", [(4096, 4096, 4096), (16000, 16000, 256), (300, 200, 20)])
+def test_shaped_problems_follow_the_recipe(mnk):
+    rng = np.random.default_rng(5)
+    m, n, k = mnk
+    for _ in range(50):
+        p = W.shaped_problem(rng, m, n, k)
+        I, J, P = bundles(p)
+        # every label in exactly two tensors; one to three dims per bundle
+        for x in p.ext:
+            assert (x in p.labA) + (x in p.labB) + (x in p.labC) == 2
+        assert all(1 <= len(b) <= 3 for b in (I, J, P))
+        assert sorted(p.labA) == sorted(I + P) and sorted(p.labB) == sorted(P + J)
+        # storage orders are permutations of each tensor's labels
+        for lab, order in ((p.labA, p.orderA), (p.labB, p.orderB), (p.labC, p.orderC)):
+            assert sorted(lab) == sorted(order)
+        # bundle products close to the matrix lengths
+        for b, target in ((I, m), (J, n), (P, k)):
+            assert abs(size(p, b) / target - 1) < 0.3, (b, size(p, b), target)
+        assert p.flops() == 2.0 * size(p, I) * size(p, J) * size(p, P)
+
+
+def test_effective_lengths():
+    assert W.effective_square(2.0 * 4096 ** 3) == pytest.approx(4096)
+    assert W.effective_rank_k(2.0 * 16000 * 16000 * 256, 16000, 16000) == pytest.approx(256)
+
+
+def test_paper_problem_sets_are_seeded():
+    for name in W.PAPER_SHAPES:
+        a, b = W.paper_problems(name), W.paper_problems(name)
+        assert [(p.labA, p.labB, p.labC, p.ext) for p in a] == [(p.labA, p.labB, p.labC, p.ext) for p in b]
+        assert len(a) == W.PAPER_SHAPES[name]["count"]
