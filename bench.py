@@ -45,9 +45,10 @@ def parse():
                     choices=sorted(W.SPECS) + ["batch512"] + sorted(W.PAPER_SHAPES))
     ap.add_argument("--mode", choices=["f64", "bf16x3", "bf16x6"], default=None,
                     help="override the workload's arithmetic")
-    ap.add_argument("--access", choices=["block", "scatter", "box"], default="block",
-                    help="tensor-core operand access: block-scatter gathers (block), element "
-                         "gathers (scatter) or TMA boxes where tiles are boxes (box)")
+    ap.add_argument("--access", choices=["box", "block", "scatter"], default="box",
+                    help="tensor-core operand access: TMA boxes where tiles are boxes and "
+                         "block-scatter gathers elsewhere (box), block-scatter gathers only "
+                         "(block), or element gathers only (scatter)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttgt", action="store_true", help="skip the TTGT comparison leg")
     return ap.parse_args()

@@ -175,25 +175,25 @@ TC_API void tc_plan_destroy(tc_plan* plan);
 /* How the tensor-core mainloop (BF16X3 / BF16X6 modes) reads A and B into
  * shared memory.  Results are identical, bit for bit, in every setting; only
  * the speed differs.
- * TC_ACCESS_BLOCK (default): gathers through the scatter vectors (Section
- * 6.1), 16 bytes at a time wherever the block-scatter vectors (Section 6.2)
- * show four consecutive elements at unit stride: the paper's block-scatter
- * form.
+ * TC_ACCESS_BOX (default): an operand whose tile rows and k-tile form one box
+ * in its own dims -- its unit-stride dim leads the row or the k bundle, the
+ * bundle dims before the one a tile ends in are covered whole, and that dim's
+ * tile extent divides its length (the last dim of a bundle may run past its
+ * end), at most 5 dims, FP32 strides that are multiples of 4 elements,
+ * 16-byte aligned data -- is loaded with one TMA box per tile (a regular
+ * block in the sense of Section 6.2, in several dims at once, read along the
+ * unit stride as Section 7.3 prefers, with no scatter entry); every other
+ * operand as in TC_ACCESS_BLOCK.
+ * TC_ACCESS_BLOCK: gathers through the scatter vectors (Section 6.1), 16
+ * bytes at a time wherever the block-scatter vectors (Section 6.2) show four
+ * consecutive elements at unit stride: the paper's block-scatter form.
  * TC_ACCESS_SCATTER: the same gathers one element at a time, ignoring the
  * block-scatter vectors: the paper's plain scatter-matrix form, kept for
  * comparison.
- * TC_ACCESS_BOX: an operand whose tile rows and k-tile form one box in its
- * own dims -- its unit-stride dim leads the row or the k bundle, the bundle
- * dims before the one a tile ends in are covered whole, and that dim's tile
- * extent divides its length (the last dim of a bundle may run past its end),
- * at most 5 dims, FP32 strides that are multiples of 4 elements, 16-byte
- * aligned data -- is loaded with one TMA box per tile (a regular block in the
- * sense of Section 6.2, in several dims at once, read along the unit stride
- * as Section 7.3 prefers, with no scatter entry); other operands as BLOCK.
  * The FP64 mode always uses the BLOCK form.  The setting is process-wide and
  * read when a contraction is issued or a plan is created.  Returns the
  * previous setting, or TC_ERR_ARG for an unknown value. */
-typedef enum { TC_ACCESS_BLOCK = 0, TC_ACCESS_SCATTER = 1, TC_ACCESS_BOX = 2 } tc_access;
+typedef enum { TC_ACCESS_BOX = 0, TC_ACCESS_BLOCK = 1, TC_ACCESS_SCATTER = 2 } tc_access;
 TC_API int tc_set_access(int access);
 
 /* Report how tc_contract would read A and B (matrix roles, as in

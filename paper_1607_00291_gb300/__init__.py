@@ -113,11 +113,11 @@ _ACCESS = {"block": L.TC_ACCESS_BLOCK, "scatter": L.TC_ACCESS_SCATTER, "box": L.
 
 def set_access(access: str) -> str:
     """Operand access of the tensor-core mainloop, process-wide (results are
-    identical in every setting): "block" (default) gathers through the
-    scatter vectors, 16 bytes at a time where the block-scatter vectors allow;
-    "scatter" gathers element by element (the plain scatter-matrix form);
-    "box" loads every operand whose tiles are boxes in its own dims with TMA
-    and block-gathers the rest.  Returns the previous setting."""
+    identical in every setting): "box" (default) loads every operand whose
+    tiles are boxes in its own dims with TMA and block-gathers the rest;
+    "block" gathers every operand through the scatter vectors, 16 bytes at a
+    time where the block-scatter vectors allow; "scatter" gathers element by
+    element (the plain scatter-matrix form).  Returns the previous setting."""
     if access not in _ACCESS:
         raise ValueError(f"access must be one of {sorted(_ACCESS)}")
     prev = L.lib().tc_set_access(_ACCESS[access])
@@ -127,7 +127,7 @@ def set_access(access: str) -> str:
 
 
 class access:
-    """Context manager: ``with access("box"): ...`` restores the previous setting."""
+    """Context manager: ``with access("block"): ...`` restores the previous setting."""
 
     def __init__(self, mode: str):
         self.mode = mode
@@ -144,7 +144,7 @@ class access:
 def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):
     """(a_box, b_box): whether tc_contract in tensor-core `mode` loads the
     matrix-role operands A and B as TMA boxes (True) or gathers them (False)
-    under the current access setting (only "box" takes boxes).  Host only; A, B, C are tensors or
+    under the current access setting (only "box", the default, takes boxes).  Host only; A, B, C are tensors or
     (shape, strides) pairs (pairs are taken as 16-byte aligned)."""
     keep = []
 

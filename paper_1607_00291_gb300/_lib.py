@@ -10,7 +10,7 @@ MAX_RANK = 16
 
 TC_F64, TC_F32 = 0, 1
 TC_MODE_F64, TC_MODE_BF16X3, TC_MODE_BF16X6 = 0, 1, 2
-TC_ACCESS_BLOCK, TC_ACCESS_SCATTER, TC_ACCESS_BOX = 0, 1, 2
+TC_ACCESS_BOX, TC_ACCESS_BLOCK, TC_ACCESS_SCATTER = 0, 1, 2
 TC_OK = 0
 STATUS = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_LABEL", -3: "TC_ERR_EXTENT", -4: "TC_ERR_OVERLAP",
           -5: "TC_ERR_WORKSPACE", -6: "TC_ERR_CUDA", -7: "TC_ERR_DEVICE_TIMEOUT",

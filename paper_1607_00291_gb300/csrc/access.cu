@@ -10,7 +10,8 @@
 // scatter entry at all.  This file decides, per operand, whether its tiles
 // are such boxes and encodes the tensor map; operands that are not keep the
 // scatter-vector gather of Section 6.1.  It also carries the process-wide
-// access setting: block gathers (default), element gathers, or boxes.
+// access setting: boxes where tiles are boxes (default), block gathers only,
+// or element gathers only.
 //
 // A tile of T consecutive linear indices of a bundle (dims d0, d1, ... with
 // extents n0, n1, ..., d0 fastest, tiles starting at multiples of T) is a box
@@ -31,7 +32,7 @@
 namespace tc {
 namespace {
 
-std::atomic<int> g_access{TC_ACCESS_BLOCK};
+std::atomic<int> g_access{TC_ACCESS_BOX};
 
 constexpr int kTileK = 32;  // k-tile of the tensor-core mainloop
 constexpr int kTileM = 128; // rows of an A tile
@@ -104,6 +105,13 @@ bool make_box(const Bundle& R, const int64_t* rs, const Bundle& K, const int64_t
   if (!tile_box(R.len, nr, rows, rbox, &rend) || !tile_box(K.len, nk, kTileK, kbox, &kend))
     return false;
   if (kcontig ? kbox[0] != (uint32_t)kTileK : (rbox[0] % 4) != 0) return false;
+  // every box extent within its dim's length (a tile may still run past the
+  // end of a bundle's last dim, whose excess the box reads as zeros): boxes
+  // larger than their tensor are not taken
+  for (int i = 0; i < nr; ++i)
+    if ((int64_t)rbox[i] > R.len[i]) return false;
+  for (int i = 0; i < nk; ++i)
+    if ((int64_t)kbox[i] > K.len[i]) return false;
 
   // tensor-map dims: the unit-stride bundle first, each bundle fastest dim first
   const int rank = nr + nk;
@@ -154,12 +162,12 @@ bool make_box(const Bundle& R, const int64_t* rs, const Bundle& K, const int64_t
 
 }  // namespace
 
-void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps) {
+void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box) {
   std::memset(&d.boxA, 0, sizeof d.boxA);
   std::memset(&d.boxB, 0, sizeof d.boxB);
   const int acc = g_access.load();
   d.elem_gather = acc == TC_ACCESS_SCATTER ? 1 : 0;
-  if (acc != TC_ACCESS_BOX || L.m <= 0 || L.n <= 0 || L.k <= 0) return;
+  if (!allow_box || acc != TC_ACCESS_BOX || L.m <= 0 || L.n <= 0 || L.k <= 0) return;
   make_box(L.I, L.I.s0, L.P, L.P.s0, d.a, kTileM, d.a_kc != 0, maps ? &maps[0] : nullptr,
            &d.boxA);
   make_box(L.J, L.J.s0, L.P, L.P.s1, d.b, d.bn, d.b_kc != 0, maps ? &maps[1] : nullptr, &d.boxB);

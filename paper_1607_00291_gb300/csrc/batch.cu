@@ -131,7 +131,7 @@ float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, 
   d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
   d.splits = c.splits;
   d.kps = c.kps;
-  plan_access(p.L, d, q.tm);
+  plan_access(p.L, d, q.tm, /*allow_box=*/false);  // as the batch kernel will run it
   q.pieces = pieces;
   q.ctas = 1;
   q.err = err_word();
@@ -232,7 +232,7 @@ struct tc_plan {
   int64_t max_m_split = 0, max_n_split = 0;
   int pieces = 2;
   int64_t ctas = 152;
-  bool any_box = false;  // some problem loads an operand as TMA boxes
+  int box_form = 0;  // 0: no TMA boxes, 1: some operands, 2: every operand of every problem
 };
 
 namespace {
@@ -438,9 +438,12 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     d.splits = c.splits;
     d.kps = c.kps;
     if (!f64) {
-      plan_access(p.L, d, &maps[2 * (size_t)i]);
+      // batch plans gather every operand: their kernel form with boxes faulted
+      // the GPU on the 512-problem workload, cause not yet found
+      plan_access(p.L, d, &maps[2 * (size_t)i], /*allow_box=*/false);
       d.tmaps = d_maps + 2 * (size_t)i;
-      pl->any_box = pl->any_box || d.boxA.rank > 0 || d.boxB.rank > 0;
+      const int f = d.boxA.rank > 0 && d.boxB.rank > 0 ? 2 : d.boxA.rank > 0 || d.boxB.rank > 0 ? 1 : 0;
+      pl->box_form = i == 0 ? f : (pl->box_form == f ? f : (pl->box_form || f ? 1 : 0));
     }
   }
   auto up = [](void* dst, const void* src, size_t bytes) {
@@ -525,7 +528,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
-    q.any_box = plan->any_box ? 1 : 0;
+    q.box_form = plan->box_form;
     q.err = err_word();
     e = launch_tc(q, s);
   }

@@ -73,9 +73,10 @@ struct BoxAccess {
 // process-wide access setting (tc_set_access) and the problem's layout,
 // operands, access flags and tile width, and encode the tensor maps of the
 // operands that take boxes into maps[0] (A) and maps[1] (B); with maps ==
-// null only the eligibility is decided.  Defined in access.cu.
+// null only the eligibility is decided; allow_box = false keeps every operand
+// gathered.  Defined in access.cu.
 struct DevProblem;
-void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps);
+void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box = true);
 bool box_encoder_available();  // the driver's tensor-map encoder could be found
 
 // One planned contraction as the persistent kernels see it: a kernel
@@ -123,7 +124,7 @@ struct TcLaunch {
   int64_t split_cols;         // batch: total columns of the split problems
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
-  int32_t any_box;            // batch: some problem loads an operand as TMA boxes
+  int32_t box_form;           // batch: 0 no TMA boxes, 1 some operands, 2 every operand
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path

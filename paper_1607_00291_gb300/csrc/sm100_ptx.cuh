@@ -25,6 +25,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
       "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(bar))
       : "memory");
 }
+// `count` arrivals at once.
+__device__ __forceinline__ void mbar_arrive_n(uint64_t* bar, uint32_t count) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_u32(bar)),
+      "r"(count)
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -74,6 +82,14 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)),
                "r"(bytes)
+               : "memory");
+}
+// Make the tensor map at `map` (global memory, 128 bytes) as last written
+// through the generic proxy -- here by the host's copy into a plan buffer,
+// whose address an earlier plan may have used for other maps -- visible to
+// the tensor-map proxy that box loads read it through.
+__device__ __forceinline__ void fence_tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;\n" ::"l"(map)
                : "memory");
 }
 // Load the box at coordinates c[0..rank) (fastest dim first) of the tensor map

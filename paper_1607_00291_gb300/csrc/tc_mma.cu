@@ -53,10 +53,11 @@ using namespace ptx;
 
 constexpr int BM = 128, BK = 32;
 constexpr int NLOAD = 256, NCONV = 256, NEPI = 128;
-constexpr int NT = NLOAD + NCONV + NEPI + 32;
+constexpr int NT = NLOAD + NCONV + NEPI + 64;  // + the MMA warp and the box warp
 constexpr int CONV_W0 = NLOAD / 32;
 constexpr int EPI_W0 = (NLOAD + NCONV) / 32;
 constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
+constexpr int BOX_WARP = MMA_WARP + 1;  // issues the TMA box loads (BOX instantiation)
 constexpr int BAR_LOAD = 1, BAR_CONV = 2, BAR_EPI = 3;
 constexpr int KRING = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
@@ -82,8 +83,7 @@ struct Lay {
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
   static constexpr int NBARS = 2 * RS + 2 * MS + 5;
   static constexpr int MISC = BARS + NBARS * 8;
-  static constexpr int BOXS = MISC + 16;  // BoxState of the loaders' thread 0
-  static constexpr int END = BOXS + 64;
+  static constexpr int END = MISC + 16;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
   static_assert(BNMAX % NEPI == 0 && BM == NEPI && NLOAD % 32 == 0 && BK % (NLOAD / 32) == 0,
@@ -212,58 +212,43 @@ __device__ __forceinline__ int64_t kslot_fetch(const KSlotSrc& src, int64_t k0, 
 }
 
 // ---- box loads (operands whose tiles are TMA boxes) ------------------------------
-// Thread 0 of the loaders issues them; its state lives in shared memory so
-// that it takes no registers from the gather loop of the other loaders.
-struct BoxState {
-  int32_t c[2][5];  // coordinates of the next box of A and of B (map order)
-  int32_t pad[2];
-  long long g_box;  // the last k-tile box loads were issued for (-1: none)
-  long long g_iss;  // the last k-tile thread 0 issued any loads for
-};
-static_assert(sizeof(BoxState) <= 64, "box state slot");
-
+// Issued by one lane of the box warp; coordinates live in its registers.
+//
 // Coordinates of the box whose rows start at linear row r0 and whose k-tile
 // starts at linear k index k0: the mixed-radix digits of r0 and k0 over the
 // two bundles' extents (the last dim of each bundle keeps the quotient, which
 // may point past its end: the box reads zeros there).  Once per work item.
-__device__ __noinline__ void box_coords(const BoxAccess* x, uint32_t r0, uint32_t k0, int32_t* c) {
-  uint32_t v1 = x->kfirst ? k0 : r0, v2 = x->kfirst ? r0 : k0;
-  const int rank = x->rank, nf = x->nfirst;
-  for (int i = 0; i < rank; ++i) {
-    const bool first = i < nf;
-    const bool lastdim = i == nf - 1 || i == rank - 1;
-    const uint32_t v = first ? v1 : v2;
-    const uint32_t len = (uint32_t)x->len[i];
-    c[i] = (int32_t)(lastdim ? v : v % len);
-    const uint32_t q = lastdim ? 0u : v / len;
-    if (first) v1 = q; else v2 = q;
+__device__ __forceinline__ void box_coords(const BoxAccess& x, uint32_t r0, uint32_t k0,
+                                           int32_t (&c)[5]) {
+  uint32_t v1 = x.kfirst ? k0 : r0, v2 = x.kfirst ? r0 : k0;
+  const int rank = x.rank, nf = x.nfirst;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    c[i] = 0;
+    if (i < rank) {
+      const bool first = i < nf;
+      const bool lastdim = i == nf - 1 || i == rank - 1;
+      const uint32_t v = first ? v1 : v2;
+      const uint32_t len = (uint32_t)x.len[i];
+      c[i] = (int32_t)(lastdim ? v : v % len);
+      const uint32_t q = lastdim ? 0u : v / len;
+      if (first) v1 = q; else v2 = q;
+    }
   }
 }
 
-// The box loads of one k-tile into the raw stage whose barrier is `bar`, then
-// the coordinates of the next k-tile's boxes (one step along the dim the
-// k-tile ends in, carried into the k bundle's higher dims; the step divides
-// that dim's extent, so a wrap lands exactly on 0).  The transaction count
-// goes up before thread 0's own arrival on `bar`, so the phase cannot
-// complete before the boxes have landed.
-__device__ __noinline__ void box_issue(const DevProblem* d, const CUtensorMap* maps,
-                                       uint32_t rawA, uint32_t rawB, uint64_t* bar,
-                                       BoxState* bs) {
-  const BoxAccess* x[2] = {&d->boxA, &d->boxB};
-  const uint32_t ra = (uint32_t)x[0]->rank, rb = (uint32_t)x[1]->rank;
-  mbar_expect_tx(bar, (ra ? (uint32_t)x[0]->bytes : 0u) + (rb ? (uint32_t)x[1]->bytes : 0u));
-  for (int o = 0; o < 2; ++o) {
-    const BoxAccess* b = x[o];
-    if (b->rank == 0) continue;
-    int32_t* c = bs->c[o];
-    tma_load(o ? rawB : rawA, maps + o, c, b->rank, bar);
-    int i = b->kstep_dim;
-    c[i] += b->kstep;
-    while (i < b->klast && c[i] >= b->len[i]) {
-      c[i] = 0;
-      ++i;
-      c[i] += 1;
-    }
+// The next k-tile's box: one step along the dim the k-tile ends in, carried
+// into the k bundle's higher dims (the step divides that dim's extent, so a
+// wrap lands exactly on 0; the bundle's last dim is not wrapped).
+__device__ __forceinline__ void box_advance(const BoxAccess& x, int32_t (&c)[5]) {
+  const int sd = x.kstep_dim, kl = x.klast;
+  bool carry = false;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i == sd) c[i] += x.kstep;
+    else if (carry) c[i] += 1;
+    carry = i >= sd && i < kl && c[i] >= x.len[i];
+    if (carry) c[i] = 0;
   }
 }
 
@@ -336,15 +321,16 @@ __device__ __forceinline__ void load_panel(int t, uint32_t raw, const float* __r
 // ---- converter: raw panel -> NS bf16 pieces in the canonical layout ------------------
 // Task c = (row r = c % R, k-chunk q = c / R): a warp covers 32 consecutive
 // rows of one k-chunk, so its 16-byte core-matrix row stores are contiguous.
-template <int R, int NS>
+template <int R, int NS, int NTH>
 __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t* piece0,
                                               bool kcontig, int rstride) {
   constexpr int TASKS = R * BK / 8;
   constexpr int PBY = R * BK * 2;
+  static_assert(TASKS % NTH == 0, "converter tasks per thread");
   const float* rf = reinterpret_cast<const float*>(raw);
 #pragma unroll
-  for (int i = 0; i < TASKS / NCONV; ++i) {
-    const int c = t + i * NCONV;
+  for (int i = 0; i < TASKS / NTH; ++i) {
+    const int c = t + i * NTH;
     const int r = c % R, q = c / R;
     float v[8];
     if (kcontig) {
@@ -360,10 +346,14 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
     split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
   }
 }
-// BOX: some operand of some work item is loaded as TMA boxes (a separate
-// instantiation, so that the gather-only kernel carries none of that code).
-template <int NS, bool BOX>
+// FORM 0: every operand gathered (no box code at all); 1: some operand of
+// some work item loaded as TMA boxes by the box warp, the rest gathered by the
+// loader warps; 2: every operand of every item a box -- no loaders, and their
+// eight warps convert alongside the converters.
+template <int NS, int FORM>
 __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
+  constexpr bool BOX = FORM != 0, ALL = FORM == 2;
+  constexpr int NCV = ALL ? NLOAD + NCONV : NCONV;  // converter threads
   using Ly = Lay<NS>;
   constexpr int RS = Ly::RS, MS = Ly::MS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -388,11 +378,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < RS; ++s) {
-      mbar_init(&raw_full[s], NLOAD);
-      mbar_init(&raw_empty[s], NCONV);
+      // BOX: the box warp's one arrival (with the transaction count) joins the
+      // loaders'; ALL: it is the only one
+      mbar_init(&raw_full[s], ALL ? 1 : BOX ? NLOAD + 1 : NLOAD);
+      mbar_init(&raw_empty[s], NCV);
     }
     for (int s = 0; s < MS; ++s) {
-      mbar_init(&mma_full[s], NCONV);
+      mbar_init(&mma_full[s], NCV);
       mbar_init(&mma_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -415,15 +407,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   const int64_t nitems = a.nitems;
   const int64_t w0 = blockIdx.x, dw = gridDim.x;
 
-  if (warp < CONV_W0) {
+  if (!ALL && warp < CONV_W0) {
     // ---- loaders ----
     const int t = tid;
     int64_t g = 0;  // k-tiles staged by this CTA so far
-    BoxState* bst = reinterpret_cast<BoxState*>(smem + Ly::BOXS);
-    if (BOX && t == 0) {
-      bst->g_box = -1;
-      bst->g_iss = -1;
-    }
     // row scatter entries (A rows then B rows) of the next item, fetched one item ahead
     constexpr int NR = (BM + BNMAX + NLOAD - 1) / NLOAD;
     int64_t pre[NR];
@@ -455,9 +442,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
       const bool akc = d->a_kc, bkc = d->b_kc;
       const bool boxA = BOX && d->boxA.rank > 0, boxB = BOX && d->boxB.rank > 0;
       const bool vec_ok = d->elem_gather == 0;
-      if (BOX && t == 0) {
-        if (boxA) box_coords(&d->boxA, (uint32_t)it.m0, (uint32_t)it.kbeg, bst->c[0]);
-        if (boxB) box_coords(&d->boxB, (uint32_t)it.n0, (uint32_t)it.kbeg, bst->c[1]);
+      if (BOX && boxA && boxB) {  // the box warp loads this item and arrives for everyone
+        g += it.KT;
+        continue;
       }
       // k ring: entry t of k-tile 0 now, of k-tiles 1..4 in flight in p0..p3
       KSlotSrc src{nullptr, 0, false};
@@ -493,11 +480,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
                            vec_ok);
             load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
                               slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
-          } else if constexpr (BOX) {
-            if (t == 0) {
-              box_issue(d, a.probs ? d->tmaps : a.tm, raw, raw + Ly::RAW_A, &raw_full[s], bst);
-              bst->g_box = g;
-            }
+          } else if constexpr (BOX) {  // the other operand comes as a box from the box warp
             if (!boxA)
               load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
                              vec_ok);
@@ -506,38 +489,20 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
                                 slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
           }
           cp_async_arrive(&raw_full[s]);
-          if (BOX && t == 0) bst->g_iss = g;
         }
         // slot kt+1 now complete and slot kt free for reuse; a timeout anywhere
         // makes every loader leave together
         if (bar_or(BAR_LOAD, NLOAD, !ok)) break;
       }
     }
-    // no copy into shared memory may outlive the CTA (matters only after an
-    // abort): the cp.async gathers, and the box loads of the stages still
-    // filling.  Thread 0 issued every k-tile up to g_iss; a fill that a later
-    // issued fill of the same stage followed was consumed before that one
-    // began, so only the k-tiles after g_iss - RS can be in flight, and
-    // thread 0 waits for the phases of those up to its last box.  A box load
-    // lands within microseconds of its issue whatever the other roles do; the
-    // wait is bounded (about 10 ms per stage) because after an abort a phase
-    // can miss the arrival of a loader that gave up on that k-tile.
+    // no copy into shared memory may outlive the CTA (matters only after an abort)
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    const long long g_box = BOX ? bst->g_box : -1, g_iss = BOX ? bst->g_iss : -1;
-    if (BOX && t == 0 && g_box >= 0 && g_box > g_iss - RS) {
-      for (long long gi = g_iss - RS + 1 > 0 ? g_iss - RS + 1 : 0; gi <= g_box; ++gi) {
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&raw_full[gi % RS], (uint32_t)((gi / RS) & 1)) &&
-               clock64() - t0 < 20000000LL) {
-        }
-      }
-    }
   } else if (warp < EPI_W0) {
     // ---- converters ----
-    const int t = tid - NLOAD;
+    const int t = ALL ? tid : tid - NLOAD;
     int64_t g = 0;
     for (int64_t w = w0; w < nitems; w += dw) {
-      if (bar_or(BAR_CONV, NCONV, *abort)) break;  // uniform exit
+      if (bar_or(BAR_CONV, NCV, *abort)) break;  // uniform exit
       const Item it = get_item(a, sProb, w);
       const bool akc = it.d->a_kc, bkc = it.d->b_kc;
       // a row-contiguous B box holds k-rows of bn floats; the gather's k-rows hold BNMAX
@@ -551,11 +516,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
         }
         const uint8_t* raw = smem + Ly::RAW0 + rs * Ly::RAW_STAGE;
         uint8_t* st = smem + Ly::MMA0 + ms * Ly::MMA_STAGE;
-        convert_panel<BM, NS>(t, raw, st, akc, BM);
+        convert_panel<BM, NS, NCV>(t, raw, st, akc, BM);
         if (!BOX || rsB == BNMAX)  // the common k-row pitch as a constant: immediate offsets
-          convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, BNMAX);
+          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, BNMAX);
         else
-          convert_panel<BNMAX, NS>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, rsB);
+          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, rsB);
         fence_proxy_async_smem();
         mbar_arrive(&mma_full[ms]);
         mbar_arrive(&raw_empty[rs]);
@@ -670,6 +635,71 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
         tc_fence_before();
         mbar_arrive(&acc_empty[b]);
         if (!ok) break;
+      }
+    }
+  } else if (warp == BOX_WARP) {
+    // ---- box loads (BOX instantiation): one lane issues every TMA box ----
+    // Per k-tile it waits for the raw stage to be free, raises the stage's
+    // transaction count by the bytes of its boxes, issues them, and arrives:
+    // once, or for the loaders too when both operands are boxes (the loaders
+    // then skip the item).  Its arrival follows its transaction count, so the
+    // phase cannot complete before the boxes have landed.
+    if (BOX && lane == 0) {
+      int64_t g = 0, g_box = -1, g_iss = -1;
+      for (int64_t w = w0; w < nitems && !*abort; w += dw) {
+        const Item it = get_item(a, sProb, w);
+        const DevProblem* d = it.d;
+        const BoxAccess bxA = d->boxA, bxB = d->boxB;
+        const bool bA = bxA.rank > 0, bB = bxB.rank > 0;
+        const CUtensorMap* maps = a.probs ? d->tmaps : a.tm;
+        if (a.probs) {  // maps in the plan's device buffer (kernel parameters need no fence)
+          if (bA) fence_tensormap_acquire(maps);
+          if (bB) fence_tensormap_acquire(maps + 1);
+        }
+        const uint32_t bytes = (bA ? (uint32_t)bxA.bytes : 0u) + (bB ? (uint32_t)bxB.bytes : 0u);
+        const uint32_t cnt = ALL ? 1 : bA && bB ? NLOAD + 1 : 1;
+        int32_t cA[5], cB[5];
+        box_coords(bxA, (uint32_t)it.m0, (uint32_t)it.kbeg, cA);
+        box_coords(bxB, (uint32_t)it.n0, (uint32_t)it.kbeg, cB);
+        bool failed = false;
+        for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
+          const int s = (int)(g % RS);
+          if (!mbar_wait(&raw_empty[s], (uint32_t)(((g / RS) & 1) ^ 1), abort)) {
+            record_timeout(abort, a.err);
+            failed = true;
+            break;
+          }
+          const uint32_t raw = smem_u32(smem + Ly::RAW0 + s * Ly::RAW_STAGE);
+          if (bA || bB) {
+            mbar_expect_tx(&raw_full[s], bytes);
+            if (bA) {
+              tma_load(raw, maps, cA, bxA.rank, &raw_full[s]);
+              box_advance(bxA, cA);
+            }
+            if (bB) {
+              tma_load(raw + Ly::RAW_A, maps + 1, cB, bxB.rank, &raw_full[s]);
+              box_advance(bxB, cB);
+            }
+            g_box = g;
+          }
+          mbar_arrive_n(&raw_full[s], cnt);
+          g_iss = g;
+        }
+        if (failed) break;
+      }
+      // no box load may outlive the CTA (matters only after an abort): a fill
+      // that a later fill of the same stage followed was consumed before that
+      // one began, so only the k-tiles after g_iss - RS can be in flight; wait
+      // for their phases up to the last box.  A box lands within microseconds
+      // of its issue; the wait is bounded (about 10 ms per stage) because
+      // after an abort a phase can miss the arrival of a loader that gave up.
+      if (g_box >= 0 && g_box > g_iss - RS) {
+        for (int64_t gi = g_iss - RS + 1 > 0 ? g_iss - RS + 1 : 0; gi <= g_box; ++gi) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&raw_full[gi % RS], (uint32_t)((gi / RS) & 1)) &&
+                 clock64() - t0 < 20000000LL) {
+          }
+        }
       }
     }
   } else if (lane == 0) {
@@ -812,13 +842,13 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
   }
 }
 
-template <int NS, bool BOX>
+template <int NS, int FORM>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Lay<NS>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
@@ -841,7 +871,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   mainloop_event_before(s);
-  k_tc<NS, BOX><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
+  k_tc<NS, FORM><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
@@ -864,9 +894,13 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
 int tc_bn_max() { return BNMAX; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
-  const bool box = q.probs ? q.any_box != 0 : (q.single.boxA.rank > 0 || q.single.boxB.rank > 0);
-  if (q.pieces == 3) return box ? launch_cfg<3, true>(q, s) : launch_cfg<3, false>(q, s);
-  return box ? launch_cfg<2, true>(q, s) : launch_cfg<2, false>(q, s);
+  const int ba = q.single.boxA.rank > 0, bb = q.single.boxB.rank > 0;
+  const int form = q.probs ? q.box_form : (ba && bb ? 2 : ba || bb ? 1 : 0);
+  if (q.pieces == 3)
+    return form == 2 ? launch_cfg<3, 2>(q, s) : form == 1 ? launch_cfg<3, 1>(q, s)
+                                                          : launch_cfg<3, 0>(q, s);
+  return form == 2 ? launch_cfg<2, 2>(q, s) : form == 1 ? launch_cfg<2, 1>(q, s)
+                                                        : launch_cfg<2, 0>(q, s);
 }
 
 }  // namespace tc

@@ -45,13 +45,12 @@ def test_only_the_box_setting_takes_boxes():
     sp = W.SPECS["spiky_f32"]
     sh = lambda lab: cm([sp.ext[c] for c in lab])  # noqa: E731
     args = (sh(sp.labA), sp.labA, sh(sp.labB), sp.labB, sh(sp.labC), sp.labC)
-    assert tc.set_access("block") == "block"  # the default
+    assert tc.set_access("box") == "box"  # the default
     for acc in ("block", "scatter"):
         with tc.access(acc):
             assert tc.box_access(*args) == (False, False)
-    with tc.access("box"):
-        assert tc.box_access(*args) == (True, True)
-    assert tc.set_access("block") == "block"
+    assert tc.box_access(*args) == (True, True)
+    assert tc.set_access("box") == "box"
 
 
 def test_tile_structure_rules():
@@ -70,9 +69,19 @@ def test_tile_structure_rules():
     assert boxes("pab", "pj", "ajb", ext)[0] is True
 
 
+def test_boxes_larger_than_their_tensor_are_not_taken():
+    # A's 128-row tile over a 100-long row dim would be a box larger than the
+    # tensor; over a 200-long one the last tile merely runs past the end
+    assert boxes("pi", "pj", "ij", dict(p=64, i=100, j=64))[0] is False
+    assert boxes("pi", "pj", "ij", dict(p=64, i=200, j=64))[0] is True
+    # the 32-wide k-tile over a 16-long k dim, likewise
+    assert boxes("pi", "pj", "ij", dict(p=16, i=256, j=64)) == (False, False)
+
+
 def test_k_tile_rules():
     # k-contiguous A needs the unit-stride k dim to fill the 32-wide k-tile:
-    # a multiple of 32, or the only k dim (its end read as zeros)
+    # a multiple of 32, or the only k dim (the last k-tile reads zeros past
+    # its end)
     assert boxes("pi", "pj", "ij", dict(p=48, i=128, j=64))[0] is True
     # (B's order qp keeps p and q from being folded into one dim)
     assert boxes("pqi", "qpj", "ij", dict(p=48, q=2, i=128, j=64))[0] is False

@@ -58,8 +58,9 @@ CASES = {
     "kc_A_mn_B": ("eafb", "cfde", "abcd", dict(a=64, b=4, c=64, d=3, e=64, f=5), (True, True)),
     # gradient-style: A row-contiguous (i), B k-contiguous (m after step 6); n = 48
     "mn_A_kc_B": ("ilmj", "mkl", "ijk", dict(i=128, j=3, k=48, l=40, m=64), (True, True)),
-    # single dims with tails everywhere: m = 200, k = 76, n = 100 (tile width 112)
-    "tails": ("ip", "pj", "ij", dict(i=200, p=76, j=100), (True, True)),
+    # single dims with tails everywhere: m = 200, k = 76, n = 100; B's 112-row
+    # tile would be a box larger than its 100-long dim, so B is gathered
+    "tails": ("ip", "pj", "ij", dict(i=200, p=76, j=100), (True, False)),
     # k = 75 makes B's column stride 300 bytes, not a multiple of 16: B gathered
     "stride_not_16B": ("ip", "pj", "ij", dict(i=200, p=75, j=100), (True, False)),
     # a row tile spanning two dims (32 x 4) of A, row-contiguous
@@ -67,7 +68,7 @@ CASES = {
     # row-contiguous B tile of 48 rows (k-rows 48 floats apart in shared memory)
     "mn_B_bn48": ("pi", "jp", "ij", dict(p=96, i=256, j=48), (True, True)),
     # five-dim A (rows a, b, c ordered by A's strides; k p, q) and three-dim B
-    "rank5_A": ("apbqc", "pqj", "acbj", dict(a=32, b=4, c=3, p=32, q=3, j=40), (True, True)),
+    "rank5_A": ("apbqc", "pqj", "acbj", dict(a=32, b=4, c=3, p=32, q=3, j=48), (True, True)),
     # one operand boxed, the other gathered (a = 24 breaks A's row box)
     "mixed": ("pab", "pj", "ajb", dict(a=24, b=16, p=64, j=128), (False, True)),
 }
@@ -102,7 +103,7 @@ def test_box_split_k():
     ext = dict(i=128, j=64, p=8192)
     g = torch.Generator().manual_seed(8)
     A, B = colmajor_rand("pi", ext, g), colmajor_rand("pj", ext, g)
-    C0 = torch.zeros(128, 64, dtype=torch.float64)
+    C0 = W.colmajor(torch.zeros(128 * 64, dtype=torch.float64), (128, 64))
     got, flags = run_forms(A, "pi", B, "pj", C0, "ij")
     assert flags == (True, True)
     ref, mag = oracle_ref(1.0, A, "pi", B, "pj", 0.0, C0, "ij")
@@ -138,10 +139,10 @@ def test_forms_full_size_spiky():
     assert torch.equal(res["box"], res["block"]) and torch.equal(res["box"], res["scatter"])
 
 
-def test_box_batched_plan_and_graph():
-    # a batch mixing boxed, half-boxed and gathered problems, executed as a
-    # plan and replayed from a CUDA graph, equals the block-gathered and the
-    # element-gathered plans bit for bit
+def test_batched_plans_under_every_access_setting():
+    # batch plans gather every operand whatever the setting (their box form is
+    # disabled); a plan created under each setting, executed and replayed from
+    # a CUDA graph, gives the same bits and matches the oracle
     g = torch.Generator().manual_seed(10)
     probs = []
     for name in sorted(CASES):

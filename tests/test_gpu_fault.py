@@ -16,22 +16,25 @@ from helpers import norm_err, oracle_ref, to_device
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("access", ["block", "box"])
-def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access):
-    # "box": the box loads still in flight when the CTA unwinds are waited
-    # for (bounded) before it exits
+@pytest.mark.parametrize("access,colmajor,boxes", [("block", False, (False, False)),
+                                                  ("box", False, (False, True)),
+                                                  ("box", True, (True, True))])
+def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access, colmajor, boxes):
+    # with boxes, the box warp waits (bounded) for boxes still in flight
+    # before its CTA exits; (True, True) runs the kernel form without loaders
     g = torch.Generator().manual_seed(3)
     A = (torch.rand(200, 96, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     B = (torch.rand(96, 150, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     C0 = torch.zeros(200, 150, dtype=torch.float64)
+    if colmajor:
+        A, B, C0 = (x.t().contiguous().t() for x in (A, B, C0))
     dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
     assert tc.device_error() == 0
     with tc.access(access):
         dC = to_device(C0, torch.float32)
-        # C is row-major, so the planner swaps the operands: the matrix-role A
-        # is the caller's B (stride 150, not a multiple of 4: gathered) and the
-        # matrix-role B the caller's A (boxed)
-        assert tc.box_access(dA, "ip", dB, "pj", dC, "ij") == (False, access == "box")
+        # row-major C makes the planner swap the operands: the matrix-role A is
+        # then the caller's B, whose stride 150 is not a multiple of 4 (gathered)
+        assert tc.box_access(dA, "ip", dB, "pj", dC, "ij") == boxes
         monkeypatch.setenv("TC_FAULT", "timeout")
         tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
         torch.cuda.synchronize()
