@@ -168,9 +168,17 @@ void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_b
   const int acc = g_access.load();
   d.elem_gather = acc == TC_ACCESS_SCATTER ? 1 : 0;
   if (!allow_box || acc != TC_ACCESS_BOX || L.m <= 0 || L.n <= 0 || L.k <= 0) return;
-  make_box(L.I, L.I.s0, L.P, L.P.s0, d.a, kTileM, d.a_kc != 0, maps ? &maps[0] : nullptr,
-           &d.boxA);
-  make_box(L.J, L.J.s0, L.P, L.P.s1, d.b, d.bn, d.b_kc != 0, maps ? &maps[1] : nullptr, &d.boxB);
+  // both operands or neither: with one operand boxed and the other gathered
+  // the kernel would need loader warps and the box warp on one stage, which
+  // measured slower than gathering both
+  const bool a_ok = make_box(L.I, L.I.s0, L.P, L.P.s0, d.a, kTileM, d.a_kc != 0,
+                             maps ? &maps[0] : nullptr, &d.boxA);
+  const bool b_ok = make_box(L.J, L.J.s0, L.P, L.P.s1, d.b, d.bn, d.b_kc != 0,
+                             maps ? &maps[1] : nullptr, &d.boxB);
+  if (!(a_ok && b_ok)) {
+    std::memset(&d.boxA, 0, sizeof d.boxA);
+    std::memset(&d.boxB, 0, sizeof d.boxB);
+  }
 }
 
 bool box_encoder_available() { return encoder() != nullptr; }

@@ -232,7 +232,6 @@ struct tc_plan {
   int64_t max_m_split = 0, max_n_split = 0;
   int pieces = 2;
   int64_t ctas = 152;
-  int box_form = 0;  // 0: no TMA boxes, 1: some operands, 2: every operand of every problem
 };
 
 namespace {
@@ -442,8 +441,6 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       // the GPU on the 512-problem workload, cause not yet found
       plan_access(p.L, d, &maps[2 * (size_t)i], /*allow_box=*/false);
       d.tmaps = d_maps + 2 * (size_t)i;
-      const int f = d.boxA.rank > 0 && d.boxB.rank > 0 ? 2 : d.boxA.rank > 0 || d.boxB.rank > 0 ? 1 : 0;
-      pl->box_form = i == 0 ? f : (pl->box_form == f ? f : (pl->box_form || f ? 1 : 0));
     }
   }
   auto up = [](void* dst, const void* src, size_t bytes) {
@@ -528,7 +525,6 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
-    q.box_form = plan->box_form;
     q.err = err_word();
     e = launch_tc(q, s);
   }

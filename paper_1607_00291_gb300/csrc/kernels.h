@@ -124,7 +124,6 @@ struct TcLaunch {
   int64_t split_cols;         // batch: total columns of the split problems
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
-  int32_t box_form;           // batch: 0 no TMA boxes, 1 some operands, 2 every operand
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path

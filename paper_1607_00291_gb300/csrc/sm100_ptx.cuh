@@ -25,14 +25,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
       "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(bar))
       : "memory");
 }
-// `count` arrivals at once.
-__device__ __forceinline__ void mbar_arrive_n(uint64_t* bar, uint32_t count) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_u32(bar)),
-      "r"(count)
-      : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

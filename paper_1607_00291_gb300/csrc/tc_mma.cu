@@ -346,14 +346,13 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
     split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
   }
 }
-// FORM 0: every operand gathered (no box code at all); 1: some operand of
-// some work item loaded as TMA boxes by the box warp, the rest gathered by the
-// loader warps; 2: every operand of every item a box -- no loaders, and their
-// eight warps convert alongside the converters.
-template <int NS, int FORM>
+// BOX = false: the loader warps gather every operand through the scatter
+// vectors (no box code at all).  BOX = true: both operands of every work item
+// are TMA boxes, issued by the box warp; there are no loaders, and their eight
+// warps convert alongside the converters.
+template <int NS, bool BOX>
 __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
-  constexpr bool BOX = FORM != 0, ALL = FORM == 2;
-  constexpr int NCV = ALL ? NLOAD + NCONV : NCONV;  // converter threads
+  constexpr int NCV = BOX ? NLOAD + NCONV : NCONV;  // converter threads
   using Ly = Lay<NS>;
   constexpr int RS = Ly::RS, MS = Ly::MS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -378,9 +377,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < RS; ++s) {
-      // BOX: the box warp's one arrival (with the transaction count) joins the
-      // loaders'; ALL: it is the only one
-      mbar_init(&raw_full[s], ALL ? 1 : BOX ? NLOAD + 1 : NLOAD);
+      // BOX: the box warp's one arrival, with the transaction count
+      mbar_init(&raw_full[s], BOX ? 1 : NLOAD);
       mbar_init(&raw_empty[s], NCV);
     }
     for (int s = 0; s < MS; ++s) {
@@ -407,7 +405,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   const int64_t nitems = a.nitems;
   const int64_t w0 = blockIdx.x, dw = gridDim.x;
 
-  if (!ALL && warp < CONV_W0) {
+  if (!BOX && warp < CONV_W0) {
     // ---- loaders ----
     const int t = tid;
     int64_t g = 0;  // k-tiles staged by this CTA so far
@@ -440,12 +438,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
-      const bool boxA = BOX && d->boxA.rank > 0, boxB = BOX && d->boxB.rank > 0;
       const bool vec_ok = d->elem_gather == 0;
-      if (BOX && boxA && boxB) {  // the box warp loads this item and arrives for everyone
-        g += it.KT;
-        continue;
-      }
       // k ring: entry t of k-tile 0 now, of k-tiles 1..4 in flight in p0..p3
       KSlotSrc src{nullptr, 0, false};
       int64_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
@@ -475,19 +468,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
           const uint32_t raw = smem_u32(smem + Ly::RAW0 + s * Ly::RAW_STAGE);
           const int64_t* slot = kring + (kt % KRING) * KSLOT;
           const int64_t k0 = it.kbeg + kt * BK;
-          if (!(boxA || boxB)) {  // both gathered: one block, so the two panels interleave
-            load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
-                           vec_ok);
-            load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
-                              slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
-          } else if constexpr (BOX) {  // the other operand comes as a box from the box warp
-            if (!boxA)
-              load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
-                             vec_ok);
-            if (!boxB)
-              load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
-                                slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
-          }
+          load_panel<BM>(t, raw, A, sRA, it.rows_a, slot, slot + 2 * BK, k0, it.kend, akc,
+                         vec_ok);
+          load_panel<BNMAX>(t, raw + Ly::RAW_A, B, sRA + BM, it.rows_b, slot + BK,
+                            slot + 2 * BK + BK / 4, k0, it.kend, bkc, vec_ok);
           cp_async_arrive(&raw_full[s]);
         }
         // slot kt+1 now complete and slot kt free for reuse; a timeout anywhere
@@ -499,14 +483,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   } else if (warp < EPI_W0) {
     // ---- converters ----
-    const int t = ALL ? tid : tid - NLOAD;
+    const int t = BOX ? tid : tid - NLOAD;
     int64_t g = 0;
     for (int64_t w = w0; w < nitems; w += dw) {
       if (bar_or(BAR_CONV, NCV, *abort)) break;  // uniform exit
       const Item it = get_item(a, sProb, w);
       const bool akc = it.d->a_kc, bkc = it.d->b_kc;
       // a row-contiguous B box holds k-rows of bn floats; the gather's k-rows hold BNMAX
-      const int rsB = BOX && it.d->boxB.rank > 0 ? it.d->bn : BNMAX;
+      const int rsB = BOX && !it.d->b_kc ? it.d->bn : BNMAX;
       for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
         const int rs = (int)(g % RS), ms = (int)(g % MS);
         if (!mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) ||
@@ -640,24 +624,21 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
   } else if (warp == BOX_WARP) {
     // ---- box loads (BOX instantiation): one lane issues every TMA box ----
     // Per k-tile it waits for the raw stage to be free, raises the stage's
-    // transaction count by the bytes of its boxes, issues them, and arrives:
-    // once, or for the loaders too when both operands are boxes (the loaders
-    // then skip the item).  Its arrival follows its transaction count, so the
-    // phase cannot complete before the boxes have landed.
+    // transaction count by the bytes of its two boxes, issues them, and
+    // arrives.  Its arrival follows its transaction count, so the phase
+    // cannot complete before the boxes have landed.
     if (BOX && lane == 0) {
-      int64_t g = 0, g_box = -1, g_iss = -1;
+      int64_t g = 0, g_iss = -1;  // the last k-tile whose boxes were issued
       for (int64_t w = w0; w < nitems && !*abort; w += dw) {
         const Item it = get_item(a, sProb, w);
         const DevProblem* d = it.d;
         const BoxAccess bxA = d->boxA, bxB = d->boxB;
-        const bool bA = bxA.rank > 0, bB = bxB.rank > 0;
         const CUtensorMap* maps = a.probs ? d->tmaps : a.tm;
         if (a.probs) {  // maps in the plan's device buffer (kernel parameters need no fence)
-          if (bA) fence_tensormap_acquire(maps);
-          if (bB) fence_tensormap_acquire(maps + 1);
+          fence_tensormap_acquire(maps);
+          fence_tensormap_acquire(maps + 1);
         }
-        const uint32_t bytes = (bA ? (uint32_t)bxA.bytes : 0u) + (bB ? (uint32_t)bxB.bytes : 0u);
-        const uint32_t cnt = ALL ? 1 : bA && bB ? NLOAD + 1 : 1;
+        const uint32_t bytes = (uint32_t)bxA.bytes + (uint32_t)bxB.bytes;
         int32_t cA[5], cB[5];
         box_coords(bxA, (uint32_t)it.m0, (uint32_t)it.kbeg, cA);
         box_coords(bxB, (uint32_t)it.n0, (uint32_t)it.kbeg, cB);
@@ -670,31 +651,23 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
             break;
           }
           const uint32_t raw = smem_u32(smem + Ly::RAW0 + s * Ly::RAW_STAGE);
-          if (bA || bB) {
-            mbar_expect_tx(&raw_full[s], bytes);
-            if (bA) {
-              tma_load(raw, maps, cA, bxA.rank, &raw_full[s]);
-              box_advance(bxA, cA);
-            }
-            if (bB) {
-              tma_load(raw + Ly::RAW_A, maps + 1, cB, bxB.rank, &raw_full[s]);
-              box_advance(bxB, cB);
-            }
-            g_box = g;
-          }
-          mbar_arrive_n(&raw_full[s], cnt);
+          mbar_expect_tx(&raw_full[s], bytes);
+          tma_load(raw, maps, cA, bxA.rank, &raw_full[s]);
+          tma_load(raw + Ly::RAW_A, maps + 1, cB, bxB.rank, &raw_full[s]);
+          box_advance(bxA, cA);
+          box_advance(bxB, cB);
+          mbar_arrive(&raw_full[s]);
           g_iss = g;
         }
         if (failed) break;
       }
       // no box load may outlive the CTA (matters only after an abort): a fill
       // that a later fill of the same stage followed was consumed before that
-      // one began, so only the k-tiles after g_iss - RS can be in flight; wait
-      // for their phases up to the last box.  A box lands within microseconds
-      // of its issue; the wait is bounded (about 10 ms per stage) because
-      // after an abort a phase can miss the arrival of a loader that gave up.
-      if (g_box >= 0 && g_box > g_iss - RS) {
-        for (int64_t gi = g_iss - RS + 1 > 0 ? g_iss - RS + 1 : 0; gi <= g_box; ++gi) {
+      // one began, so only the last RS k-tiles can be in flight; wait for
+      // their phases.  A box lands within microseconds of its issue; the wait
+      // is bounded (about 10 ms per stage) all the same.
+      if (g_iss >= 0) {
+        for (int64_t gi = g_iss - RS + 1 > 0 ? g_iss - RS + 1 : 0; gi <= g_iss; ++gi) {
           const long long t0 = clock64();
           while (!mbar_try_wait(&raw_full[gi % RS], (uint32_t)((gi / RS) & 1)) &&
                  clock64() - t0 < 20000000LL) {
@@ -842,13 +815,13 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
   }
 }
 
-template <int NS, int FORM>
+template <int NS, bool BOX>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Lay<NS>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
@@ -871,7 +844,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   mainloop_event_before(s);
-  k_tc<NS, FORM><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
+  k_tc<NS, BOX><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
@@ -894,13 +867,11 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
 int tc_bn_max() { return BNMAX; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
-  const int ba = q.single.boxA.rank > 0, bb = q.single.boxB.rank > 0;
-  const int form = q.probs ? q.box_form : (ba && bb ? 2 : ba || bb ? 1 : 0);
-  if (q.pieces == 3)
-    return form == 2 ? launch_cfg<3, 2>(q, s) : form == 1 ? launch_cfg<3, 1>(q, s)
-                                                          : launch_cfg<3, 0>(q, s);
-  return form == 2 ? launch_cfg<2, 2>(q, s) : form == 1 ? launch_cfg<2, 1>(q, s)
-                                                        : launch_cfg<2, 0>(q, s);
+  // boxes only when every work item has both operands as boxes (the planner
+  // sets both or neither; batch plans set neither)
+  const bool box = !q.probs && q.single.boxA.rank > 0 && q.single.boxB.rank > 0;
+  if (q.pieces == 3) return box ? launch_cfg<3, true>(q, s) : launch_cfg<3, false>(q, s);
+  return box ? launch_cfg<2, true>(q, s) : launch_cfg<2, false>(q, s);
 }
 
 }  // namespace tc

@@ -2,9 +2,10 @@
 operands take one TMA box per tile and which are gathered through scatter
 vectors.  A tile of T consecutive linear indices of a bundle is a box when it
 covers the bundle's leading dims whole and a divisor-sized run of the next
-one (the bundle's last dim may run past its end); the operand's unit-stride
-dim must lead the bundle the access flag names; at most 5 dims; FP32 strides
-multiples of 4 elements."""
+one (the bundle's last dim may run past its end), no box extent above its
+dim's length; the operand's unit-stride dim must lead the bundle the access
+flag names; at most 5 dims; FP32 strides multiples of 4 elements; and both
+operands qualify, or neither is taken."""
 import pytest
 
 import paper_1607_00291_gb300 as tc
@@ -54,26 +55,28 @@ def test_only_the_box_setting_takes_boxes():
 
 
 def test_tile_structure_rules():
-    # C keeps j between the row dims, so the planner cannot fold them
+    # boxes are taken for both operands or for neither; B = pj (k-contiguous,
+    # 64- or 128-row tiles) is a box throughout, so the pair follows A.
+    # C keeps j between the row dims, so the planner cannot fold them.
     # rows: I = (a, b) with a = 24 does not tile 128 rows into a box
     ext = dict(a=24, b=16, p=64, j=128)
-    assert boxes("pab", "pj", "ajb", ext)[0] is False
+    assert boxes("pab", "pj", "ajb", ext) == (False, False)
     # a = 32 and b divisible by 128 / 32 = 4: a box (32 x 4)
     ext = dict(a=32, b=8, p=64, j=128)
-    assert boxes("pab", "pj", "ajb", ext)[0] is True
+    assert boxes("pab", "pj", "ajb", ext) == (True, True)
     # b = 6 is not a multiple of 4 and not the last row dim (c follows)
     ext = dict(a=32, b=6, c=2, p=64, j=64)
-    assert boxes("pacb", "pj", "ajbc", ext)[0] is False
+    assert boxes("pacb", "pj", "ajbc", ext) == (False, False)
     # ... but as the last row dim it may run past its end
     ext = dict(a=32, b=6, p=64, j=64)
-    assert boxes("pab", "pj", "ajb", ext)[0] is True
+    assert boxes("pab", "pj", "ajb", ext) == (True, True)
 
 
 def test_boxes_larger_than_their_tensor_are_not_taken():
     # A's 128-row tile over a 100-long row dim would be a box larger than the
     # tensor; over a 200-long one the last tile merely runs past the end
-    assert boxes("pi", "pj", "ij", dict(p=64, i=100, j=64))[0] is False
-    assert boxes("pi", "pj", "ij", dict(p=64, i=200, j=64))[0] is True
+    assert boxes("pi", "pj", "ij", dict(p=64, i=100, j=64)) == (False, False)
+    assert boxes("pi", "pj", "ij", dict(p=64, i=200, j=64)) == (True, True)
     # the 32-wide k-tile over a 16-long k dim, likewise
     assert boxes("pi", "pj", "ij", dict(p=16, i=256, j=64)) == (False, False)
 
@@ -81,29 +84,36 @@ def test_boxes_larger_than_their_tensor_are_not_taken():
 def test_k_tile_rules():
     # k-contiguous A needs the unit-stride k dim to fill the 32-wide k-tile:
     # a multiple of 32, or the only k dim (the last k-tile reads zeros past
-    # its end)
-    assert boxes("pi", "pj", "ij", dict(p=48, i=128, j=64))[0] is True
-    # (B's order qp keeps p and q from being folded into one dim)
-    assert boxes("pqi", "qpj", "ij", dict(p=48, q=2, i=128, j=64))[0] is False
-    assert boxes("pqi", "qpj", "ij", dict(p=64, q=3, i=128, j=64))[0] is True
-    assert boxes("pqi", "qpj", "ij", dict(p=16, q=4, i=128, j=64))[0] is False
+    # its end).  B = jqp is row-contiguous, its k box follows the same
+    # structure, and q before p keeps the planner from folding p and q.
+    assert boxes("pi", "jp", "ij", dict(p=48, i=128, j=64)) == (True, True)
+    assert boxes("pqi", "jqp", "ij", dict(p=48, q=2, i=128, j=64)) == (False, False)
+    assert boxes("pqi", "jqp", "ij", dict(p=64, q=3, i=128, j=64)) == (True, True)
+    assert boxes("pqi", "jqp", "ij", dict(p=16, q=4, i=128, j=64)) == (False, False)
+
+
+def test_both_operands_or_neither():
+    # A alone would be a box (k = 75 makes B's column stride 300 bytes, not a
+    # multiple of 16): neither is taken
+    assert boxes("ip", "pj", "ij", dict(i=256, p=75, j=128)) == (False, False)
+    assert boxes("ip", "pj", "ij", dict(i=256, p=76, j=128)) == (True, True)
 
 
 def test_rank_and_stride_rules():
     # six dims in A: more than a tensor map holds
     ext = dict(a=32, b=2, c=2, p=32, q=2, r=2, j=16)
-    assert boxes("apbqcr", "pqrj", "acbj", ext)[0] is False
+    assert boxes("apbqcr", "pqrj", "acbj", ext) == (False, False)
     # a stride that is not a multiple of 4 FP32 elements (16 bytes)
     B = ((64, 64), (1, 64))
     C = ((128, 64), (1, 128))
     with tc.access("box"):
         A = ((128, 64), (1, 130))
-        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is False
+        assert tc.box_access(A, "ip", B, "pj", C, "ij") == (False, False)
         A = ((128, 64), (1, 132))
-        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is True
+        assert tc.box_access(A, "ip", B, "pj", C, "ij") == (True, True)
         # negative or zero strides are gathered
         A = ((128, 64), (1, -128))
-        assert tc.box_access(A, "ip", B, "pj", C, "ij")[0] is False
+        assert tc.box_access(A, "ip", B, "pj", C, "ij") == (False, False)
 
 
 def test_fp64_mode_has_no_box_plan():

@@ -58,19 +58,22 @@ CASES = {
     "kc_A_mn_B": ("eafb", "cfde", "abcd", dict(a=64, b=4, c=64, d=3, e=64, f=5), (True, True)),
     # gradient-style: A row-contiguous (i), B k-contiguous (m after step 6); n = 48
     "mn_A_kc_B": ("ilmj", "mkl", "ijk", dict(i=128, j=3, k=48, l=40, m=64), (True, True)),
-    # single dims with tails everywhere: m = 200, k = 76, n = 100; B's 112-row
-    # tile would be a box larger than its 100-long dim, so B is gathered
-    "tails": ("ip", "pj", "ij", dict(i=200, p=76, j=100), (True, False)),
-    # k = 75 makes B's column stride 300 bytes, not a multiple of 16: B gathered
-    "stride_not_16B": ("ip", "pj", "ij", dict(i=200, p=75, j=100), (True, False)),
+    # single dims with tails: m = 200 (the second row tile runs past the end),
+    # k = 76 (the last k-tile too)
+    "tails": ("ip", "pj", "ij", dict(i=200, p=76, j=128), (True, True)),
+    # n = 100: B's 112-row tile would be a box larger than its dim, so neither
+    # operand is a box
+    "n_tail_gathered": ("ip", "pj", "ij", dict(i=200, p=76, j=100), (False, False)),
+    # k = 75 makes B's column stride 300 bytes, not a multiple of 16: gathered
+    "stride_not_16B": ("ip", "pj", "ij", dict(i=200, p=75, j=100), (False, False)),
     # a row tile spanning two dims (32 x 4) of A, row-contiguous
     "row_box_2d": ("apb", "pj", "ajb", dict(a=32, b=8, p=64, j=64), (True, True)),
     # row-contiguous B tile of 48 rows (k-rows 48 floats apart in shared memory)
     "mn_B_bn48": ("pi", "jp", "ij", dict(p=96, i=256, j=48), (True, True)),
     # five-dim A (rows a, b, c ordered by A's strides; k p, q) and three-dim B
     "rank5_A": ("apbqc", "pqj", "acbj", dict(a=32, b=4, c=3, p=32, q=3, j=48), (True, True)),
-    # one operand boxed, the other gathered (a = 24 breaks A's row box)
-    "mixed": ("pab", "pj", "ajb", dict(a=24, b=16, p=64, j=128), (False, True)),
+    # B alone would be a box (a = 24 breaks A's row box): both gathered
+    "mixed": ("pab", "pj", "ajb", dict(a=24, b=16, p=64, j=128), (False, False)),
 }
 
 

@@ -17,11 +17,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("access,colmajor,boxes", [("block", False, (False, False)),
-                                                  ("box", False, (False, True)),
+                                                  ("box", False, (False, False)),
                                                   ("box", True, (True, True))])
 def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access, colmajor, boxes):
-    # with boxes, the box warp waits (bounded) for boxes still in flight
-    # before its CTA exits; (True, True) runs the kernel form without loaders
+    # with boxes (True, True), the box warp waits (bounded) for boxes still in
+    # flight before its CTA exits
     g = torch.Generator().manual_seed(3)
     A = (torch.rand(200, 96, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     B = (torch.rand(96, 150, generator=g, dtype=torch.float64) * 2 - 1).float().double()
@@ -33,7 +33,8 @@ def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access, 
     with tc.access(access):
         dC = to_device(C0, torch.float32)
         # row-major C makes the planner swap the operands: the matrix-role A is
-        # then the caller's B, whose stride 150 is not a multiple of 4 (gathered)
+        # then the caller's B, whose stride 150 is not a multiple of 4, so
+        # neither operand is a box
         assert tc.box_access(dA, "ip", dB, "pj", dC, "ij") == boxes
         monkeypatch.setenv("TC_FAULT", "timeout")
         tc.contract(dA, "ip", dB, "pj", dC, "ij", mode="bf16x3")
