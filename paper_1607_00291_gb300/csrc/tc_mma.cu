@@ -53,7 +53,8 @@ using namespace ptx;
 
 constexpr int BM = 128, BK = 32;
 constexpr int NLOAD = 256, NCONV = 256, NEPI = 128;
-constexpr int NT = NLOAD + NCONV + NEPI + 64;  // + the MMA warp and the box warp
+// threads of a CTA: + the MMA warp, and the box warp in the BOX form
+constexpr int nthreads(bool box) { return NLOAD + NCONV + NEPI + (box ? 64 : 32); }
 constexpr int CONV_W0 = NLOAD / 32;
 constexpr int EPI_W0 = (NLOAD + NCONV) / 32;
 constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
@@ -351,7 +352,7 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
 // are TMA boxes, issued by the box warp; there are no loaders, and their eight
 // warps convert alongside the converters.
 template <int NS, bool BOX>
-__global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__ Args a) {
   constexpr int NCV = BOX ? NLOAD + NCONV : NCONV;  // converter threads
   using Ly = Lay<NS>;
   constexpr int RS = Ly::RS, MS = Ly::MS;
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc(const __grid_constant__ Args a) {
         if (!ok) break;
       }
     }
-  } else if (warp == BOX_WARP) {
+  } else if (BOX && warp == BOX_WARP) {
     // ---- box loads (BOX instantiation): one lane issues every TMA box ----
     // Per k-tile it waits for the raw stage to be free, raises the stage's
     // transaction count by the bytes of its two boxes, issues them, and
@@ -844,7 +845,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   mainloop_event_before(s);
-  k_tc<NS, BOX><<<(unsigned)grid, NT, Lay<NS>::ALLOC, s>>>(a);
+  k_tc<NS, BOX><<<(unsigned)grid, nthreads(BOX), Lay<NS>::ALLOC, s>>>(a);
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
