@@ -384,10 +384,10 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     for (int s = 0; s < RS; ++s) {
       // BOX: the box warp's one arrival, with the transaction count
       mbar_init(&raw_full[s], BOX ? 1 : NLOAD);
-      mbar_init(&raw_empty[s], NCV);
+      mbar_init(&raw_empty[s], NCV / 32);  // one arrival per converter warp
     }
     for (int s = 0; s < MS; ++s) {
-      mbar_init(&mma_full[s], NCV);
+      mbar_init(&mma_full[s], NCV / 32);
       mbar_init(&mma_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -498,8 +498,9 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       const int rsB = BOX && !it.d->b_kc ? it.d->bn : BNMAX;
       for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
         const int rs = (int)(g % RS), ms = (int)(g % MS);
-        if (!mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) ||
-            !mbar_wait(&mma_empty[ms], (uint32_t)(((g / MS) & 1) ^ 1), abort)) {
+        const bool ok = mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) &&
+                        mbar_wait(&mma_empty[ms], (uint32_t)(((g / MS) & 1) ^ 1), abort);
+        if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together (it arrives as one)
           record_timeout(abort, a.err);
           break;
         }
@@ -510,9 +511,14 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
           convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, BNMAX);
         else
           convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, rsB);
+        // every lane's pieces visible to the tensor core's proxy and every
+        // lane's raw reads done, then one arrival per warp on each barrier
         fence_proxy_async_smem();
-        mbar_arrive(&mma_full[ms]);
-        mbar_arrive(&raw_empty[rs]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&mma_full[ms]);
+          mbar_arrive(&raw_empty[rs]);
+        }
       }
     }
   } else if (warp < MMA_WARP) {
