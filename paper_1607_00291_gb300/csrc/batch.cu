@@ -238,8 +238,8 @@ namespace {
 
 int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const int sms = sm_count();
-  pl->ctas = sms;
   const bool f64 = pl->mode == TC_MODE_F64;
+  pl->ctas = f64 ? (int64_t)sms * f64_batch_ctas_per_sm() : sms;
   pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
   std::vector<double> alpha, beta;
   for (const tc_problem& pr : probs) {
@@ -256,7 +256,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->cfg.resize(np);
 
   // per-problem tiles and k-splits
-  const int tm_f = f64_tile_m(), tn_f = f64_tile_n(), tk_f = f64_tile_k();
+  const int tm_f = f64_batch_tile_m(), tn_f = f64_batch_tile_n(), tk_f = f64_tile_k();
   double total_cost = 0;
   std::vector<double> cost(np);
   for (int i = 0; i < np; ++i) {
@@ -314,7 +314,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     }
   }
   if (f64) {
-    const double fair = total_cost / (double)sms;
+    const double fair = total_cost / (double)pl->ctas;
     for (int i = 0; i < np; ++i) {
       const Layout& L = pl->planned[i].L;
       ProbCfg& c = pl->cfg[i];

@@ -24,12 +24,29 @@
 namespace tc {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 16, NT = 256;
-constexpr int LDA = BM + 8, LDB = BN + 8;  // row pitch (doubles); rows land 64 B apart in banks
-constexpr int A_PER_T = BM * BK / NT;
-constexpr int B_PER_T = BN * BK / NT;
-constexpr size_t kSmem = (size_t)(2 * BK * LDA + 2 * BK * LDB) * sizeof(double) +
-                         (size_t)(2 * BM + 2 * BN) * sizeof(int64_t);
+constexpr int BK = 16;
+
+// A BM_ x BN_ output tile computed by (BM_/32) x (BN_/32) warps of 32 x 32.
+// The single-contraction kernels use 128 x 64 (one 256-thread CTA per SM);
+// batches use 64 x 64 (128-thread CTAs, two per SM): the problems of a batch
+// are small, and a finer tile pads them less.
+template <int BM_, int BN_>
+struct FT {
+  static constexpr int BM = BM_, BN = BN_;
+  static constexpr int WN = BN / 32;                       // warps along n
+  static constexpr int NT = (BM / 32) * WN * 32;           // threads
+  static constexpr int LDA = BM + 8, LDB = BN + 8;  // row pitch (doubles); rows 64 B apart in banks
+  static constexpr int A_PER_T = BM * BK / NT;
+  static constexpr int B_PER_T = BN * BK / NT;
+  static constexpr size_t SMEM = (size_t)(2 * BK * LDA + 2 * BK * LDB) * sizeof(double) +
+                                 (size_t)(2 * BM + 2 * BN) * sizeof(int64_t);
+  static_assert(BM % 32 == 0 && BN % 32 == 0 && (BM * BK) % NT == 0 && (BN * BK) % NT == 0,
+                "tile shape");
+};
+using F1 = FT<128, 64>;  // single contractions
+using FB = FT<64, 64>;   // batches
+constexpr int BM = F1::BM, BN = F1::BN, NT = F1::NT;
+constexpr size_t kSmem = F1::SMEM;
 
 __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
@@ -71,14 +88,15 @@ struct F64Smem {
   int64_t *sRA, *sRC, *sCB, *sCC;
 };
 
+template <class F>
 __device__ __forceinline__ F64Smem f64_smem(unsigned char* smem) {
   F64Smem S;
   S.As = reinterpret_cast<double*>(smem);
-  S.Bs = S.As + 2 * BK * LDA;
-  S.sRA = reinterpret_cast<int64_t*>(S.Bs + 2 * BK * LDB);
-  S.sRC = S.sRA + BM;
-  S.sCB = S.sRC + BM;
-  S.sCC = S.sCB + BN;
+  S.Bs = S.As + 2 * BK * F::LDA;
+  S.sRA = reinterpret_cast<int64_t*>(S.Bs + 2 * BK * F::LDB);
+  S.sRC = S.sRA + F::BM;
+  S.sCB = S.sRC + F::BM;
+  S.sCC = S.sCB + F::BN;
   return S;
 }
 
@@ -86,13 +104,15 @@ __device__ __forceinline__ F64Smem f64_smem(unsigned char* smem) {
 // direct: apply the epilogue to C.  Otherwise store the raw FP64 sums at
 // part[nn * ldp + mm] for the tile-local (mm, nn) -- only inside the operand
 // when `bounded`.  All threads of the CTA call it together.
-template <typename T>
+template <typename T, class F>
 __device__ __forceinline__ void f64_tile(const F64Ctx<T>& P, const F64Smem& S, int64_t m0,
                                          int64_t n0, int64_t kb, int64_t ke, bool direct,
                                          double* part, int64_t ldp, bool bounded) {
+  constexpr int BM = F::BM, BN = F::BN, NT = F::NT, LDA = F::LDA, LDB = F::LDB;
+  constexpr int A_PER_T = F::A_PER_T, B_PER_T = F::B_PER_T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tig = lane & 3;
-  const int wm = warp >> 1, wn = warp & 1;
+  const int wm = warp / F::WN, wn = warp % F::WN;
   const int64_t M = P.M, N = P.N, K = P.K;
 
   // element e of a panel -> (row, k) with consecutive threads along the
@@ -217,7 +237,7 @@ __global__ void __launch_bounds__(NT, 1)
           const int64_t M, const int64_t N, const int64_t K, const double alpha, const double beta,
           const int a_kc, const int b_kc, const SkArgs sk) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const F64Smem S = f64_smem(smem);
+  const F64Smem S = f64_smem<F1>(smem);
   F64Ctx<T> P{a, b, c, sp, M, N, K, alpha, beta, a_kc, b_kc};
   const int64_t Tt = sk.tiles * sk.KT;
   const int64_t start = sk_start(blockIdx.x, Tt, sk.G), end = sk_start(blockIdx.x + 1, Tt, sk.G);
@@ -228,7 +248,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int64_t m0 = (tile / sk.tiles_n) * BM, n0 = (tile % sk.tiles_n) * BN;
     const bool whole = kb == 0 && ke == sk.KT;
     double* slot = sk.partial + ((int64_t)blockIdx.x * 2 + (it == start ? 0 : 1)) * (BM * BN);
-    f64_tile<T>(P, S, m0, n0, kb, ke, whole, slot, BM, false);
+    f64_tile<T, F1>(P, S, m0, n0, kb, ke, whole, slot, BM, false);
     it = tile * sk.KT + ke;
   }
 }
@@ -238,11 +258,12 @@ __global__ void __launch_bounds__(NT, 1)
 // finish in place; split ones leave FP64 partials in [split][n][m] for
 // k_f64_batched_reduce.
 template <typename T>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(FB::NT, 2)
     k_f64_batched(const DevProblem* __restrict__ probs, const WorkItem* __restrict__ items,
                   int64_t nitems) {
+  constexpr int BM = FB::BM, BN = FB::BN;
   extern __shared__ __align__(16) unsigned char smem[];
-  const F64Smem S = f64_smem(smem);
+  const F64Smem S = f64_smem<FB>(smem);
   for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
     const WorkItem wi = items[w];
     const DevProblem& d = probs[wi.prob];
@@ -255,7 +276,7 @@ __global__ void __launch_bounds__(NT, 1)
     double* part = d.splits > 1 ? static_cast<double*>(d.partial) +
                                       (int64_t)wi.split * d.m * d.n + n0 * d.m + m0
                                 : nullptr;
-    f64_tile<T>(P, S, m0, n0, kb, ke, d.splits == 1, part, d.m, true);
+    f64_tile<T, FB>(P, S, m0, n0, kb, ke, d.splits == 1, part, d.m, true);
   }
 }
 
@@ -361,14 +382,15 @@ cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
     cudaError_t e = cudaFuncSetAttribute(k_f64_batched<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FB::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   if (q.nitems > 0) {
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, q.nitems));
     mainloop_event_before(s);
-    k_f64_batched<T><<<(unsigned)grid, NT, kSmem, s>>>(q.probs, q.items, q.nitems);
+    k_f64_batched<T><<<(unsigned)grid, FB::NT, FB::SMEM, s>>>(q.probs, q.items, q.nitems);
     note_launch();
     if (q.n_split_probs > 0) {
       const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 16));
@@ -391,6 +413,9 @@ cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s) {
 int f64_tile_m() { return BM; }
 int f64_tile_n() { return BN; }
 int f64_tile_k() { return BK; }
+int f64_batch_tile_m() { return FB::BM; }
+int f64_batch_tile_n() { return FB::BN; }
+int f64_batch_ctas_per_sm() { return 2; }
 
 // CTAs for the FP64 mainloop: plain tiling (one CTA per tile) when the tiles
 // fill whole waves of `max_ctas` (or no partial workspace is available),

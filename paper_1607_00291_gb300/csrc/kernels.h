@@ -48,6 +48,10 @@ size_t f64_partial_bytes(int64_t max_ctas);
 int f64_tile_m();
 int f64_tile_n();
 int f64_tile_k();
+// tiles and resident CTAs per SM of the batched FP64 kernel
+int f64_batch_tile_m();
+int f64_batch_tile_n();
+int f64_batch_ctas_per_sm();
 
 // Access plan of one operand of the tensor-core mainloop (Section 7.3's
 // preference for unit-stride access, in the GPU's terms).  When the rows of a
