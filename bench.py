@@ -411,33 +411,29 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def run_paper(args, ws, rank, local):
-    """Section 9's randomly generated contractions of one matrix shape (square
-    m = n = k, or rank-k m = n >> k): three seeded contractions, 1-3 dims per
-    bundle, random label and storage orders; one step = the three tc_contract
-    calls.  Effective lengths from the flops actually performed."""
-    shape = W.PAPER_SHAPES[args.workload]
-    mode = args.mode or "f64"
-    dt = torch.float64 if mode == "f64" else torch.float32
+def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, desc, cfg_extra,
+              hbm_bytes=None, cpu=None):
+    """Time one step = the tc_contract `calls` (tuples A, labA, B, labB, C, labC, alpha,
+    beta) in order, with the same line as run_ours.  `inputs` / `outputs`: the
+    device tensors a step reads from / returns to the host (for e2e).
+    `hbm_bytes`: algorithmic DRAM bytes per step when the step is HBM-bound
+    (roofline against the measured copy bandwidth), else the tensor/FP64 pipe
+    is the denominator.  `cpu`: (spec, host arrays, index of the call) for the
+    oracle baseline."""
     warm, K = max(3, args.warmup), max(1, args.steps)
-    probs = W.paper_problems(args.workload)
-    host = [W.make_random_inputs(p, seed=shape["seed"] * 10 + i, dtype=dt) for i, p in enumerate(probs)]
-    dev = [(to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB, to_device(h["C"], dt),
-            p.labC, 1.0, 0.0) for p, h in zip(probs, host)]
-    C0 = [d[4].clone() for d in dev]
-    works = [torch.empty(max(1, tc.workspace_size(d[0], d[1], d[2], d[3], d[4], d[5], mode=mode)),
-                         dtype=torch.uint8, device="cuda") for d in dev]
-    flops = sum(p.flops() for p in probs)
+    C0 = [c[4].clone() for c in calls]
+    works = [torch.empty(max(1, tc.workspace_size(c[0], c[1], c[2], c[3], c[4], c[5], mode=mode)),
+                         dtype=torch.uint8, device="cuda") for c in calls]
     lib = L.lib()
 
     def step():
-        for d, w in zip(dev, works):
-            tc.contract(d[0], d[1], d[2], d[3], d[4], d[5], alpha=d[6], beta=d[7], mode=mode, workspace=w)
+        for c, w in zip(calls, works):
+            tc.contract(c[0], c[1], c[2], c[3], c[4], c[5], alpha=c[6], beta=c[7], mode=mode, workspace=w)
 
     for _ in range(warm):
         step()
     torch.cuda.synchronize()
-    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in dev]
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
            for _ in range(K)]
     for row in kev:
         for a, b in row:
@@ -453,9 +449,9 @@ def run_paper(args, ws, rank, local):
     launches0 = lib.tc_launch_count()
     e0.record()
     for i in range(K):
-        for (d, w), (ka, kb) in zip(zip(dev, works), kev[i]):
+        for (c, w), (ka, kb) in zip(zip(calls, works), kev[i]):
             lib.tc_set_mainloop_events(L.c_vp(ka.cuda_event), L.c_vp(kb.cuda_event))
-            tc.contract(d[0], d[1], d[2], d[3], d[4], d[5], alpha=d[6], beta=d[7], mode=mode, workspace=w)
+            tc.contract(c[0], c[1], c[2], c[3], c[4], c[5], alpha=c[6], beta=c[7], mode=mode, workspace=w)
     e1.record()
     torch.cuda.synchronize()
     launches = lib.tc_launch_count() - launches0
@@ -463,23 +459,24 @@ def run_paper(args, ws, rank, local):
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
     kms = max_over_ranks(float(np.mean([sum(a.elapsed_time(b) for a, b in row) for row in kev])), ws)
+    per_call = [round(float(np.mean([row[j][0].elapsed_time(row[j][1]) for row in kev])), 4)
+                for j in range(len(calls))]
     err_code = tc.device_error()
 
-    # end to end through the public API with host buffers
-    pins = [tuple(torch.empty_strided(h[x].shape, h[x].stride(), dtype=dt).pin_memory().copy_(h[x])
-                  for x in "ABC") for h in host]
-    outs = [torch.empty_strided(h["C"].shape, h["C"].stride(), dtype=dt).pin_memory() for h in host]
-    bi = sum(sum(t.numel() * t.element_size() for t in pp) for pp in pins)
+    # end to end through the public API: the step's inputs from pinned host
+    # memory, its outputs back
+    pins = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype).pin_memory().copy_(t.cpu())
+            for t in inputs]
+    outs = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype).pin_memory() for t in outputs]
+    bi = sum(t.numel() * t.element_size() for t in pins)
     bo = sum(t.numel() * t.element_size() for t in outs)
 
     def e2e_step():
-        for d, pp in zip(dev, pins):
-            d[0].copy_(pp[0], non_blocking=True)
-            d[2].copy_(pp[1], non_blocking=True)
-            d[4].copy_(pp[2], non_blocking=True)
+        for t, h in zip(inputs, pins):
+            t.copy_(h, non_blocking=True)
         step()
-        for d, o in zip(dev, outs):
-            o.copy_(d[4], non_blocking=True)
+        for t, o in zip(outputs, outs):
+            o.copy_(t, non_blocking=True)
 
     for _ in range(warm):
         e2e_step()
@@ -493,63 +490,59 @@ def run_paper(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / K, ws)
 
-    square = shape["m"] == shape["n"] == shape["k"]
-    eff = [round(W.effective_square(p.flops()) if square
-                 else W.effective_rank_k(p.flops(), shape["m"], shape["n"]), 1) for p in probs]
-    if mode == "f64":
-        peak_v = fp64_peak_tflops()
-        peak_src = "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
-        prods, kname = 1, "k_f64"
-    else:
+    prods = 1 if mode == "f64" else (3 if mode == "bf16x3" else 6)
+    kname = "k_f64" if mode == "f64" else "k_tc"
+    if hbm_bytes is not None:
         mp = measured_peaks()
-        peak_v = mp.get("bf16_tflops", 1900.0)
-        peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
-        prods, kname = (3 if mode == "bf16x3" else 6), "k_tc"
-    ach = prods * flops / (kms * 1e-3) / 1e12
-    desc = (f"{args.workload}: {len(probs)} random contractions shaped like m={shape['m']}, "
-            f"n={shape['n']}, k={shape['k']} (1-3 dims per bundle, random label and storage "
-            f"orders, seed {shape['seed']}): " + "; ".join(
-                f"{p.labC} <- {p.labA}.{p.labB}" for p in probs)
-            + f"; mode={mode}")
+        peak_v = mp.get("hbm_gbs", 6800.0)
+        peak_src = "MEASURED_PEAKS.json hbm_gbs" if mp else "fallback 6.8 TB/s"
+        roof = {"bound": "hbm", "achieved": round(hbm_bytes / (kms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                "algorithmic": f"{hbm_bytes / 1e6:.1f} MB per step (each operand read once, each "
+                               f"output written once) over {len(calls)} launches"}
+    else:
+        if mode == "f64":
+            peak_v = fp64_peak_tflops()
+            peak_src = "cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in MEASURED_PEAKS.json)"
+        else:
+            mp = measured_peaks()
+            peak_v = mp.get("bf16_tflops", 1900.0)
+            peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
+        roof = {"bound": "tensor", "achieved": round(prods * flops / (kms * 1e-3) / 1e12, 5),
+                "unit": "TFLOP/s",
+                "algorithmic": f"{flops:.4g} flops per step over {len(calls)} launches"
+                               + (f" (x{prods} bf16 products)" if mode != "f64" else "")}
+    roof.update({"kernel": kname, "peak": round(peak_v, 5), "frac": round(roof["achieved"] / peak_v, 4),
+                 "peak_source": peak_src, "kernel_ms": round(kms, 4), "kernel_ms_per_call": per_call,
+                 "traffic": None})
+    cfg = {"workload": desc}
+    cfg.update(cfg_extra)
+    cfg["parallelism"] = f"replicas x{ws}"
     line = {
         "metric": METRIC, "value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
         "n_gpus": ws, "steps": K, "warmup": warm, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if mode == "f64" else f"f32 data, {mode} products, f32 accumulate",
-        "data": "synthetic (seeded uniform[-1,1], randomly permuted dense layouts)",
-        "config": {"workload": desc, "effective_lengths": eff,
-                   "extents": [{str(k): v for k, v in p.ext.items()} for p in probs],
-                   "l2": "operands larger than L2" if max(d[0].numel() * d[0].element_size() for d in dev)
-                         > L2_BYTES else "operands smaller than L2",
-                   "parallelism": f"replicas x{ws}"},
-        "clocks": clk,
+        "data": "synthetic (seeded, layouts of the workload; see config)",
+        "config": cfg, "clocks": clk,
         "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "gpu_launches": int(launches),
-        "roofline": {"bound": "tensor", "kernel": kname, "achieved": round(ach, 5), "peak": round(peak_v, 5),
-                     "unit": "TFLOP/s", "frac": round(ach / peak_v, 4), "peak_source": peak_src,
-                     "kernel_ms": round(kms, 4), "traffic": None,
-                     "algorithmic": f"{flops:.4g} flops per step over {len(probs)} launches"
-                                    + (f" (x{prods} bf16 products)" if mode != "f64" else "")},
-        "device_error": err_code,
+        "gpu_launches": int(launches), "roofline": roof, "device_error": err_code,
     }
     if not args.no_ttgt:
-        for d, c in zip(dev, C0):
-            d[4].copy_(c)
-        tt = time_ttgt(dev, warm, K, flops, ws)
+        for c, c0 in zip(calls, C0):
+            c[4].copy_(c0)
+        tt = time_ttgt(calls, warm, K, flops, ws)
         tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms, 3)
         tt["ours_workspace_bytes"] = int(sum(w.numel() for w in works))
         line["ttgt"] = tt
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        for d, c in zip(dev, C0):
-            d[4].copy_(c)
+    if cpu is not None and rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        spec0, h0, ci = cpu
+        for c, c0 in zip(calls, C0):
+            c[4].copy_(c0)
         step()
         torch.cuda.synchronize()
-        p0, h0 = probs[0], host[0]
-        spec0 = W.Spec(args.workload, p0.labA, p0.labB, p0.labC, {str(k): v for k, v in p0.ext.items()},
-                       dt, 1.0, 0.0)
         fl, sec, S, cores, cref, mag = oracle_sample(spec0, h0, seconds=12.0)
-        got = dev[0][4].cpu().to(torch.float64).numpy()
+        got = calls[ci][4].cpu().to(torch.float64).numpy()
         # the oracle's first S elements: colexicographic over C's own dims
         g = got.ravel(order="F")[:S]
         r = cref.ravel(order="F")[:S]
@@ -557,11 +550,79 @@ def run_paper(args, ws, rank, local):
         err = float(np.max(np.abs(g - r) / np.maximum(m, 1e-300)))
         line["cpu_baseline"] = {"value": round(fl / sec / 1e12, 8), "unit": "TFLOP/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": f"first {S} output elements of the first contraction "
-                                          f"(all k terms each), {sec:.1f} s on {cores} host threads",
+                                "sample": f"first {S} output elements of {spec0.labC} <- "
+                                          f"{spec0.labA}.{spec0.labB} (all k terms each), {sec:.1f} s "
+                                          f"on {cores} host threads",
                                 "max_normalised_err_gpu_vs_oracle": err}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_paper(args, ws, rank, local):
+    """Section 9's randomly generated contractions of one matrix shape (square
+    m = n = k, or rank-k m = n >> k): three seeded contractions, 1-3 dims per
+    bundle, random label and storage orders; one step = the three tc_contract
+    calls.  Effective lengths from the flops actually performed."""
+    shape = W.PAPER_SHAPES[args.workload]
+    mode = args.mode or "f64"
+    dt = torch.float64 if mode == "f64" else torch.float32
+    probs = W.paper_problems(args.workload)
+    host = [W.make_random_inputs(p, seed=shape["seed"] * 10 + i, dtype=dt) for i, p in enumerate(probs)]
+    calls = [(to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB, to_device(h["C"], dt),
+              p.labC, 1.0, 0.0) for p, h in zip(probs, host)]
+    flops = sum(p.flops() for p in probs)
+    square = shape["m"] == shape["n"] == shape["k"]
+    eff = [round(W.effective_square(p.flops()) if square
+                 else W.effective_rank_k(p.flops(), shape["m"], shape["n"]), 1) for p in probs]
+    desc = (f"{args.workload}: {len(probs)} random contractions shaped like m={shape['m']}, "
+            f"n={shape['n']}, k={shape['k']} (1-3 dims per bundle, random label and storage "
+            f"orders, seed {shape['seed']}): " + "; ".join(
+                f"{p.labC} <- {p.labA}.{p.labB}" for p in probs) + f"; mode={mode}")
+    extra = {"effective_lengths": eff,
+             "extents": [{str(k): v for k, v in p.ext.items()} for p in probs],
+             "l2": "operands larger than L2" if max(c[0].numel() * c[0].element_size() for c in calls)
+                   > L2_BYTES else "operands smaller than L2"}
+    p0 = probs[0]
+    spec0 = W.Spec(args.workload, p0.labA, p0.labB, p0.labC, {str(k): v for k, v in p0.ext.items()},
+                   dt, 1.0, 0.0)
+    run_calls(args, ws, rank, local, calls=calls,
+              inputs=[t for c in calls for t in (c[0], c[2], c[4])], outputs=[c[4] for c in calls],
+              flops=flops, mode=mode, desc=desc, cfg_extra=extra, cpu=(spec0, host[0], 0))
+
+
+def run_grad(args, ws, rank, local):
+    """The gradient workload forward and backward (autograd's three
+    contractions): C = A.B, dA = dC . B over J, dB = A . dC over I, each a
+    transposition-free tc_contract on the tensors' own layouts."""
+    spec = W.SPECS["grad_f32"]
+    mode = args.mode or spec.mode
+    dt = spec.dtype
+    seed = 1000 + list(W.SPECS).index(spec.name)
+    host = W.make_inputs(spec, seed=seed)
+    g = torch.Generator().manual_seed(seed + 7)
+    shapeC = spec.shape(spec.labC)
+    dC_h = W.colmajor(torch.randn(int(np.prod(shapeC)), generator=g, dtype=torch.float64)
+                      .to(dt).to(torch.float64), shapeC)
+    A, B, C = (to_device(host[x], dt) for x in "ABC")
+    dC = to_device(dC_h, dt)
+    dA = torch.empty_like(A)
+    dB = torch.empty_like(B)
+    calls = [(A, spec.labA, B, spec.labB, C, spec.labC, 1.0, 0.0),
+             (dC, spec.labC, B, spec.labB, dA, spec.labA, 1.0, 0.0),
+             (A, spec.labA, dC, spec.labC, dB, spec.labB, 1.0, 0.0)]
+    flops = 3 * spec.flops()
+    es = torch.tensor([], dtype=dt).element_size()
+    nbytes = lambda t: t.numel() * es  # noqa: E731
+    hbm = sum(nbytes(c[0]) + nbytes(c[2]) + nbytes(c[4]) for c in calls)
+    desc = (f"grad_f32 forward + backward: {spec.labC} <- {spec.labA}.{spec.labB}, "
+            f"d{spec.labA} <- d{spec.labC}.{spec.labB}, d{spec.labB} <- {spec.labA}.d{spec.labC}, extents "
+            + ",".join(f"{k}={v}" for k, v in sorted(spec.ext.items()))
+            + f", column-major, normal inputs, mode={mode}")
+    extra = {"l2": f"inputs larger than L2 (A = {nbytes(A) / 1e6:.1f} MB > {L2_BYTES / 1e6:.0f} MB)",
+             "m_n_k": [[16384, 128, 4096], [16384, 4096, 128], [4096, 128, 16384]], "mode": mode}
+    run_calls(args, ws, rank, local, calls=calls, inputs=[A, B, dC], outputs=[C, dA, dB],
+              flops=flops, mode=mode, desc=desc, cfg_extra=extra, hbm_bytes=hbm,
+              cpu=(spec, host, 0))
 
 
 def run_ours(args, ws, rank, local):
@@ -569,6 +630,8 @@ def run_ours(args, ws, rank, local):
         return run_batch(args, ws, rank, local)
     if args.workload in W.PAPER_SHAPES:
         return run_paper(args, ws, rank, local)
+    if args.workload == "grad_f32":
+        return run_grad(args, ws, rank, local)
     spec = W.SPECS[args.workload]
     if args.mode:
         import dataclasses
