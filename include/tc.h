@@ -175,15 +175,16 @@ TC_API void tc_plan_destroy(tc_plan* plan);
 /* How the tensor-core mainloop (BF16X3 / BF16X6 modes) reads A and B into
  * shared memory.  Results are identical, bit for bit, in every setting; only
  * the speed differs.
- * TC_ACCESS_BOX (default): an operand whose tile rows and k-tile form one box
- * in its own dims -- its unit-stride dim leads the row or the k bundle, the
- * bundle dims before the one a tile ends in are covered whole, and that dim's
- * tile extent divides its length (the last dim of a bundle may run past its
- * end), at most 5 dims, FP32 strides that are multiples of 4 elements,
- * 16-byte aligned data -- is loaded with one TMA box per tile (a regular
- * block in the sense of Section 6.2, in several dims at once, read along the
- * unit stride as Section 7.3 prefers, with no scatter entry); every other
- * operand as in TC_ACCESS_BLOCK.
+ * TC_ACCESS_BOX (default): when, for both A and B, the tile rows and a k-tile
+ * form one box in the operand's own dims -- its unit-stride dim leads the row
+ * or the k bundle, the bundle dims before the one a tile ends in are covered
+ * whole, and that dim's tile extent divides its length (the last dim of a
+ * bundle may run past its end), no box extent exceeds its dim's length, at
+ * most 5 dims, FP32 strides that are multiples of 4 elements, 16-byte aligned
+ * data -- both are loaded with one TMA box per tile (a regular block in the
+ * sense of Section 6.2, in several dims at once, read along the unit stride
+ * as Section 7.3 prefers, with no scatter entry); otherwise, and for batches
+ * (tc_plan_*, tc_contract_batched), as in TC_ACCESS_BLOCK.
  * TC_ACCESS_BLOCK: gathers through the scatter vectors (Section 6.1), 16
  * bytes at a time wherever the block-scatter vectors (Section 6.2) show four
  * consecutive elements at unit stride: the paper's block-scatter form.
@@ -198,10 +199,10 @@ TC_API int tc_set_access(int access);
 
 /* Report how tc_contract would read A and B (matrix roles, as in
  * tc_plan_describe) in tensor-core mode `mode` with the current setting:
- * *a_box, *b_box = 1 for a TMA box per tile, 0 for the scatter gather.  Host
- * only; without a CUDA driver it reports the eligibility rules alone (the
- * driver may still refuse a tensor map, and the operand is then gathered).
- * TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
+ * *a_box, *b_box = 1 for a TMA box per tile, 0 for the scatter gather (both
+ * or neither).  Host only; without a CUDA driver it reports the eligibility
+ * rules alone (the driver may still refuse a tensor map, and both operands
+ * are then gathered).  TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
 TC_API int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
                          const tc_tensor* C, int32_t* a_box, int32_t* b_box);
 

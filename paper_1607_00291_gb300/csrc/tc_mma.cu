@@ -1,11 +1,14 @@
 // K3 + K5: the FP32 contraction on the fifth-generation tensor cores (tcgen05),
 // persistent over output tiles (of one problem, or of a batch of problems).
 //
-// Each operand panel is gathered in place through the scatter vectors of
-// Section 6.1 -- 16-byte cp.async copies wherever the block-scatter vectors of
-// Section 6.2 (or the row scatter entries) show a unit-stride run of four,
-// 4-byte copies otherwise, zero-filled past the end of the contracted range --
-// into a raw FP32 stage.  Converter warps split every value into bf16 pieces
+// Each operand panel reaches a raw FP32 stage in shared memory in one of two
+// ways.  Gathered in place through the scatter vectors of Section 6.1 --
+// 16-byte cp.async copies wherever the block-scatter vectors of Section 6.2
+// (or the row scatter entries) show a unit-stride run of four, 4-byte copies
+// otherwise, zero-filled past the end of the contracted range -- or, when the
+// tiles of both operands are boxes in their own dims (the BOX form), as one
+// TMA box per operand and k-tile, which lands in exactly the layout the gather
+// produces.  Converter warps split every value into bf16 pieces
 // (x = b0 + b1 [+ b2], each b_i = RN_bf16 of the residual left so far, every
 // residual exact in FP32) and write them in the tensor core's K-major
 // canonical layout.  One elected thread issues, per 16-wide k-slice, a
@@ -23,22 +26,25 @@
 // rscat(C) + cscat(C), or -- when a tile's range is also split across CTAs for
 // parallelism -- store the FP32 partial that K4 sums the same compensated way.
 //
-// Warp roles (672 threads): warps 0-7 load (cp.async), warps 8-15 convert,
-// warps 16-19 run the epilogue (one per Tensor Memory lane quarter), warp 20
-// owns the Tensor Memory allocation (512 columns: two accumulators, the hi and
-// lo words of the running sum) and its lane 0 issues the MMAs.  The epilogue
-// of one chunk overlaps the MMAs of the next.  Hand-offs go through mbarriers:
-// raw_full (cp.async completion) / raw_empty, mma_full / mma_empty
-// (tcgen05.commit), acc_full[2] (tcgen05.commit) / acc_empty[2].  Every
-// mbarrier wait is bounded: on expiry the CTA records TC_ERR_DEVICE_TIMEOUT in
-// the device error word and raises a CTA-wide abort flag; the roles leave
-// their loops together (barrier reductions of the flag), the MMA thread waits
-// for its issued MMAs to drain, and Tensor Memory is always released.
+// Warp roles (672 threads; 704 in the BOX form): warps 0-7 load (cp.async),
+// or in the BOX form convert, warps 8-15 convert, warps 16-19 run the
+// epilogue (one per Tensor Memory lane quarter), warp 20 owns the Tensor
+// Memory allocation (512 columns: two accumulators, the hi and lo words of
+// the running sum) and its lane 0 issues the MMAs, and in the BOX form lane 0
+// of warp 21 issues the boxes.  The epilogue of one chunk overlaps the MMAs
+// of the next.  Hand-offs go through mbarriers: raw_full (cp.async
+// completion, or the boxes' transaction count) / raw_empty, mma_full /
+// mma_empty (tcgen05.commit), acc_full[2] (tcgen05.commit) / acc_empty[2].
+// Every mbarrier wait is bounded: on expiry the CTA records
+// TC_ERR_DEVICE_TIMEOUT in the device error word and raises a CTA-wide abort
+// flag; the roles leave their loops together (barrier reductions of the
+// flag), the MMA thread waits for its issued MMAs to drain, the box warp for
+// its boxes in flight, and Tensor Memory is always released.
 //
-// Rows of a panel beyond the operand's edge are not loaded: a row of A (or B)
-// only reaches the matching row (column) of the accumulator, which the
-// epilogue skips.  Past the end of the contracted range the panels are
-// zero-filled, since those entries reach every output.
+// Rows of a panel beyond the operand's edge are not gathered (a box reads
+// them as zeros): a row of A (or B) only reaches the matching row (column) of
+// the accumulator, which the epilogue skips.  Past the end of the contracted
+// range the panels are zero-filled, since those entries reach every output.
 #include <cuda_bf16.h>
 
 #include <algorithm>
