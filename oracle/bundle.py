@@ -27,10 +27,13 @@ in label order and repeating until no pair merges.  The steps move no data.
    order P by |stride| in B instead (smallest first), so that B is read along its own unit
    stride.  Step 5's aim -- stride-1 access for A -- is unaffected.
 ``normalize(..., gpu_row_order=True)`` adds a second one:
-7. when A's smallest stride lies in I (A is read along its rows), order I by
-   |stride| in A instead of C (smallest first); likewise J by |stride| in B
-   when B's smallest stride lies in J.  C, which step 3 serves, is written
-   once, while A and B are read once per output tile across from them.
+7. when B's smallest stride lies in J (B is read along its rows), order J by
+   |stride| in B instead of C (smallest first); likewise I by |stride| in A
+   when A's smallest stride lies in I, but only when k (the product of the P
+   lengths) is at least 512.  C, which step 3 serves, is written once, while
+   A and B are read once per output tile across from them (about k / 128
+   times C's traffic); after step 4 C's unit stride lies in I, so only
+   re-ordering I costs C its unit-stride writes.
 """
 from dataclasses import dataclass, field
 from typing import Dict, List, Tuple
@@ -167,11 +170,12 @@ def normalize(A, B, C, gpu_p_order: bool = False, gpu_row_order: bool = False) -
         if a_rows and b_k:
             P = sorted(P, key=lambda d: abs(d.s["B"]))
     # 7. (not in the paper) an operand whose smallest stride lies in its row
-    #    bundle orders that bundle by its own strides
+    #    bundle orders that bundle by its own strides (I only when k >= 512)
     if gpu_row_order:
         minA_P = min((abs(d.s["A"]) for d in P), default=None)
         minB_P = min((abs(d.s["B"]) for d in P), default=None)
-        if I and (minA_P is None or min(abs(d.s["A"]) for d in I) <= minA_P):
+        if I and _prod(d.n for d in P) >= 512 and \
+                (minA_P is None or min(abs(d.s["A"]) for d in I) <= minA_P):
             I = sorted(I, key=lambda d: abs(d.s["A"]))
         if J and (minB_P is None or min(abs(d.s["B"]) for d in J) <= minB_P):
             J = sorted(J, key=lambda d: abs(d.s["B"]))

@@ -214,10 +214,14 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
     if (a_rows && b_k) stable_sort(P, nP, [](const LDim& x) { return std::llabs(x.s1); });
   }
   // step 7 (GPU): an operand read along its rows orders its row bundle by its
-  // own strides.  Step 3 serves C, which the epilogue writes once; A and B
-  // are read once per output tile across from them, so when A's smallest
-  // stride lies in I (B's in J), I (J) is re-sorted by A's (B's) strides:
-  // the loaders' consecutive rows are then A's (B's) unit-stride run.
+  // own strides, so that the loaders' consecutive rows are its unit-stride
+  // run.  For J and B this costs nothing: after step 4 C's unit stride lies
+  // in I, and the epilogue's threads run along I.  For I and A it moves C's
+  // unit-stride dim away from the epilogue's threads; A is read once per
+  // output tile across from it, about k / 128 times C's traffic, so I is
+  // re-sorted only for k >= 512.
+  int64_t kprod = 1;
+  for (int i = 0; i < nP; ++i) kprod *= P[i].len;
   {
     int64_t minAP = INT64_MAX, minAI = INT64_MAX, minBP = INT64_MAX, minBJ = INT64_MAX;
     for (int i = 0; i < nP; ++i) {
@@ -226,7 +230,8 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
     }
     for (int i = 0; i < nI; ++i) minAI = std::min<int64_t>(minAI, std::llabs(I[i].s0));
     for (int i = 0; i < nJ; ++i) minBJ = std::min<int64_t>(minBJ, std::llabs(J[i].s0));
-    if (nI > 0 && minAI <= minAP) stable_sort(I, nI, [](const LDim& x) { return std::llabs(x.s0); });
+    if (kprod >= 512 && nI > 0 && minAI <= minAP)
+      stable_sort(I, nI, [](const LDim& x) { return std::llabs(x.s0); });
     if (nJ > 0 && minBJ <= minBP) stable_sort(J, nJ, [](const LDim& x) { return std::llabs(x.s0); });
   }
 

@@ -70,8 +70,9 @@ CASES = {
     "row_box_2d": ("apb", "pj", "ajb", dict(a=32, b=8, p=64, j=64), (True, True)),
     # row-contiguous B tile of 48 rows (k-rows 48 floats apart in shared memory)
     "mn_B_bn48": ("pi", "jp", "ij", dict(p=96, i=256, j=48), (True, True)),
-    # five-dim A (rows a, b, c ordered by A's strides; k p, q) and three-dim B
-    "rank5_A": ("apbqc", "pqj", "acbj", dict(a=32, b=4, c=3, p=32, q=3, j=48), (True, True)),
+    # five-dim A (rows a, b, c ordered by A's strides, k = 512 being long
+    # enough for that; k dims p, q) and three-dim B
+    "rank5_A": ("apbqc", "pqj", "acbj", dict(a=32, b=4, c=3, p=32, q=16, j=48), (True, True)),
     # B alone would be a box (a = 24 breaks A's row box): both gathered
     "mixed": ("pab", "pj", "ajb", dict(a=24, b=16, p=64, j=128), (False, False)),
 }

@@ -117,6 +117,19 @@ def test_gpu_row_order_step():
     assert ["".join(d.labels) for d in paper.I][0] == "gd"  # the paper's step 3 alone
 
 
+def test_gpu_row_order_needs_long_k_for_I():
+    # A's unit stride (c) lies in I; C stores b fastest.  With k = 256 the
+    # epilogue's unit-stride writes of C win (I = b, c as step 3 orders it);
+    # with k = 1024 A's re-reads do (I = c, b)
+    for k, first in ((256, "b"), (1024, "c")):
+        ext = dict(a=k, b=127, c=126, d=500)
+        A = ("acb", *stride_of("acb", "cab", ext))
+        B = ("da", *stride_of("da", "ad", ext))
+        C = ("dcb", *stride_of("dcb", "bcd", ext))
+        g = compare(A[0], A[1:], B[0], B[1:], C[0], C[1:])
+        assert g["I"][0]["labels"] == first, k
+
+
 def stride_of(labels, order, ext):
     """Lengths and strides of a tensor indexed by `labels`, stored column-major
     in the label order `order`."""
