@@ -197,6 +197,20 @@ TC_API void tc_plan_destroy(tc_plan* plan);
 typedef enum { TC_ACCESS_BOX = 0, TC_ACCESS_BLOCK = 1, TC_ACCESS_SCATTER = 2 } tc_access;
 TC_API int tc_set_access(int access);
 
+/* How the tensor-core path sums the FP32 partial results of a contracted
+ * range split across CTAs (for parallelism on few output tiles, or for
+ * balance in a batch), before alpha/beta and the final FP32 rounding.
+ * TC_REDUCE_COMPENSATED (default): error-free transformations on the FP32
+ * pipes (Knuth's two-sum, the errors collected once): for up to 64 partials
+ * as accurate as an FP64 sum, and faster on GB300, whose FP64 rate is low.
+ * TC_REDUCE_F64: each partial widened to FP64, summed and scaled in FP64.
+ * Within one tile the tensor core's own FP32 accumulation is summed in
+ * float-float chunks of at most 1024 terms in either setting.  Process-wide,
+ * read when a contraction is issued or a plan is created.  Returns the
+ * previous setting, or TC_ERR_ARG for an unknown value. */
+typedef enum { TC_REDUCE_COMPENSATED = 0, TC_REDUCE_F64 = 1 } tc_reduce;
+TC_API int tc_set_split_reduction(int reduce);
+
 /* Report how tc_contract would read A and B (matrix roles, as in
  * tc_plan_describe) in tensor-core mode `mode` with the current setting:
  * *a_box, *b_box = 1 for a TMA box per tile, 0 for the scatter gather (both

@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import TcError  # noqa: F401
 
 __all__ = ["contract", "workspace_size", "plan_describe", "build_scatter", "device_error",
-           "set_access", "access", "box_access", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
+           "set_access", "access", "box_access", "set_split_reduction", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
 
 _MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3, "bf16x6": L.TC_MODE_BF16X6}
 
@@ -139,6 +139,21 @@ class access:
     def __exit__(self, *exc):
         set_access(self.prev)
         return False
+
+
+_REDUCE = {"compensated": L.TC_REDUCE_COMPENSATED, "f64": L.TC_REDUCE_F64}
+
+
+def set_split_reduction(form: str) -> str:
+    """How the tensor-core path sums the FP32 partials of a contracted range
+    split across CTAs: "compensated" (default; two-sum FP32, as accurate as FP64
+    for up to 64 partials) or "f64".  Process-wide; returns the previous form."""
+    if form not in _REDUCE:
+        raise ValueError(f"form must be one of {sorted(_REDUCE)}")
+    prev = L.lib().tc_set_split_reduction(_REDUCE[form])
+    if prev < 0:
+        L.check(prev, "tc_set_split_reduction")
+    return {v: k for k, v in _REDUCE.items()}[prev]
 
 
 def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):

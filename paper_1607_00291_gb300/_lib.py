@@ -11,6 +11,7 @@ MAX_RANK = 16
 TC_F64, TC_F32 = 0, 1
 TC_MODE_F64, TC_MODE_BF16X3, TC_MODE_BF16X6 = 0, 1, 2
 TC_ACCESS_BOX, TC_ACCESS_BLOCK, TC_ACCESS_SCATTER = 0, 1, 2
+TC_REDUCE_COMPENSATED, TC_REDUCE_F64 = 0, 1
 TC_OK = 0
 STATUS = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_LABEL", -3: "TC_ERR_EXTENT", -4: "TC_ERR_OVERLAP",
           -5: "TC_ERR_WORKSPACE", -6: "TC_ERR_CUDA", -7: "TC_ERR_DEVICE_TIMEOUT",
@@ -56,6 +57,7 @@ SIGNATURES = {
     "tc_contract_noalloc": (c_i32, [c_i32, c_dbl, ctypes.POINTER(TcTensor), ctypes.POINTER(TcTensor), c_dbl,
                                     ctypes.POINTER(TcTensor), c_vp]),
     "tc_set_access": (c_i32, [c_i32]),
+    "tc_set_split_reduction": (c_i32, [c_i32]),
     "tc_box_access": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
                       [ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     "tc_set_mainloop_events": (c_i32, [c_vp, c_vp]),

@@ -10,8 +10,9 @@
 // scatter entry at all.  This file decides, per operand, whether its tiles
 // are such boxes and encodes the tensor map; operands that are not keep the
 // scatter-vector gather of Section 6.1.  It also carries the process-wide
-// access setting: boxes where tiles are boxes (default), block gathers only,
-// or element gathers only.
+// settings of the tensor-core path: the access (boxes where tiles are boxes
+// (default), block gathers only, or element gathers only) and the form of the
+// k-split reduction.
 //
 // A tile of T consecutive linear indices of a bundle (dims d0, d1, ... with
 // extents n0, n1, ..., d0 fastest, tiles starting at multiples of T) is a box
@@ -184,6 +185,18 @@ void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_b
 bool box_encoder_available() { return encoder() != nullptr; }
 
 }  // namespace tc
+
+namespace tc {
+namespace {
+std::atomic<int> g_reduce{TC_REDUCE_COMPENSATED};
+}
+bool split_reduction_f64() { return g_reduce.load() == TC_REDUCE_F64; }
+}  // namespace tc
+
+extern "C" int tc_set_split_reduction(int reduce) {
+  if (reduce != TC_REDUCE_COMPENSATED && reduce != TC_REDUCE_F64) return TC_ERR_ARG;
+  return tc::g_reduce.exchange(reduce);
+}
 
 extern "C" int tc_set_access(int access) {
   if (access != TC_ACCESS_BLOCK && access != TC_ACCESS_SCATTER && access != TC_ACCESS_BOX)

@@ -170,6 +170,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     d.kps = w.tcc.kps;
     plan_access(L, d, q.tm);
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+    q.reduce_f64 = split_reduction_f64() ? 1 : 0;
     q.ctas = sm_count();
     q.err = err_word();
     // TC_FAULT=timeout: test hook that makes the kernel's first wait expire

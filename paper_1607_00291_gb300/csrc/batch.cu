@@ -231,6 +231,7 @@ struct tc_plan {
   int32_t n_split = 0;
   int64_t max_m_split = 0, max_n_split = 0;
   int pieces = 2;
+  int reduce_f64 = 0;  // the split-reduction setting when the plan was created
   int64_t ctas = 152;
 };
 
@@ -240,6 +241,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const int sms = sm_count();
   const bool f64 = pl->mode == TC_MODE_F64;
   pl->ctas = f64 ? (int64_t)sms * f64_batch_ctas_per_sm() : sms;
+  pl->reduce_f64 = split_reduction_f64() ? 1 : 0;
   pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
   std::vector<double> alpha, beta;
   for (const tc_problem& pr : probs) {
@@ -518,6 +520,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.nitems = plan->nitems;
     q.nprobs = np;
     q.pieces = plan->pieces;
+    q.reduce_f64 = plan->reduce_f64;
     q.ctas = plan->ctas;
     q.split_probs = plan->d_split;
     q.split_col_prefix = plan->d_split_cols;

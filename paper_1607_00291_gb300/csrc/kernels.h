@@ -82,6 +82,8 @@ struct BoxAccess {
 struct DevProblem;
 void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box = true);
 bool box_encoder_available();  // the driver's tensor-map encoder could be found
+// The process-wide split-reduction setting (tc_set_split_reduction): true for FP64.
+bool split_reduction_f64();
 
 // One planned contraction as the persistent kernels see it: a kernel
 // parameter for a single call, an array in device memory for a batch.
@@ -128,6 +130,7 @@ struct TcLaunch {
   int64_t split_cols;         // batch: total columns of the split problems
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
+  int32_t reduce_f64;         // sum the k-split partials in FP64 (else compensated FP32)
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path

@@ -782,6 +782,9 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
 
 // Columns [n0, n1) of one problem (the single-problem launch strides its
 // block rows over all columns; the batched one hands each block row one).
+// F64: the partials are summed in FP64 instead, alpha and beta applied in FP64,
+// one rounding to FP32 at the end (the selectable tc_set_split_reduction form).
+template <bool F64>
 __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int64_t n1) {
   const int64_t M = d.m, plane = M * d.n;
   const int S = d.splits;
@@ -794,6 +797,15 @@ __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int6
     const float* pn = part + n * M;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
+      if constexpr (F64) {
+        double sum = 0.0;
+        for (int ks = 0; ks < S; ++ks) sum += (double)__ldg(pn + ks * plane + m);
+        float* cp = c + __ldg(d.sp.rC + m) + cn;
+        double r = d.alpha * sum;
+        if (d.beta != 0.0) r += d.beta * (double)*cp;
+        *cp = (float)r;
+        continue;
+      }
       float hi = __ldg(pn + m), lo = 0.f;
       for (int ks = 1; ks < S; ++ks) {
         float e;
@@ -813,11 +825,12 @@ __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int6
 // One launch for the single problem, or for every split problem of a batch:
 // block row y walks the flattened list of (problem, column) pairs, found from
 // the prefix sums of the problems' column counts.
+template <bool F64>
 __global__ void k_reduce_partials(const DevProblem single, const DevProblem* probs,
                                   const int32_t* split_probs, const int64_t* col_prefix,
                                   int32_t n_split) {
   if (!probs) {
-    reduce_one(single, 0, single.n);
+    reduce_one<F64>(single, 0, single.n);
     return;
   }
   const int64_t total = col_prefix[n_split];
@@ -828,7 +841,7 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
       if (col_prefix[mid] <= r) lo = mid; else hi = mid;
     }
     const int64_t n = r - col_prefix[lo];
-    reduce_one(probs[split_probs[lo]], n, n + 1);
+    reduce_one<F64>(probs[split_probs[lo]], n, n + 1);
   }
 }
 
@@ -870,9 +883,14 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
     const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((mm + 255) / 256, 16));
     const unsigned by = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(single_split ? nn : q.split_cols, single_split ? 8192 : 16384));
-    k_reduce_partials<<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
-                                                   q.split_col_prefix,
-                                                   single_split ? 0 : q.n_split_probs);
+    if (q.reduce_f64)
+      k_reduce_partials<true><<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
+                                                           q.split_col_prefix,
+                                                           single_split ? 0 : q.n_split_probs);
+    else
+      k_reduce_partials<false><<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
+                                                            q.split_col_prefix,
+                                                            single_split ? 0 : q.n_split_probs);
     note_launch();
   }
   mainloop_event_after(s);

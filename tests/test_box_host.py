@@ -127,3 +127,8 @@ def test_fp64_mode_has_no_box_plan():
     with pytest.raises(ValueError):
         tc.set_access("tma")
     assert L.lib().tc_set_access(7) == -1
+    assert L.lib().tc_set_split_reduction(5) == -1
+    assert tc.set_split_reduction("f64") == "compensated"  # the default
+    assert tc.set_split_reduction("compensated") == "f64"
+    with pytest.raises(ValueError):
+        tc.set_split_reduction("fp32")

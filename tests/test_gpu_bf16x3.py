@@ -118,6 +118,28 @@ def test_split_k_reduction(mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_split_reduction_forms_agree(mode):
+    # the k-split partials summed in FP64 or with compensated FP32 arithmetic:
+    # both within the mode's bound, and within a few FP32 ulps of each other
+    g = torch.Generator().manual_seed(14)
+    A = f32(torch.randn(256, 8192, generator=g, dtype=torch.float64))
+    B = f32(torch.randn(8192, 100, generator=g, dtype=torch.float64))
+    C0 = f32(torch.randn(256, 100, generator=g, dtype=torch.float64))
+    ref, mag = oracle_ref(0.5, A, "ip", B, "pj", 2.0, C0, "ij")
+    res = {}
+    for form in ("f64", "compensated"):
+        prev = tc.set_split_reduction(form)
+        try:
+            res[form] = run(0.5, A, "ip", B, "pj", 2.0, C0, "ij", mode)
+        finally:
+            tc.set_split_reduction(prev)
+        assert norm_err(res[form], ref, mag) <= TOLS[mode], form
+    # (normalised like the parity bound: an FP32 rounding of a near-cancelling
+    # sum is a few ulps of its terms, not of the result)
+    assert np.max(np.abs(res["f64"] - res["compensated"]) / mag) <= 4 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_degenerate_shapes(mode):
     g = torch.Generator().manual_seed(5)
     r = lambda *s: f32(torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1)
