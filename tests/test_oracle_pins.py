@@ -279,6 +279,36 @@ def test_ttgt_agreement():
         assert norm_err(C, ref, mag) < 1e-13
 
 
+def test_gradient_contractions_match_finite_differences():
+    # the backward rule the GPU path uses, on the oracle alone: for
+    # f(A, B) = <dC, C(A, B)> with C = A_ilmj B_mkl, df/dA = dC_ijk B_mkl (as
+    # an ilmj tensor) and df/dB = A_ilmj dC_ijk (as mkl); checked against
+    # central differences of the forward oracle along random directions
+    rng = np.random.default_rng(21)
+    ext = dict(i=3, j=2, k=3, l=2, m=2)
+    sh = lambda lab: tuple(ext[x] for x in lab)  # noqa: E731
+    A, B = rng.standard_normal(sh("ilmj")), rng.standard_normal(sh("mkl"))
+    dC = rng.standard_normal(sh("ijk"))
+    zero = lambda lab: np.zeros(sh(lab))  # noqa: E731
+    f = lambda a, b: float(np.sum(dC * oracle.contract(1.0, a, "ilmj", b, "mkl", 0.0,  # noqa: E731
+                                                       zero("ijk"), "ijk")[0]))
+    dA, _ = oracle.contract(1.0, dC, "ijk", B, "mkl", 0.0, zero("ilmj"), "ilmj")
+    dB, _ = oracle.contract(1.0, A, "ilmj", dC, "ijk", 0.0, zero("mkl"), "mkl")
+    h = 1e-6
+    for _ in range(5):
+        VA, VB = rng.standard_normal(A.shape), rng.standard_normal(B.shape)
+        fd_a = (f(A + h * VA, B) - f(A - h * VA, B)) / (2 * h)
+        fd_b = (f(A, B + h * VB) - f(A, B - h * VB)) / (2 * h)
+        assert abs(fd_a - float(np.sum(dA * VA))) < 1e-7 * max(1.0, abs(fd_a))
+        assert abs(fd_b - float(np.sum(dB * VB))) < 1e-7 * max(1.0, abs(fd_b))
+    # the plausible slip of reading B with l and m exchanged (lkm for mkl)
+    # gives a gradient that the finite differences reject
+    wrong, _ = oracle.contract(1.0, dC, "ijk", B, "lkm", 0.0, zero("ilmj"), "ilmj")
+    VA = rng.standard_normal(A.shape)
+    fd_a = (f(A + h * VA, B) - f(A - h * VA, B)) / (2 * h)
+    assert abs(fd_a - float(np.sum(wrong * VA))) > 1e-3
+
+
 def test_bruteforce_tiny():
     rng = np.random.default_rng(9)
     A = rng.uniform(-1, 1, (2, 3, 2))   # a p q
