@@ -5,13 +5,15 @@
 // per problem the tile shape and the split of the contracted range (from the
 // autotune table when TC_AUTOTUNE=1, else from the same rules as a single
 // call), builds one work list -- every output tile x k-split of every
-// problem, sorted by decreasing cost so that a static round-robin over the
-// persistent CTAs stays balanced -- and copies the problem descriptors, the
-// work list and the scatter-vector layouts into one device buffer it owns.
-// tc_plan_execute then only launches kernels: the batched scatter builder
-// (K1 for every problem), the persistent mainloop (FP64: DMMA tiles; FP32:
-// tcgen05 tiles) and, for problems split along k, the reduction -- no host
-// synchronisation and no allocation, so it can be captured in a CUDA graph.
+// problem, longest first -- and copies the problem descriptors, the work list
+// and the scatter-vector layouts into one device buffer it owns.  The
+// persistent CTAs take the items in that order from a shared counter, so that
+// a CTA that drew cheap items (short k, coalesced operands) takes more.
+// tc_plan_execute then only launches work: the batched scatter builder (K1
+// for every problem), a reset of the work counter, the persistent mainloop
+// (FP64: DMMA tiles; FP32: tcgen05 tiles) and, for problems split along k,
+// the reduction -- no host synchronisation and no allocation, so it can be
+// captured in a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -224,6 +226,7 @@ struct tc_plan {
   int64_t* d_scat = nullptr;
   DevProblem* d_probs = nullptr;
   WorkItem* d_items = nullptr;
+  unsigned long long* d_counter = nullptr;  // work counter of the persistent mainloop
   int32_t* d_split = nullptr;
   int64_t* d_split_cols = nullptr;
   int64_t split_cols = 0;
@@ -394,6 +397,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const size_t o_scols = take(sizeof(int64_t) * (pl->n_split + 1));
   const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
   const size_t o_tmap = take(sizeof(CUtensorMap) * 2 * std::max(np, 1));
+  const size_t o_ctr = take(sizeof(unsigned long long));
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -405,6 +409,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->d_scat = reinterpret_cast<int64_t*>(base + o_scat);
   pl->d_probs = reinterpret_cast<DevProblem*>(base + o_prob);
   pl->d_items = reinterpret_cast<WorkItem*>(base + o_item);
+  pl->d_counter = reinterpret_cast<unsigned long long*>(base + o_ctr);
   pl->d_split = reinterpret_cast<int32_t*>(base + o_split);
   pl->d_split_cols = reinterpret_cast<int64_t*>(base + o_scols);
   std::vector<int64_t> scols(pl->n_split + 1, 0);
@@ -511,6 +516,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
+    q.counter = plan->d_counter;
     e = launch_f64_batched(q, s);
   } else {
     TcLaunch q;
@@ -528,6 +534,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.n_split_probs = plan->n_split;
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
+    q.counter = plan->d_counter;
     q.err = err_word();
     e = launch_tc(q, s);
   }

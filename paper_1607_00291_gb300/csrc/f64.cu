@@ -254,17 +254,19 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // Batched FP64 contractions: a persistent grid walks the work list (output
-// tile x k-split of every problem, sorted by decreasing cost).  Unsplit tiles
-// finish in place; split ones leave FP64 partials in [split][n][m] for
-// k_f64_batched_reduce.
+// tile x k-split of every problem, longest first): CTA b starts with item b
+// and then claims the next unclaimed item from `counter` (zero at launch).
+// Unsplit tiles finish in place; split ones leave FP64 partials in
+// [split][n][m] for k_f64_batched_reduce.
 template <typename T>
 __global__ void __launch_bounds__(FB::NT, 2)
     k_f64_batched(const DevProblem* __restrict__ probs, const WorkItem* __restrict__ items,
-                  int64_t nitems) {
+                  int64_t nitems, unsigned long long* __restrict__ counter) {
   constexpr int BM = FB::BM, BN = FB::BN;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int64_t next_w;
   const F64Smem S = f64_smem<FB>(smem);
-  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+  for (int64_t w = blockIdx.x; w < nitems;) {
     const WorkItem wi = items[w];
     const DevProblem& d = probs[wi.prob];
     F64Ctx<T> P{static_cast<const T*>(d.a), static_cast<const T*>(d.b), static_cast<T*>(d.c),
@@ -277,6 +279,10 @@ __global__ void __launch_bounds__(FB::NT, 2)
                                       (int64_t)wi.split * d.m * d.n + n0 * d.m + m0
                                 : nullptr;
     f64_tile<T, FB>(P, S, m0, n0, kb, ke, d.splits == 1, part, d.m, true);
+    __syncthreads();  // every thread has read next_w of the previous claim
+    if (threadIdx.x == 0) next_w = (int64_t)gridDim.x + (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    w = next_w;
   }
 }
 
@@ -388,9 +394,14 @@ cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
     attr_set[dev] = true;
   }
   if (q.nitems > 0) {
+    if (!q.counter) return cudaErrorInvalidValue;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, q.nitems));
+    // the work counter starts from zero in every launch (a memset node under capture)
+    if (cudaMemsetAsync(q.counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
+      return cudaGetLastError();
     mainloop_event_before(s);
-    k_f64_batched<T><<<(unsigned)grid, FB::NT, FB::SMEM, s>>>(q.probs, q.items, q.nitems);
+    k_f64_batched<T><<<(unsigned)grid, FB::NT, FB::SMEM, s>>>(q.probs, q.items, q.nitems,
+                                                              q.counter);
     note_launch();
     if (q.n_split_probs > 0) {
       const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 16));

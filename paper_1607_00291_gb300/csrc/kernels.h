@@ -131,6 +131,7 @@ struct TcLaunch {
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;  // batch: largest m and n among split problems
   int32_t reduce_f64;         // sum the k-split partials in FP64 (else compensated FP32)
+  unsigned long long* counter;  // batch: device work counter for dynamic items, or null
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path
@@ -150,6 +151,7 @@ struct F64BatchLaunch {
   int64_t split_cols;
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;
+  unsigned long long* counter;  // device work counter for dynamic items, or null
 };
 cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s);
 

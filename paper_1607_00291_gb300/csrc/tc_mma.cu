@@ -67,6 +67,12 @@ constexpr int MMA_WARP = (NLOAD + NCONV + NEPI) / 32;
 constexpr int BOX_WARP = MMA_WARP + 1;  // issues the TMA box loads (BOX instantiation)
 constexpr int BAR_LOAD = 1, BAR_CONV = 2, BAR_EPI = 3;
 constexpr int KRING = 2;
+// Batches take their work items from a shared counter: loader thread 0 claims
+// items up to QPUB ahead of the loaders and publishes them in a ring of QR
+// entries that every role reads in order.  A role lags the loaders by at most
+// the pipeline's depth in items (raw and MMA stages plus two accumulators),
+// well inside the ring.
+constexpr int QR = 16, QPUB = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
 constexpr int BNMAX = 128;        // widest output tile (columns)
 constexpr int CHUNK_KT = 32;      // k-tiles per accumulation chunk (1024 terms)
@@ -94,7 +100,8 @@ struct Lay {
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
   static constexpr int NBARS = 2 * RS + 2 * MS + 5;
   static constexpr int MISC = BARS + NBARS * 8;
-  static constexpr int END = MISC + 16;
+  static constexpr int WQ = MISC + 16;  // work queue: QR int64 entries, QR full + QR empty barriers
+  static constexpr int END = WQ + 3 * QR * 8;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
   static_assert(BNMAX % NEPI == 0 && BM == NEPI && NLOAD % 32 == 0 && BK % (NLOAD / 32) == 0,
@@ -140,6 +147,7 @@ struct Args {
   int64_t tiles_single;
   int32_t* err;
   int fault;  // 1: injected timeout (see TcLaunch::fault)
+  unsigned long long* counter;  // batch: the shared work counter (dynamic items), or null
 };
 
 __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err) {
@@ -384,6 +392,12 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
+  volatile int64_t* wq = reinterpret_cast<volatile int64_t*>(smem + Ly::WQ);
+  uint64_t* wq_full = reinterpret_cast<uint64_t*>(smem + Ly::WQ + QR * 8);
+  uint64_t* wq_empty = wq_full + QR;
+  // one release per entry from every warp of the loaders, converters and
+  // epilogue, and from the MMA thread
+  constexpr int NWQ = (NLOAD + NCV + NEPI) / 32 + 1;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -401,6 +415,10 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       mbar_init(&acc_empty[b], NEPI);
     }
     mbar_init(drain, 1);
+    for (int q = 0; q < QR; ++q) {
+      mbar_init(&wq_full[q], 1);
+      mbar_init(&wq_empty[q], NWQ);
+    }
     *abort = 0;
     *sProb = a.single;
     fence_mbar_init();
@@ -415,6 +433,24 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
   const uint32_t tmem = *tmem_slot;
   const int64_t nitems = a.nitems;
   const int64_t w0 = blockIdx.x, dw = gridDim.x;
+  // dynamic items (batches, gather form): the j-th item of this CTA is entry
+  // j of the work queue; otherwise items w0, w0 + dw, ...
+  const bool dyn = !BOX && a.counter != nullptr;
+  auto item_of = [&](int64_t j) -> int64_t {
+    if (!dyn) return w0 + j * dw;
+    const int q = (int)(j % QR);
+    if (!mbar_wait(&wq_full[q], (uint32_t)((j / QR) & 1), abort)) {
+      record_timeout(abort, a.err);
+      return nitems;
+    }
+    return wq[q];
+  };
+  // this warp has read entry j (its warps' lanes converge first)
+  auto release_item = [&](int64_t j) {
+    if (!dyn) return;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&wq_empty[j % QR]);
+  };
 
   if (!BOX && warp < CONV_W0) {
     // ---- loaders ----
@@ -435,9 +471,34 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         }
       }
     };
-    if (w0 < nitems) fetch_rows(get_item(a, sProb, w0));
-    for (int64_t w = w0; w < nitems; w += dw) {
-      if (bar_or(BAR_LOAD, NLOAD, *abort)) break;  // uniform exit; previous rows consumed
+    // the claimer (thread 0): entries up to `last` claimed and published
+    int64_t pub = 0;
+    bool pub_end = false;
+    auto publish_upto = [&](int64_t last) {
+      while (!pub_end && pub <= last) {
+        const int q = (int)(pub % QR);
+        if (!mbar_wait(&wq_empty[q], (uint32_t)(((pub / QR) & 1) ^ 1), abort)) {
+          record_timeout(abort, a.err);
+          pub_end = true;
+          return;
+        }
+        int64_t wc = pub == 0 ? w0 : dw + (int64_t)atomicAdd(a.counter, 1ull);
+        if (wc >= nitems) {
+          wc = nitems;  // the end of this CTA's sequence
+          pub_end = true;
+        }
+        wq[q] = wc;
+        mbar_arrive(&wq_full[q]);
+        ++pub;
+      }
+    };
+    if (dyn && t == 0) publish_upto(QPUB - 1);
+    int64_t w = item_of(0);
+    if (w < nitems) fetch_rows(get_item(a, sProb, w));
+    for (int64_t j = 0;; ++j) {
+      // uniform exit; previous rows consumed
+      if (bar_or(BAR_LOAD, NLOAD, *abort || w >= nitems)) break;
+      if (dyn && t == 0) publish_upto(j + QPUB);
       const Item it = get_item(a, sProb, w);
       const DevProblem* d = it.d;
 #pragma unroll
@@ -445,7 +506,9 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         const int r = t + i * NLOAD;
         if (r < BM + BNMAX) sRA[r] = pre[i];  // B rows follow A rows
       }
-      if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
+      w = item_of(j + 1);
+      release_item(j);
+      if (w < nitems) fetch_rows(get_item(a, sProb, w));
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
@@ -496,9 +559,12 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     // ---- converters ----
     const int t = BOX ? tid : tid - NLOAD;
     int64_t g = 0;
-    for (int64_t w = w0; w < nitems; w += dw) {
-      if (bar_or(BAR_CONV, NCV, *abort)) break;  // uniform exit
+    int64_t w = item_of(0);
+    for (int64_t j = 0;; ++j) {
+      if (bar_or(BAR_CONV, NCV, *abort || w >= nitems)) break;  // uniform exit
       const Item it = get_item(a, sProb, w);
+      w = item_of(j + 1);
+      release_item(j);
       const bool akc = it.d->a_kc, bkc = it.d->b_kc;
       // a row-contiguous B box holds k-rows of bn floats; the gather's k-rows hold BNMAX
       const int rsB = BOX && !it.d->b_kc ? it.d->bn : BNMAX;
@@ -543,16 +609,20 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         pre_c[i] = c < it.rows_b ? __ldg(it.d->sp.cC + it.n0 + c) : 0;
       }
     };
-    if (w0 < nitems) fetch_rows(get_item(a, sProb, w0));
+    int64_t w = item_of(0);
+    if (w < nitems) fetch_rows(get_item(a, sProb, w));
     int64_t gc = 0;  // chunks finished by this CTA
-    for (int64_t w = w0; w < nitems; w += dw) {
-      if (bar_or(BAR_EPI, NEPI, *abort)) break;  // uniform exit; previous rows consumed
+    for (int64_t j = 0;; ++j) {
+      // uniform exit; previous rows consumed
+      if (bar_or(BAR_EPI, NEPI, *abort || w >= nitems)) break;
       const Item it = get_item(a, sProb, w);
       const DevProblem* d = it.d;
       sRC[t] = pre_r;
 #pragma unroll
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
-      if (w + dw < nitems) fetch_rows(get_item(a, sProb, w + dw));
+      w = item_of(j + 1);
+      release_item(j);
+      if (w < nitems) fetch_rows(get_item(a, sProb, w));
       bar_sync(BAR_EPI, NEPI);
       const bool have = it.KT > 0;
       // descriptor fields in registers: the stores below could alias them as
@@ -705,8 +775,11 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         failed = true;
       }
     }
-    for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
+    int64_t w = failed ? nitems : item_of(0);
+    for (int64_t j = 0; w < nitems && !*abort && !failed; ++j) {
       const Item it = get_item(a, sProb, w);
+      w = item_of(j + 1);
+      if (dyn) mbar_arrive(&wq_empty[j % QR]);  // (this thread alone reads the queue here)
       const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
       for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
         const int b = (int)(gc & 1);
@@ -864,6 +937,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   a.items = q.items;
   a.err = q.err;
   a.fault = q.fault;
+  a.counter = q.probs && !BOX ? q.counter : nullptr;
   if (q.probs) {
     a.nitems = q.nitems;
     a.tiles_single = 1;
@@ -873,6 +947,9 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   }
   if (a.nitems == 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
+  // dynamic items count from zero in every launch (a memset node under capture)
+  if (a.counter && cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return cudaGetLastError();
   mainloop_event_before(s);
   k_tc<NS, BOX><<<(unsigned)grid, nthreads(BOX), Lay<NS, BOX>::ALLOC, s>>>(a);
   note_launch();

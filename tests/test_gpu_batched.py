@@ -139,3 +139,31 @@ def test_batch512_workload_sampled(mode):
         worst = max(worst, norm_err(got[:w], np.asarray(c).ravel(order="F")[:w],
                                     mag.ravel(order="F")[:w]))
     assert worst <= TOLS[mode], worst
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3"])
+def test_dynamic_items_many_small_and_empty(mode):
+    # 300 problems, every third with an empty contracted range (C = beta * C
+    # alone): many more work items than CTAs, most of them short, so the
+    # persistent CTAs claim items from the shared counter many times over and
+    # the tensor-core kernel's item queue wraps around repeatedly
+    dt = torch.float64 if mode == "f64" else torch.float32
+    g = torch.Generator().manual_seed(17)
+    r = lambda *s: (torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1).to(dt).double()
+    cases = []
+    for i in range(300):
+        m, n = 5 + (i * 7) % 150, 3 + (i * 11) % 140
+        k = 0 if i % 3 == 0 else 1 + (i * 13) % 90
+        cases.append((1.0 - 0.01 * i, r(m, k), "ip", r(k, n), "pj", 0.5, r(m, n), "ij"))
+    dev = [(to_device(A, dt), la, to_device(B, dt), lb, to_device(C, dt), lc, al, be)
+           for (al, A, la, B, lb, be, C, lc) in cases]
+    for rep in range(2):  # a second execution of the same plan reuses the counter
+        for d, c in zip(dev, cases):
+            d[4].copy_(c[6].to(dt))
+        tc.contract_batched(dev, mode=mode)
+        assert tc.device_error() == 0
+        worst = 0.0
+        for (al, A, la, B, lb, be, C, lc), d in zip(cases, dev):
+            ref, mag = oracle_ref(al, A, la, B, lb, be, C, lc)
+            worst = max(worst, norm_err(d[4].cpu().double().numpy(), ref, mag))
+        assert worst <= TOLS[mode], (rep, worst)
