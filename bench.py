@@ -49,6 +49,9 @@ def parse():
                     help="tensor-core operand access: TMA boxes where tiles are boxes and "
                          "block-scatter gathers elsewhere (box), block-scatter gathers only "
                          "(block), or element gathers only (scatter)")
+    ap.add_argument("--profile", action="store_true",
+                    help="after the timed region, run one more step between cudaProfilerStart "
+                         "and cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttgt", action="store_true", help="skip the TTGT comparison leg")
     return ap.parse_args()
@@ -157,6 +160,17 @@ def fp64_peak_tflops() -> float:
         best = min(best, e0.elapsed_time(e1))
     del a, b, c
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def profiled_step(args, fn):
+    """--profile: one untimed step inside a profiler range, after the timed region."""
+    if not args.profile:
+        return
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    fn()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
 
 
 def traffic_for(kernel: str, workload: str):
@@ -320,6 +334,7 @@ def run_batch(args, ws, rank, local):
     e1.record(cur)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    profiled_step(args, graph.replay)
     # graph replays launch libtc's kernels without passing through the library;
     # count them from one direct execution
     l0 = lib.tc_launch_count()
@@ -459,6 +474,7 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
     kms = max_over_ranks(float(np.mean([sum(a.elapsed_time(b) for a, b in row) for row in kev])), ws)
+    profiled_step(args, step)
     per_call = [round(float(np.mean([row[j][0].elapsed_time(row[j][1]) for row in kev])), 4)
                 for j in range(len(calls))]
     err_code = tc.device_error()
@@ -682,6 +698,7 @@ def run_ours(args, ws, rank, local):
     kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
     ms_max = max_over_ranks(ms, ws)
     kms_max = max_over_ranks(kms, ws)
+    profiled_step(args, step)
     err_code = tc.device_error()
 
     # end-to-end through the public API with host buffers
