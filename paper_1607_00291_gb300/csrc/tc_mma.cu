@@ -10,31 +10,37 @@
 // TMA box per operand and k-tile, which lands in exactly the layout the gather
 // produces.  Converter warps split every value into bf16 pieces
 // (x = b0 + b1 [+ b2], each b_i = RN_bf16 of the residual left so far, every
-// residual exact in FP32) and write them in the tensor core's K-major
-// canonical layout.  One elected thread issues, per 16-wide k-slice, a
-// tcgen05.mma for every piece pair (i, j) with i + j < pieces -- three for two
-// pieces (BF16x3), six for three (BF16x6) -- into an FP32 accumulator in
-// Tensor Memory.
+// residual exact in FP32): A's pieces straight into Tensor Memory
+// (tcgen05.st; one thread per row, the tensor core's A-in-TMEM layout), B's
+// into shared memory in the tensor core's K-major canonical layout.  One
+// elected thread issues, per 16-wide k-slice, a tcgen05.mma (A from Tensor
+// Memory, B from shared memory) for every piece pair (i, j) with i + j <
+// pieces -- three for two pieces (BF16x3), six for three (BF16x6) -- into an
+// FP32 accumulator in Tensor Memory.  Keeping A's pieces out of shared memory
+// cuts the shared-memory traffic per k-tile, which with the tensor core's
+// operand reads is what sets the pace, by a quarter or more.
 //
 // Accumulation: the tensor core adds in FP32 with unspecified rounding, and
 // over thousands of terms that alone exceeds 1e-5 of sum|a||b| (measured on
 // the spiky 4096^3 workload: 2.25e-5 with 4096-term chains).  So a tile's
 // contracted range is processed in chunks of at most 1024 terms, each into a
-// fresh accumulator (two buffers, alternating), and the epilogue warps add the
-// finished chunks into a running float-float sum (Knuth's two-sum) that stays
-// in Tensor Memory.  After the last chunk they apply alpha/beta through
+// fresh accumulator, and the epilogue warps add the finished chunks into a
+// running float-float sum (Knuth's two-sum) that stays in Tensor Memory,
+// releasing the accumulator to the next chunk's MMAs as soon as they have
+// read it.  After the last chunk they apply alpha/beta through
 // rscat(C) + cscat(C), or -- when a tile's range is also split across CTAs for
 // parallelism -- store the FP32 partial that K4 sums the same compensated way.
 //
 // Warp roles (672 threads; 704 in the BOX form): warps 0-7 load (cp.async),
 // or in the BOX form convert, warps 8-15 convert, warps 16-19 run the
 // epilogue (one per Tensor Memory lane quarter), warp 20 owns the Tensor
-// Memory allocation (512 columns: two accumulators, the hi and lo words of
-// the running sum) and its lane 0 issues the MMAs, and in the BOX form lane 0
-// of warp 21 issues the boxes.  The epilogue of one chunk overlaps the MMAs
-// of the next.  Hand-offs go through mbarriers: raw_full (cp.async
-// completion, or the boxes' transaction count) / raw_empty, mma_full /
-// mma_empty (tcgen05.commit), acc_full[2] (tcgen05.commit) / acc_empty[2].
+// Memory allocation (512 columns: the accumulator, the hi and lo words of the
+// running sum, A's piece stages) and its lane 0 issues the MMAs, and in the
+// BOX form lane 0 of warp 21 issues the boxes.  The output stores of one tile
+// overlap the MMAs of the next.  Hand-offs go through mbarriers: raw_full
+// (cp.async completion, or the boxes' transaction count) / raw_empty,
+// mma_full / mma_empty (tcgen05.commit), acc_full (tcgen05.commit) /
+// acc_empty.
 // Every mbarrier wait is bounded: on expiry the CTA records
 // TC_ERR_DEVICE_TIMEOUT in the device error word and raises a CTA-wide abort
 // flag; the roles leave their loops together (barrier reductions of the
@@ -76,20 +82,21 @@ constexpr int QR = 16, QPUB = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
 constexpr int BNMAX = 128;        // widest output tile (columns)
 constexpr int CHUNK_KT = 32;      // k-tiles per accumulation chunk (1024 terms)
-constexpr uint32_t TM_ACC = 0, TM_HI = 2 * BNMAX, TM_LO = 3 * BNMAX, TM_COLS = 4 * BNMAX;
+// Tensor Memory columns: accumulator, running hi and lo words, A's piece
+// stages (16 columns per piece and k-tile: 32 bf16 k-values, two per column)
+constexpr uint32_t TM_ACC = 0, TM_HI = BNMAX, TM_LO = 2 * BNMAX, TM_A = 3 * BNMAX, TM_COLS = 512;
 
 // Shared-memory plan.  Raw FP32 stages hide the load latency; bf16 MMA stages
-// let the converters run ahead of the tensor core.  The gathers need more of
-// the former (four), the box form gains from a third MMA stage instead
-// (measured: 0.590 against 0.606 ms on 4096^3 BF16x3).
+// (B's pieces in shared memory, A's in Tensor Memory) let the converters run
+// ahead of the tensor core.
 template <int NS, bool BOX>
 struct Lay {
-  static constexpr int RS = NS == 3 ? 3 : (BOX ? 3 : 4);  // raw FP32 stages
-  static constexpr int MS = NS == 3 ? 2 : (BOX ? 3 : 2);  // bf16 MMA stages
-  static constexpr int PA = BM * BK * 2;       // one bf16 piece of A
-  static constexpr int PB = BNMAX * BK * 2;
-  static constexpr int B_OFF = NS * PA;
-  static constexpr int MMA_STAGE = NS * (PA + PB);
+  static constexpr int RS = 5;                   // raw FP32 stages
+  static constexpr int MS = NS == 3 ? 2 : 3;     // bf16 MMA stages
+  static constexpr int PB = BNMAX * BK * 2;      // one bf16 piece of B
+  static constexpr int MMA_STAGE = NS * PB;
+  static constexpr uint32_t TA_STAGE = NS * 16;  // Tensor Memory columns of A's pieces
+  static_assert(TM_A + MS * TA_STAGE <= TM_COLS, "Tensor Memory plan");
   static constexpr int RAW_A = BM * BK * 4;
   static constexpr int RAW_STAGE = RAW_A + BNMAX * BK * 4;
   static constexpr int MMA0 = 0;
@@ -365,6 +372,50 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
     split8_store<NS>(v, piece0, PBY, panel_off<R>(r, q));
   }
 }
+// A's raw panel (BM rows x BK k) into NS bf16 pieces in Tensor Memory at
+// column `tcol` (+16 per piece).  Converter warp cw (of NCVW) may access only
+// its Tensor Memory lane quarter cw % 4 (its warp index in the CTA is cw plus
+// a multiple of 4), so it converts rows 32 (cw % 4) + lane, and of each row
+// the 8-value k-chunks cw / 4, cw / 4 + NCVW / 4, ...; a chunk's pieces are
+// four columns each.
+template <int NS, int NCVW>
+__device__ __forceinline__ void convert_a_tmem(int cw, int lane, const uint8_t* raw,
+                                               uint32_t tmem, uint32_t tcol, bool kcontig) {
+  static_assert(NCVW % 4 == 0 && 4 % (NCVW / 4) == 0, "converter warps per lane quarter");
+  const float* rf = reinterpret_cast<const float*>(raw);
+  const int q = cw & 3, r = 32 * q + lane;
+  const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + tcol;
+#pragma unroll
+  for (int c = cw >> 2; c < BK / 8; c += NCVW / 4) {
+    float v[8];
+    if (kcontig) {
+      const float* row = rf + r * BK;
+      const float4 x0 = *reinterpret_cast<const float4*>(row + (((2 * c) ^ (r & 7)) << 2));
+      const float4 x1 = *reinterpret_cast<const float4*>(row + (((2 * c + 1) ^ (r & 7)) << 2));
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = rf[(8 * c + j) * BM + r];
+    }
+#pragma unroll
+    for (int sidx = 0; sidx < NS; ++sidx) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        if (sidx + 1 < NS) {
+          const float2 f = __bfloat1622float2(b);
+          v[2 * j] -= f.x;
+          v[2 * j + 1] -= f.y;
+        }
+        w[j] = *reinterpret_cast<uint32_t*>(&b);
+      }
+      tmem_st4(base + (uint32_t)(sidx * 16 + c * 4), w);
+    }
+  }
+}
+
 // BOX = false: the loader warps gather every operand through the scatter
 // vectors (no box code at all).  BOX = true: both operands of every work item
 // are TMA boxes, issued by the box warp; there are no loaders, and their eight
@@ -387,8 +438,8 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
   uint64_t* raw_empty = raw_full + RS;
   uint64_t* mma_full = raw_empty + RS;
   uint64_t* mma_empty = mma_full + MS;
-  uint64_t* acc_full = mma_empty + MS;  // [2]
-  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint64_t* acc_full = mma_empty + MS;  // [1] used (two reserved)
+  uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
@@ -576,15 +627,20 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
           record_timeout(abort, a.err);
           break;
         }
+        tc_fence_after();  // the MMAs that read this stage's A pieces are complete
         const uint8_t* raw = smem + Ly::RAW0 + rs * Ly::RAW_STAGE;
         uint8_t* st = smem + Ly::MMA0 + ms * Ly::MMA_STAGE;
-        convert_panel<BM, NS, NCV>(t, raw, st, akc, BM);
+        convert_a_tmem<NS, NCV / 32>(t >> 5, lane, raw, tmem, TM_A + (uint32_t)ms * Ly::TA_STAGE,
+                                     akc);
         if (!BOX || rsB == BNMAX)  // the common k-row pitch as a constant: immediate offsets
-          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, BNMAX);
+          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, BNMAX);
         else
-          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st + Ly::B_OFF, bkc, rsB);
-        // every lane's pieces visible to the tensor core's proxy and every
-        // lane's raw reads done, then one arrival per warp on each barrier
+          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, rsB);
+        // every lane's pieces in Tensor Memory and visible to the tensor
+        // core's proxy in shared memory, every lane's raw reads done, then one
+        // arrival per warp on each barrier
+        tmem_st_wait();
+        tc_fence_before();
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -639,19 +695,18 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       const int cols = it.rows_b;
       bool ok = true;
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
-        const int b = (int)(gc & 1);
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
         if (have && !*abort) {
-          if (!mbar_wait(&acc_full[b], (uint32_t)((gc >> 1) & 1), abort)) record_timeout(abort, a.err);
+          if (!mbar_wait(&acc_full[0], (uint32_t)(gc & 1), abort)) record_timeout(abort, a.err);
         }
         tc_fence_after();
         ok = __all_sync(0xffffffffu, !*abort);
         if (ok) {
-          const uint32_t acc = lane_base + TM_ACC + (uint32_t)(b * BNMAX);
+          // fold the chunk into the running sum (hi, lo)
           for (int cb = 0; cb < bn; cb += 8) {
             float v[8], hi[8], lo[8];
             if (have) {
-              tmem_ld8(acc + (uint32_t)cb, v);
+              tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
             } else {
 #pragma unroll
               for (int q = 0; q < 8; ++q) v[q] = 0.f;
@@ -672,40 +727,44 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
                 lo[q] = __fadd_rn(lo[q], e);
               }
             }
-            if (!last) {
-              tmem_st8(lane_base + TM_HI + (uint32_t)cb, hi);
-              tmem_st8(lane_base + TM_LO + (uint32_t)cb, lo);
-              continue;
-            }
-            // output of the tile: alpha * (hi + lo) [+ beta * C], or the partial.
-            // The three cases are separate loops so that no load of C is ever
-            // issued when beta == 0 (C is then only written), and the loads of
-            // C for beta != 0 are all in flight before the first store.
-            if (mv) {
-              if (!direct) {
+            tmem_st8(lane_base + TM_HI + (uint32_t)cb, hi);
+            tmem_st8(lane_base + TM_LO + (uint32_t)cb, lo);
+          }
+          tmem_st_wait();
+        }
+        // the accumulator is free for the next chunk's MMAs
+        tc_fence_before();
+        mbar_arrive(&acc_empty[0]);
+        if (!ok) break;
+        if (!last) continue;
+        // output of the tile: alpha * (hi + lo) [+ beta * C], or the partial.
+        // The three cases are separate loops so that no load of C is ever
+        // issued when beta == 0 (C is then only written), and the loads of
+        // C for beta != 0 are all in flight before the first store.
+        for (int cb = 0; cb < bn; cb += 8) {
+          float hi[8], lo[8];
+          tmem_ld8(lane_base + TM_HI + (uint32_t)cb, hi);
+          tmem_ld8(lane_base + TM_LO + (uint32_t)cb, lo);
+          if (mv) {
+            if (!direct) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                  if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
-              } else if (be == 0.f) {
+              for (int q = 0; q < 8; ++q)
+                if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
+            } else if (be == 0.f) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                  if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
-              } else {
-                float old[8];
+              for (int q = 0; q < 8; ++q)
+                if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
+            } else {
+              float old[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
+              for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                  if (cb + q < cols)
-                    crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
-              }
+              for (int q = 0; q < 8; ++q)
+                if (cb + q < cols)
+                  crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
             }
           }
-          if (!last) tmem_st_wait();
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[b]);
-        if (!ok) break;
       }
     }
   } else if (BOX && warp == BOX_WARP) {
@@ -782,15 +841,14 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       if (dyn) mbar_arrive(&wq_empty[j % QR]);  // (this thread alone reads the queue here)
       const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
       for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
-        const int b = (int)(gc & 1);
-        const int64_t u = gc >> 1;  // use count of accumulator buffer b
-        if (u > 0 && !mbar_wait(&acc_empty[b], (uint32_t)((u - 1) & 1), abort)) {
+        // the epilogue has folded the accumulator's previous chunk
+        if (gc > 0 && !mbar_wait(&acc_empty[0], (uint32_t)((gc - 1) & 1), abort)) {
           record_timeout(abort, a.err);
           failed = true;
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + TM_ACC + (uint32_t)(b * BNMAX);
+        const uint32_t acc = tmem + TM_ACC;
         const int64_t kt0 = (int64_t)ch * CHUNK_KT;
         const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
@@ -802,26 +860,28 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
           }
           tc_fence_after();
           const uint32_t st = base + ms * Ly::MMA_STAGE;
+          const uint32_t ta = tmem + TM_A + (uint32_t)ms * Ly::TA_STAGE;
 #pragma unroll
           for (int ksl = 0; ksl < BK / 16; ++ksl) {
-            const uint32_t ao = ksl * 2 * (BM / 8) * 128, bo = ksl * 2 * (BNMAX / 8) * 128;
-            uint64_t dA[NS], dB[NS];
+            const uint32_t bo = ksl * 2 * (BNMAX / 8) * 128;
+            uint32_t tA[NS];
+            uint64_t dB[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-              dA[i] = smem_desc(st + i * Ly::PA + ao, (BM / 8) * 128, 128);
-              dB[i] = smem_desc(st + Ly::B_OFF + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
+              tA[i] = ta + (uint32_t)(i * 16 + ksl * 8);
+              dB[i] = smem_desc(st + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
             }
-            mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
+            mma_bf16_ts(acc, tA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
 #pragma unroll
             for (int ts = 1; ts < NS; ++ts)
 #pragma unroll
-              for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+              for (int i = 0; i <= ts; ++i) mma_bf16_ts(acc, tA[i], dB[ts - i], idesc, 1u);
           }
           mma_commit(&mma_empty[ms]);
         }
         if (failed) break;
-        if (kt1 > kt0) mma_commit(&acc_full[b]);
-        else mbar_arrive(&acc_full[b]);  // nothing to accumulate: hand over at once
+        if (kt1 > kt0) mma_commit(&acc_full[0]);
+        else mbar_arrive(&acc_full[0]);  // nothing to accumulate: hand over at once
       }
     }
     // every MMA this thread issued has completed once this commit arrives
