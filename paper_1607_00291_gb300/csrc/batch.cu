@@ -32,7 +32,9 @@ using namespace tc;
 namespace {
 
 struct ProbCfg {
-  int bn = 0;        // tensor-core tile width (FP64: fixed tile)
+  int bn = 0;        // tile width (n)
+  int bm = 128;      // tile height (m)
+  int cls = 0;       // FP64: tile class (f64_batch_tile)
   int splits = 1;
   int64_t kps = 0;   // k per split
   int64_t tiles = 0;
@@ -226,7 +228,8 @@ struct tc_plan {
   int64_t* d_scat = nullptr;
   DevProblem* d_probs = nullptr;
   WorkItem* d_items = nullptr;
-  unsigned long long* d_counter = nullptr;  // work counter of the persistent mainloop
+  unsigned long long* d_counter = nullptr;  // work counters of the persistent mainloop(s)
+  int64_t class_off[kF64BatchClasses + 1] = {};  // FP64: the work list's tile classes
   int32_t* d_split = nullptr;
   int64_t* d_split_cols = nullptr;
   int64_t split_cols = 0;
@@ -236,6 +239,7 @@ struct tc_plan {
   int pieces = 2;
   int reduce_f64 = 0;  // the split-reduction setting when the plan was created
   int64_t ctas = 152;
+  int64_t sms = 152;
 };
 
 namespace {
@@ -243,7 +247,8 @@ namespace {
 int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const int sms = sm_count();
   const bool f64 = pl->mode == TC_MODE_F64;
-  pl->ctas = f64 ? (int64_t)sms * f64_batch_ctas_per_sm() : sms;
+  pl->ctas = sms;
+  pl->sms = sms;
   pl->reduce_f64 = split_reduction_f64() ? 1 : 0;
   pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
   std::vector<double> alpha, beta;
@@ -261,16 +266,30 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->cfg.resize(np);
 
   // per-problem tiles and k-splits
-  const int tm_f = f64_batch_tile_m(), tn_f = f64_batch_tile_n(), tk_f = f64_tile_k();
+  const int tk_f = f64_tile_k();
   double total_cost = 0;
   std::vector<double> cost(np);
   for (int i = 0; i < np; ++i) {
     const Layout& L = pl->planned[i].L;
     ProbCfg& c = pl->cfg[i];
     if (f64) {
-      c.bn = tn_f;
-      c.tiles = ((L.m + tm_f - 1) / tm_f) * ((L.n + tn_f - 1) / tn_f);
-      cost[i] = (double)c.tiles * std::max<int64_t>(1, (L.k + tk_f - 1) / tk_f);
+      // the tile class that pads the problem least (ties: the larger tile)
+      double best = 0;
+      for (int cl = 0; cl < kF64BatchClasses; ++cl) {
+        int bm, bn;
+        f64_batch_tile(cl, &bm, &bn);
+        const double padded = (double)((L.m + bm - 1) / bm * bm) * (double)((L.n + bn - 1) / bn * bn);
+        if (cl == 0 || padded < best) {
+          best = padded;
+          c.cls = cl;
+          c.bm = bm;
+          c.bn = bn;
+        }
+      }
+      c.tiles = ((L.m + c.bm - 1) / c.bm) * ((L.n + c.bn - 1) / c.bn);
+      // in warp x k-tile units (a warp computes 32 x 32)
+      cost[i] = (double)c.tiles * (c.bm / 32) * (c.bn / 32) *
+                std::max<int64_t>(1, (L.k + tk_f - 1) / tk_f);
     } else {
       TuneVal tv{0, 1};
       // tuning times one CTA: skip problems too large to time quickly that way
@@ -319,14 +338,15 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     }
   }
   if (f64) {
-    const double fair = total_cost / (double)pl->ctas;
+    // a warp's fair share of the batch in k-tiles (eight warps per SM)
+    const double fair = total_cost / (8.0 * (double)sms);
     for (int i = 0; i < np; ++i) {
       const Layout& L = pl->planned[i].L;
       ProbCfg& c = pl->cfg[i];
       const int64_t KT = (L.k + tk_f - 1) / tk_f;
       int64_t s = 1;
       if (KT > 0 && fair > 0) {
-        const double item = cost[i] / (double)c.tiles;  // k-tiles per tile
+        const double item = (double)KT;  // k-tiles per tile
         s = (int64_t)std::ceil(item / std::max(1.0, fair / 4.0));
         s = std::max<int64_t>(1, std::min<int64_t>(s, KT));
       }
@@ -356,27 +376,37 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       pl->max_n_split = std::max(pl->max_n_split, pl->planned[i].L.n);
     }
   }
-  // longest items first (k-tiles of the item), stable for locality
+  // longest items first (k-tiles of the item), stable for locality; FP64:
+  // grouped by tile class first, one persistent launch per class
   auto item_cost = [&](const WorkItem& w) {
     const ProbCfg& c = pl->cfg[w.prob];
     const Layout& L = pl->planned[w.prob].L;
     const int64_t kb = (int64_t)w.split * c.kps, ke = std::min<int64_t>(L.k, kb + c.kps);
     return (double)std::max<int64_t>(0, ke - kb) * (f64 ? 1.0 : c.bn / 128.0);
   };
-  std::stable_sort(items.begin(), items.end(),
-                   [&](const WorkItem& x, const WorkItem& y) { return item_cost(x) > item_cost(y); });
+  std::stable_sort(items.begin(), items.end(), [&](const WorkItem& x, const WorkItem& y) {
+    if (f64 && pl->cfg[x.prob].cls != pl->cfg[y.prob].cls)
+      return pl->cfg[x.prob].cls < pl->cfg[y.prob].cls;
+    return item_cost(x) > item_cost(y);
+  });
+  for (int cl = 0; cl <= kF64BatchClasses; ++cl) pl->class_off[cl] = 0;
+  if (f64) {
+    for (const WorkItem& w : items) pl->class_off[pl->cfg[w.prob].cls + 1]++;
+    for (int cl = 0; cl < kF64BatchClasses; ++cl) pl->class_off[cl + 1] += pl->class_off[cl];
+  }
   pl->nitems = (int64_t)items.size();
   pl->n_split = (int32_t)splitp.size();
   if (const char* lg = std::getenv("TC_LOG")) {
     if (lg[0] == '1') {
-      std::map<int, int> bns;
+      std::map<std::pair<int, int>, int> tiles;
       double ksteps = 0;
       for (const WorkItem& w : items) ksteps += item_cost(w);
-      for (int i = 0; i < np; ++i) bns[pl->cfg[i].bn]++;
+      for (int i = 0; i < np; ++i) tiles[{pl->cfg[i].bm, pl->cfg[i].bn}]++;
       std::fprintf(stderr, "[libtc] batch plan: %d problems, %lld work items, %d split, "
-                   "%.3g k-index-units of work; tile widths:", np, (long long)pl->nitems,
-                   pl->n_split, ksteps);
-      for (const auto& kv : bns) std::fprintf(stderr, " %d x%d", kv.first, kv.second);
+                   "%.3g k-index-units of work; tiles (m x n: problems):", np,
+                   (long long)pl->nitems, pl->n_split, ksteps);
+      for (const auto& kv : tiles)
+        std::fprintf(stderr, " %dx%d: %d", kv.first.first, kv.first.second, kv.second);
       std::fprintf(stderr, "\n");
     }
   }
@@ -397,7 +427,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const size_t o_scols = take(sizeof(int64_t) * (pl->n_split + 1));
   const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
   const size_t o_tmap = take(sizeof(CUtensorMap) * 2 * std::max(np, 1));
-  const size_t o_ctr = take(sizeof(unsigned long long));
+  const size_t o_ctr = take(sizeof(unsigned long long) * kF64BatchClasses);
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -509,7 +539,8 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.probs = plan->d_probs;
     q.items = plan->d_items;
     q.nitems = plan->nitems;
-    q.ctas = plan->ctas;
+    for (int cl = 0; cl <= kF64BatchClasses; ++cl) q.class_off[cl] = plan->class_off[cl];
+    q.sms = plan->sms;
     q.split_probs = plan->d_split;
     q.split_col_prefix = plan->d_split_cols;
     q.split_cols = plan->split_cols;

@@ -28,8 +28,10 @@ constexpr int BK = 16;
 
 // A BM_ x BN_ output tile computed by (BM_/32) x (BN_/32) warps of 32 x 32.
 // The single-contraction kernels use 128 x 64 (one 256-thread CTA per SM);
-// batches use 64 x 64 (128-thread CTAs, two per SM): the problems of a batch
-// are small, and a finer tile pads them less.
+// batches choose per problem among 64 x 64, 32 x 64 and 64 x 32 (eight warps
+// per SM in every case): the problems of a batch are small, and the tile that
+// pads a problem least wastes the fewest FP64 operations.  (32 x 32 would pad
+// the 512-problem workload 1 % less, but a one-warp CTA spills registers.)
 template <int BM_, int BN_>
 struct FT {
   static constexpr int BM = BM_, BN = BN_;
@@ -44,7 +46,6 @@ struct FT {
                 "tile shape");
 };
 using F1 = FT<128, 64>;  // single contractions
-using FB = FT<64, 64>;   // batches
 constexpr int BM = F1::BM, BN = F1::BN, NT = F1::NT;
 constexpr size_t kSmem = F1::SMEM;
 
@@ -258,10 +259,17 @@ __global__ void __launch_bounds__(NT, 1)
 // and then claims the next unclaimed item from `counter` (zero at launch).
 // Unsplit tiles finish in place; split ones leave FP64 partials in
 // [split][n][m] for k_f64_batched_reduce.
-template <typename T>
-__global__ void __launch_bounds__(FB::NT, 2)
+template <int BM_, int BN_>
+struct FBatch {
+  using F = FT<BM_, BN_>;
+  static constexpr int CTAS_PER_SM = 8 / (F::NT / 32);  // eight warps per SM
+};
+
+template <typename T, class FBt>
+__global__ void __launch_bounds__(FBt::F::NT, FBt::CTAS_PER_SM)
     k_f64_batched(const DevProblem* __restrict__ probs, const WorkItem* __restrict__ items,
                   int64_t nitems, unsigned long long* __restrict__ counter) {
+  using FB = typename FBt::F;
   constexpr int BM = FB::BM, BN = FB::BN;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t next_w;
@@ -381,28 +389,45 @@ cudaError_t launch_t(const F64Launch& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
+using FB0 = FBatch<64, 64>;
+using FB1 = FBatch<32, 64>;
+using FB2 = FBatch<64, 32>;
+
+// One tile class's persistent launch over its slice of the work list.
+template <typename T, class FBt>
+cudaError_t launch_class(const F64BatchLaunch& q, int cls, cudaStream_t s) {
+  using F = typename FBt::F;
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_f64_batched<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FB::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_f64_batched<T, FBt>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
+  const int64_t n = q.class_off[cls + 1] - q.class_off[cls];
+  if (n <= 0) return cudaSuccess;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.sms * FBt::CTAS_PER_SM, n));
+  k_f64_batched<T, FBt><<<(unsigned)grid, F::NT, F::SMEM, s>>>(q.probs, q.items + q.class_off[cls],
+                                                               n, q.counter + cls);
+  note_launch();
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
   if (q.nitems > 0) {
     if (!q.counter) return cudaErrorInvalidValue;
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, q.nitems));
-    // the work counter starts from zero in every launch (a memset node under capture)
-    if (cudaMemsetAsync(q.counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    // the work counters start from zero in every launch (a memset node under capture)
+    if (cudaMemsetAsync(q.counter, 0, sizeof(unsigned long long) * kF64BatchClasses, s) !=
+        cudaSuccess)
       return cudaGetLastError();
     mainloop_event_before(s);
-    k_f64_batched<T><<<(unsigned)grid, FB::NT, FB::SMEM, s>>>(q.probs, q.items, q.nitems,
-                                                              q.counter);
-    note_launch();
+    cudaError_t e;
+    if ((e = launch_class<T, FB0>(q, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_class<T, FB1>(q, 1, s)) != cudaSuccess) return e;
+    if ((e = launch_class<T, FB2>(q, 2, s)) != cudaSuccess) return e;
     if (q.n_split_probs > 0) {
       const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 16));
       const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q.split_cols, 16384));
@@ -424,9 +449,17 @@ cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s) {
 int f64_tile_m() { return BM; }
 int f64_tile_n() { return BN; }
 int f64_tile_k() { return BK; }
-int f64_batch_tile_m() { return FB::BM; }
-int f64_batch_tile_n() { return FB::BN; }
-int f64_batch_ctas_per_sm() { return 2; }
+void f64_batch_tile(int cls, int* bm, int* bn) {
+  static const int t[kF64BatchClasses][2] = {
+      {FB0::F::BM, FB0::F::BN}, {FB1::F::BM, FB1::F::BN}, {FB2::F::BM, FB2::F::BN}};
+  *bm = t[cls][0];
+  *bn = t[cls][1];
+}
+int f64_batch_ctas_per_sm(int cls) {
+  static const int c[kF64BatchClasses] = {FB0::CTAS_PER_SM, FB1::CTAS_PER_SM,
+                                          FB2::CTAS_PER_SM};
+  return c[cls];
+}
 
 // CTAs for the FP64 mainloop: plain tiling (one CTA per tile) when the tiles
 // fill whole waves of `max_ctas` (or no partial workspace is available),

@@ -49,9 +49,11 @@ int f64_tile_m();
 int f64_tile_n();
 int f64_tile_k();
 // tiles and resident CTAs per SM of the batched FP64 kernel
-int f64_batch_tile_m();
-int f64_batch_tile_n();
-int f64_batch_ctas_per_sm();
+// FP64 batch tile classes: class c computes f64_batch_tile(c) = bm x bn tiles
+// in its own persistent launch of f64_batch_ctas_per_sm(c) CTAs per SM.
+constexpr int kF64BatchClasses = 3;
+void f64_batch_tile(int cls, int* bm, int* bn);
+int f64_batch_ctas_per_sm(int cls);
 
 // Access plan of one operand of the tensor-core mainloop (Section 7.3's
 // preference for unit-stride access, in the GPU's terms).  When the rows of a
@@ -143,15 +145,16 @@ cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
 struct F64BatchLaunch {
   tc_dtype dtype;
   const DevProblem* probs;
-  const WorkItem* items;
+  const WorkItem* items;      // the work list, tile class by tile class
   int64_t nitems;
-  int64_t ctas;
+  int64_t class_off[kF64BatchClasses + 1];  // class c: items [class_off[c], class_off[c + 1])
+  int64_t sms;
   const int32_t* split_probs;
   const int64_t* split_col_prefix;
   int64_t split_cols;
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;
-  unsigned long long* counter;  // device work counter for dynamic items, or null
+  unsigned long long* counter;  // device work counters, one per tile class
 };
 cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s);
 
