@@ -76,7 +76,7 @@ constexpr int KRING = 2;
 // Batches take their work items from a shared counter: loader thread 0 claims
 // items up to QPUB ahead of the loaders and publishes them in a ring of QR
 // entries that every role reads in order.  A role lags the loaders by at most
-// the pipeline's depth in items (raw and MMA stages plus two accumulators),
+// the pipeline's depth in items (raw and MMA stages plus the accumulator),
 // well inside the ring.
 constexpr int QR = 16, QPUB = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
