@@ -221,11 +221,52 @@ def host_bytes(spec):
 
 # ---- TTGT comparison (transpose-transpose-GEMM-transpose, Section 3) ----------------------
 
-def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta):
+class CublasBf16x9:
+    """cuBLAS's FP32 GEMM emulated on the bf16 tensor cores (each FP32 input
+    split into three bf16 values, nine products: CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+    emulation forced), called through its C API on torch's stream; `unavailable`
+    holds the reason when the library or the compute type is missing."""
+    COMPUTE_32F_EMULATED_16BFX9, EMULATION_EAGER, R_32F, OP_N, GEMM_DEFAULT = 78, 2, 0, 0, -1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.unavailable = None
+        self.handle = ctypes.c_void_p()
+        try:
+            torch.matmul(torch.ones(8, 8, device="cuda"), torch.ones(8, 8, device="cuda"))
+            self.lib = ctypes.CDLL("libcublas.so.13")
+            if self.lib.cublasCreate_v2(ctypes.byref(self.handle)) != 0:
+                raise RuntimeError("cublasCreate failed")
+            if self.lib.cublasSetEmulationStrategy(self.handle, self.EMULATION_EAGER) != 0:
+                raise RuntimeError("cublasSetEmulationStrategy failed")
+        except (OSError, AttributeError, RuntimeError) as e:
+            self.unavailable = str(e).splitlines()[0][:120]
+
+    def matmul(self, A, B):
+        """A (m x k) @ B (k x n), both row-major FP32 on the device, into a new tensor."""
+        ct = self.ct
+        m, k = A.shape
+        n = B.shape[1]
+        C = torch.empty(m, n, dtype=torch.float32, device=A.device)
+        self.lib.cublasSetStream_v2(self.handle, ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+        one, zero = ct.c_float(1.0), ct.c_float(0.0)
+        # row-major C = A B is column-major C^T = B^T A^T
+        st = self.lib.cublasGemmEx(self.handle, self.OP_N, self.OP_N, n, m, k, ct.byref(one),
+                                   ct.c_void_p(B.data_ptr()), self.R_32F, n,
+                                   ct.c_void_p(A.data_ptr()), self.R_32F, k, ct.byref(zero),
+                                   ct.c_void_p(C.data_ptr()), self.R_32F, n,
+                                   self.COMPUTE_32F_EMULATED_16BFX9, self.GEMM_DEFAULT)
+        if st != 0:
+            raise RuntimeError(f"cublasGemmEx (BF16x9 emulation) returned status {st}")
+        return C
+
+
+def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta, gemm=torch.matmul):
     """The contraction the way the paper's TTGT baseline computes it: copy A
     and B into matrix order (I, P) and (P, J), one library GEMM (cuBLAS via
-    torch.matmul), then a strided copy of the product back into C's layout.
-    Returns the bytes of the temporary matrices."""
+    torch.matmul, or `gemm`), then a strided copy of the product back into
+    C's layout.  Returns the bytes of the temporary matrices."""
     I = [x for x in labC if x in labA]
     J = [x for x in labC if x in labB]
     P = [x for x in labA if x in labB]
@@ -233,7 +274,7 @@ def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta):
     size = lambda xs: int(np.prod([ext[x] for x in xs])) if xs else 1  # noqa: E731
     At = A.permute(*[labA.index(x) for x in I + P]).contiguous().reshape(size(I), size(P))
     Bt = B.permute(*[labB.index(x) for x in P + J]).contiguous().reshape(size(P), size(J))
-    Ct = torch.matmul(At, Bt)
+    Ct = gemm(At, Bt)
     back = Ct.reshape([ext[x] for x in I + J]).permute(*[(I + J).index(x) for x in labC])
     if beta == 0.0:
         C.copy_(back).mul_(alpha)
@@ -242,21 +283,22 @@ def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta):
     return (At.numel() + Bt.numel() + Ct.numel()) * At.element_size()
 
 
-def time_ttgt(problems, warm: int, K: int, flops: float, ws: int):
+def time_ttgt(problems, warm: int, K: int, flops: float, ws: int, gemm=torch.matmul):
     """Device time of the TTGT form of one step (all `problems`), with the
-    temporaries' bytes; FP32 GEMMs in full FP32 (no TF32)."""
+    temporaries' bytes; FP32 GEMMs in full FP32 (no TF32) unless `gemm` says
+    otherwise."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
         extra = 0
         for _ in range(warm):
-            extra = sum(ttgt_contract(*p) for p in problems)
+            extra = sum(ttgt_contract(*p, gemm=gemm) for p in problems)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(K):
             for p in problems:
-                ttgt_contract(*p)
+                ttgt_contract(*p, gemm=gemm)
         e1.record()
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
@@ -266,6 +308,28 @@ def time_ttgt(problems, warm: int, K: int, flops: float, ws: int):
             "ms_per_step": round(ms, 4), "temporary_bytes": int(extra),
             "what": "torch permute().contiguous() + torch.matmul (cuBLAS, FP64 or full FP32) + "
                     "strided copy back, same inputs, device time"}
+
+
+def ttgt_legs(problems, warm, K, flops, ws, ms_ours, fp32):
+    """The TTGT comparison line: full-precision GEMM, and for FP32 data also
+    cuBLAS's BF16x9-emulated FP32 GEMM (the vendor's split-bf16 tensor-core
+    path) between the same transposition copies."""
+    tt = time_ttgt(problems, warm, K, flops, ws)
+    tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms_ours, 3)
+    if fp32:
+        em = CublasBf16x9()
+        if em.unavailable:
+            tt["bf16x9"] = {"unavailable": em.unavailable}
+        else:
+            try:
+                t9 = time_ttgt(problems, warm, K, flops, ws, gemm=em.matmul)
+                tt["bf16x9"] = {"ms_per_step": t9["ms_per_step"], "value": t9["value"],
+                                "ours_over_ttgt_speed": round(t9["ms_per_step"] / ms_ours, 3),
+                                "what": "the same TTGT step with cublasGemmEx in "
+                                        "CUBLAS_COMPUTE_32F_EMULATED_16BFX9 (emulation forced)"}
+            except RuntimeError as e:
+                tt["bf16x9"] = {"unavailable": str(e)[:120]}
+    return tt
 
 
 # ---- CPU oracle baseline -----------------------------------------------------------------
@@ -547,8 +611,7 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
     if not args.no_ttgt:
         for c, c0 in zip(calls, C0):
             c[4].copy_(c0)
-        tt = time_ttgt(calls, warm, K, flops, ws)
-        tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms, 3)
+        tt = ttgt_legs(calls, warm, K, flops, ws, ms, mode != "f64")
         tt["ours_workspace_bytes"] = int(sum(w.numel() for w in works))
         line["ttgt"] = tt
     if cpu is not None and rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -772,9 +835,8 @@ def run_ours(args, ws, rank, local):
     # the TTGT form of the same step (cuBLAS GEMM between transposition copies)
     if not args.no_ttgt:
         dC.copy_(C0)
-        tt = time_ttgt([(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.alpha, spec.beta)],
-                       warm, K, flops, ws)
-        tt["ours_over_ttgt_speed"] = round(tt["ms_per_step"] / ms_max, 3)
+        tt = ttgt_legs([(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.alpha, spec.beta)],
+                       warm, K, flops, ws, ms_max, spec.mode != "f64")
         tt["ours_workspace_bytes"] = int(wsz)
         line["ttgt"] = tt
 
