@@ -243,6 +243,12 @@ class CublasBf16x9:
         except (OSError, AttributeError, RuntimeError) as e:
             self.unavailable = str(e).splitlines()[0][:120]
 
+    def close(self):
+        torch.cuda.synchronize()
+        if self.handle.value:
+            self.lib.cublasDestroy_v2(self.handle)
+            self.handle = self.ct.c_void_p()
+
     def matmul(self, A, B):
         """A (m x k) @ B (k x n), both row-major FP32 on the device, into a new tensor."""
         ct = self.ct
@@ -329,6 +335,8 @@ def ttgt_legs(problems, warm, K, flops, ws, ms_ours, fp32):
                                         "CUBLAS_COMPUTE_32F_EMULATED_16BFX9 (emulation forced)"}
             except RuntimeError as e:
                 tt["bf16x9"] = {"unavailable": str(e)[:120]}
+            finally:
+                em.close()
     return tt
 
 
