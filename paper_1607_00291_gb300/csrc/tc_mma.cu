@@ -694,6 +694,30 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       const bool mv = row < it.rows_a;
       const int cols = it.rows_b;
       bool ok = true;
+      // output of 8 columns of the tile: alpha * (hi + lo) [+ beta * C], or the
+      // partial.  The three cases are separate loops so that no load of C is
+      // ever issued when beta == 0 (C is then only written), and the loads of
+      // C for beta != 0 are all in flight before the first store.
+      auto out8 = [&](int cb, const float (&hi)[8], const float (&lo)[8]) {
+        if (!mv) return;
+        if (!direct) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
+        } else if (be == 0.f) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
+        } else {
+          float old[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols)
+              crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
+        }
+      };
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
         if (have && !*abort) {
@@ -701,7 +725,21 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         }
         tc_fence_after();
         ok = __all_sync(0xffffffffu, !*abort);
-        if (ok) {
+        // A short tile (one chunk of at most four k-tiles) is written straight
+        // from the accumulator -- the running sum would be (v, 0), the same
+        // values -- which saves the round trip through the hi and lo words but
+        // holds the accumulator until the stores are issued; for longer tiles
+        // the next tile's MMAs gain more from having it released first.
+        const bool direct_out = first && last && it.KT <= 4;
+        if (ok && direct_out) {
+          for (int cb = 0; cb < bn; cb += 8) {
+            float v[8], z[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = z[q] = 0.f;
+            if (have) tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
+            out8(cb, v, z);
+          }
+        } else if (ok) {
           // fold the chunk into the running sum (hi, lo)
           for (int cb = 0; cb < bn; cb += 8) {
             float v[8], hi[8], lo[8];
@@ -736,34 +774,13 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         tc_fence_before();
         mbar_arrive(&acc_empty[0]);
         if (!ok) break;
-        if (!last) continue;
-        // output of the tile: alpha * (hi + lo) [+ beta * C], or the partial.
-        // The three cases are separate loops so that no load of C is ever
-        // issued when beta == 0 (C is then only written), and the loads of
-        // C for beta != 0 are all in flight before the first store.
+        if (!last || direct_out) continue;  // (a short tile is written above)
+        // the tile's output from the running sum
         for (int cb = 0; cb < bn; cb += 8) {
           float hi[8], lo[8];
           tmem_ld8(lane_base + TM_HI + (uint32_t)cb, hi);
           tmem_ld8(lane_base + TM_LO + (uint32_t)cb, lo);
-          if (mv) {
-            if (!direct) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
-            } else if (be == 0.f) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
-            } else {
-              float old[8];
-#pragma unroll
-              for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                if (cb + q < cols)
-                  crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
-            }
-          }
+          out8(cb, hi, lo);
         }
       }
     }
