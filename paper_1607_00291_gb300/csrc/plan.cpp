@@ -215,8 +215,10 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
   }
   // step 7 (GPU): an operand read along its rows orders its row bundle by its
   // own strides, so that the loaders' consecutive rows are its unit-stride
-  // run.  For J and B this costs nothing: after step 4 C's unit stride lies
-  // in I, and the epilogue's threads run along I.  For I and A it moves C's
+  // run.  For J and B this costs little: after step 4 C's unit stride lies
+  // in I, and the epilogue's threads run along I (each store instruction
+  // still covers whole lines; only the distance between a tile's columns
+  // grows), and ordering J by C instead can cost B its box form.  For I and A it moves C's
   // unit-stride dim away from the epilogue's threads; A is read once per
   // output tile across from it, about k / 128 times C's traffic, so I is
   // re-sorted only for k >= 512.
