@@ -151,9 +151,13 @@ TC_API int tc_batched_workspace_size(tc_dtype dtype, tc_mode mode, int32_t count
                               const tc_problem* probs, size_t* bytes);
 
 /* Run `count` independent contractions of possibly different ranks, extents,
- * strides and labels in one persistent launch (plus one launch building all
- * scatter vectors and, in BF16X3 mode, one FP64 reduction launch).  Equivalent
- * to calling tc_contract on each problem.  Problems must not write overlapping
+ * strides and labels in one persistent launch per tile shape (one on the
+ * tensor cores; on the FP64 path one for each of the 64 x 64, 32 x 64 and
+ * 64 x 32 tiles the problems are given), plus one launch building all scatter
+ * vectors and one reduction launch for problems split along k.  The
+ * persistent CTAs claim work items (output tile x k-split, longest first)
+ * from a device counter reset before each launch.  Equivalent to calling
+ * tc_contract on each problem.  Problems must not write overlapping
  * C elements.  Creates and destroys a temporary plan (allocates and frees a
  * small device descriptor buffer; synchronises `stream` before freeing it). */
 TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
@@ -162,8 +166,9 @@ TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, cons
 /* Plan form for repeated batches: tc_plan_create validates and plans every
  * problem, chooses tiles (from the autotune table), and copies the
  * descriptors into a device buffer that the plan owns (cudaMalloc at create,
- * cudaFree at destroy).  tc_plan_execute only launches kernels, with no host
- * synchronisation and no allocation, so it can be captured in a CUDA graph. */
+ * cudaFree at destroy).  tc_plan_execute only enqueues work -- kernels and
+ * the memset of the work counters -- with no host synchronisation and no
+ * allocation, so it can be captured in a CUDA graph. */
 TC_API int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
                    tc_plan** out);
 TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);
