@@ -32,3 +32,31 @@ def test_status_strings_and_version():
     for code in L.STATUS:
         assert lib.tc_status_string(code)
     assert lib.tc_version() >= 100
+
+
+def test_no_cpu_fallback():
+    # the product path runs only in libtc's kernels: host tensors are refused,
+    # never contracted on the CPU
+    import pytest
+    import torch
+
+    import paper_1607_00291_gb300 as tc
+    A, B, C = torch.ones(4, 3, dtype=torch.float64), torch.ones(3, 5, dtype=torch.float64), \
+        torch.zeros(4, 5, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        tc.contract(A, "ip", B, "pj", C, "ij")
+    with pytest.raises(TypeError):
+        tc.contract_batched([(A, "ip", B, "pj", C, "ij", 1.0, 0.0)])
+    assert torch.count_nonzero(C) == 0
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    # with no library and no way to build one, loading fails loudly
+    import pytest
+
+    from paper_1607_00291_gb300 import _lib as L
+    monkeypatch.setattr(L, "_lib", None)
+    monkeypatch.setattr(L._build, "up_to_date", lambda: True)
+    monkeypatch.setattr(L._build, "LIB", str(tmp_path / "libtc.so"))
+    with pytest.raises(RuntimeError):
+        L.lib()
