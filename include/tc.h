@@ -77,8 +77,9 @@ enum {
 };
 
 /* One tensor operand: `rank` dimensions with lengths `len[d]` >= 0, strides
- * `stride[d]` (elements) and labels `labels[d]` (rank bytes, not necessarily
- * NUL-terminated).  rank 0 is a scalar.  All arrays are host memory, read only
+ * `stride[d]` (elements) and labels `labels[d]` (rank nonzero bytes, distinct
+ * within the tensor, not necessarily NUL-terminated; TC_ERR_LABEL otherwise).
+ * rank 0 is a scalar.  All arrays are host memory, read only
  * during the call. */
 typedef struct {
   int32_t rank;

@@ -98,7 +98,8 @@ def plan_describe(A, labA, B, labB, C, labC) -> dict:
     L.check(L.lib().tc_plan_describe(d(A, labA), d(B, labB), d(C, labC), info), "tc_plan_describe")
 
     def bundle(n, lens, s0, s1, labs):
-        return [dict(labels=labs[i].value.decode(), n=lens[i], s=(s0[i], s1[i])) for i in range(n)]
+        return [dict(labels=labs[i].value.decode("latin-1"), n=lens[i], s=(s0[i], s1[i]))
+                for i in range(n)]
 
     return dict(swapped=bool(info.swapped), m=info.m, n=info.n, k=info.k,
                 I=bundle(info.nI, info.I_len, info.I_sA, info.I_sC, info.I_labels),

@@ -45,9 +45,11 @@ int check_tensor(const tc_tensor* T) {
   if (T->rank > 0 && (!T->len || !T->stride || !T->labels)) return TC_ERR_ARG;
   for (int d = 0; d < T->rank; ++d)
     if (T->len[d] < 0) return TC_ERR_ARG;
-  for (int d = 0; d < T->rank; ++d)
+  for (int d = 0; d < T->rank; ++d) {
+    if (T->labels[d] == 0) return TC_ERR_LABEL;  // the folded label strings end at a NUL
     for (int e = d + 1; e < T->rank; ++e)
       if (T->labels[d] == T->labels[e]) return TC_ERR_LABEL;
+  }
   return TC_OK;
 }
 

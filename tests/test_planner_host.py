@@ -83,6 +83,7 @@ def test_error_codes():
     assert code("ab", (2, 3), "bc", (3, 4), "ad", (2, 4)) == -2       # label in one tensor
     assert code("ab", (2, 3), "bc", (3, 4), "abc", (2, 3, 4)) == -2   # label in all three
     assert code("aa", (2, 2), "a", (2,), "", ()) == -2                # repeated label
+    assert code("a\x00", (2, 3), "\x00c", (3, 4), "ac", (2, 4)) == -2  # a zero byte as label
     assert code("ab", (2, 3), "bc", (4, 4), "ac", (2, 4)) == -3       # extent mismatch
     assert code("ab", (2, 3), "bc", (3, 4), "ac", (2, 4), (1, 1)) == -4  # C overlaps itself
     assert code("ab", (2, 3), "bc", (3, 4), "ac", (2, 4), (4, 1)) == 0   # row-major C is fine
@@ -152,3 +153,25 @@ def test_workspace_is_vector_sized_not_operand_sized():
     sms = 152
     assert n.value <= 16 * 8 * (m + nn + k) + 4096 + 2 * sms * 128 * 64 * 8 + 256
     assert n.value < 679.5e6 / 20
+
+
+def test_rank16_operands_and_byte_labels():
+    # the widest operands the ABI takes (16 dims each), labelled with bytes
+    # outside ASCII, in scrambled orders and permuted dense layouts
+    rng = np.random.default_rng(16)
+    labels = [chr(c) for c in range(0xC0, 0xC0 + 24)]
+    I, J, P = labels[:8], labels[8:16], labels[16:24]
+    ext = {x: int(rng.integers(1, 4)) for x in labels}
+    labA = "".join(rng.permutation(I + P))
+    labB = "".join(rng.permutation(P + J))
+    labC = "".join(rng.permutation(I + J))
+
+    def lay(lab):
+        order = list(rng.permutation(list(lab)))
+        acc, st = 1, {}
+        for x in order:
+            st[x] = acc
+            acc *= ext[x]
+        return tuple(ext[x] for x in lab), tuple(st[x] for x in lab)
+
+    compare(labA, lay(labA), labB, lay(labB), labC, lay(labC))
