@@ -175,3 +175,31 @@ def test_rank16_operands_and_byte_labels():
         return tuple(ext[x] for x in lab), tuple(st[x] for x in lab)
 
     compare(labA, lay(labA), labB, lay(labB), labC, lay(labC))
+
+
+def test_wide_random_plans_with_folds_match_oracle():
+    # up to five dims per bundle with small extents, where label orders
+    # shared between tensors make sequential-contiguity folds common; some
+    # layouts are general column-major in the label order (every fold open)
+    rng = np.random.default_rng(5)
+    for t in range(200):
+        nI, nJ, nP = (int(x) for x in rng.integers(0, 6, 3))
+        if nI + nP > 16 or nP + nJ > 16 or nI + nJ > 16:
+            continue
+        labs = [chr(ord("a") + i) for i in range(nI + nJ + nP)]
+        I, J, P = labs[:nI], labs[nI:nI + nJ], labs[nI + nJ:]
+        ext = {x: int(rng.integers(1, 5)) for x in labs}
+        # a shared order for the bundles keeps folds possible
+        base = list(rng.permutation(labs)) if rng.random() < 0.5 else labs
+        pick = lambda keep: "".join(x for x in base if x in keep)  # noqa: E731
+        labA, labB, labC = pick(set(I + P)), pick(set(P + J)), pick(set(I + J))
+
+        def lay(lab):
+            order = lab if rng.random() < 0.6 else "".join(rng.permutation(list(lab)))
+            acc, st = 1, {}
+            for x in order:
+                st[x] = acc
+                acc *= ext[x]
+            return tuple(ext[x] for x in lab), tuple(st[x] for x in lab)
+
+        compare(labA, lay(labA), labB, lay(labB), labC, lay(labC))
