@@ -20,20 +20,6 @@ Readings (the paper does not say): sorting uses |stride| and is stable in the
 order the labels appear in C (I, J) or A (P); folding merges a pair (x, y)
 whenever s_y(T) == s_x(T) * n_x in both tensors of the bundle, scanning pairs
 in label order and repeating until no pair merges.  The steps move no data.
-
-``normalize(..., gpu_p_order=True)`` adds one step that is not the paper's:
-6. when A's smallest stride lies outside P (A is then read along its rows and
-   the P order does not affect its access) but B's smallest stride lies in P,
-   order P by |stride| in B instead (smallest first), so that B is read along its own unit
-   stride.  Step 5's aim -- stride-1 access for A -- is unaffected.
-``normalize(..., gpu_row_order=True)`` adds a second one:
-7. when B's smallest stride lies in J (B is read along its rows), order J by
-   |stride| in B instead of C (smallest first); likewise I by |stride| in A
-   when A's smallest stride lies in I, but only when k (the product of the P
-   lengths) is at least 512.  C, which step 3 serves, is written once, while
-   A and B are read once per output tile across from them (about k / 128
-   times C's traffic); after step 4 C's unit stride lies in I, so only
-   re-ordering I costs C its unit-stride writes.
 """
 from dataclasses import dataclass, field
 from typing import Dict, List, Tuple
@@ -134,11 +120,10 @@ def _fold(dims: List[Dim]) -> List[Dim]:
     return dims
 
 
-def normalize(A, B, C, gpu_p_order: bool = False, gpu_row_order: bool = False) -> Bundles:
+def normalize(A, B, C) -> Bundles:
     """A, B, C are (labels, lens, strides) triples.  Returns the bundles after
     the five steps of Section 7.3 (names 'A' and 'B' in Dim.s refer to the
-    tensors *after* any swap), plus step 6 above when ``gpu_p_order`` and
-    step 7 when ``gpu_row_order``."""
+    tensors *after* any swap)."""
     I, J, P = _dims(A, B, C)
     # 1. discard length-1 dims
     I = [d for d in I if d.n != 1]
@@ -159,24 +144,4 @@ def normalize(A, B, C, gpu_p_order: bool = False, gpu_row_order: bool = False) -
         P = [Dim(d.labels, d.n, {"A": d.s["B"], "B": d.s["A"]}) for d in P]
     # 5. order P by stride in A
     P = sorted(P, key=lambda d: abs(d.s["A"]))
-    # 6. (not in the paper) let B's unit stride order P when A's lies outside P
-    if gpu_p_order and P:
-        minA_P = min(abs(d.s["A"]) for d in P)
-        minA_I = min((abs(d.s["A"]) for d in I), default=None)
-        minB_P = min(abs(d.s["B"]) for d in P)
-        minB_J = min((abs(d.s["B"]) for d in J), default=None)
-        a_rows = minA_I is not None and minA_I <= minA_P
-        b_k = minB_J is None or minB_P < minB_J
-        if a_rows and b_k:
-            P = sorted(P, key=lambda d: abs(d.s["B"]))
-    # 7. (not in the paper) an operand whose smallest stride lies in its row
-    #    bundle orders that bundle by its own strides (I only when k >= 512)
-    if gpu_row_order:
-        minA_P = min((abs(d.s["A"]) for d in P), default=None)
-        minB_P = min((abs(d.s["B"]) for d in P), default=None)
-        if I and _prod(d.n for d in P) >= 512 and \
-                (minA_P is None or min(abs(d.s["A"]) for d in I) <= minA_P):
-            I = sorted(I, key=lambda d: abs(d.s["A"]))
-        if J and (minB_P is None or min(abs(d.s["B"]) for d in J) <= minB_P):
-            J = sorted(J, key=lambda d: abs(d.s["B"]))
     return Bundles(I, J, P, swapped)

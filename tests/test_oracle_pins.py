@@ -124,8 +124,10 @@ def test_heuristic_jli_example():
 
 
 def test_heuristic_benchmark_example_efcad_bf():
-    # abcde-efcad-bf: A_efcad cannot be packed with stride-1 access because e
-    # has a larger stride than a in C
+    # the contraction abcde <- efcad.bf of the benchmark discussion (Section 9):
+    # step 3 orders I by C's strides, so a (unit stride in C) leads I while e,
+    # A's unit-stride label, comes last -- A is then not read along its own
+    # unit stride, the case that paper discussion uses to explain a slow row
     ext = dict(a=3, b=4, c=5, d=6, e=7, f=8)
     b = bundle.normalize(_cm("efcad", ext), _cm("bf", ext), _cm("abcde", ext))
     assert b.I[0].labels[0] == "a" and b.I[0].s["C"] == 1
