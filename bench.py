@@ -190,12 +190,21 @@ def traffic_for(kernel: str, workload: str):
 
 # ---- workload -------------------------------------------------------------------------
 
+def bundle_lengths(spec):
+    """m, n, k of a workload: the products of the extents of the labels that A
+    and C, B and C, A and B share (Section 4); computed from the labels alone,
+    so that the reference arm never loads the product library."""
+    prod = lambda labs: int(np.prod([spec.ext[x] for x in labs], dtype=np.int64))  # noqa: E731
+    a, b, c = set(spec.labA), set(spec.labB), set(spec.labC)
+    return prod(a & c), prod(b & c), prod(a & b)
+
+
 def workload_config(spec, extra=None):
-    pl = tc.plan_describe(_cm(spec, spec.labA), spec.labA, _cm(spec, spec.labB), spec.labB, _cm(spec, spec.labC), spec.labC)
+    m, n, k = bundle_lengths(spec)
     desc = (f"{spec.name}: {spec.labC} <- {spec.labA}.{spec.labB}, extents "
             + ",".join(f"{k}={v}" for k, v in sorted(spec.ext.items()))
             + f", column-major, alpha={spec.alpha}, beta={spec.beta}, mode={spec.mode}")
-    cfg = {"workload": desc, "m": pl["m"], "n": pl["n"], "k": pl["k"], "mode": spec.mode}
+    cfg = {"workload": desc, "m": m, "n": n, "k": k, "mode": spec.mode}
     if extra:
         cfg.update(extra)
     return cfg

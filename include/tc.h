@@ -198,7 +198,10 @@ TC_API void tc_plan_destroy(tc_plan* plan);
  * block-scatter vectors: the paper's plain scatter-matrix form, kept for
  * comparison.
  * The FP64 mode always uses the BLOCK form.  The setting is process-wide and
- * read when a contraction is issued or a plan is created.  Returns the
+ * read when a contraction is issued or a plan is created; it is not tied to
+ * any thread or stream, so a host thread that changes it while another issues
+ * contractions races with that thread (either setting may apply to a call
+ * issued meanwhile): set it once at start-up, or serialise.  Returns the
  * previous setting, or TC_ERR_ARG for an unknown value. */
 typedef enum { TC_ACCESS_BOX = 0, TC_ACCESS_BLOCK = 1, TC_ACCESS_SCATTER = 2 } tc_access;
 TC_API int tc_set_access(int access);
@@ -212,8 +215,9 @@ TC_API int tc_set_access(int access);
  * TC_REDUCE_F64: each partial widened to FP64, summed and scaled in FP64.
  * Within one tile the tensor core's own FP32 accumulation is summed in
  * float-float chunks of at most 1024 terms in either setting.  Process-wide,
- * read when a contraction is issued or a plan is created.  Returns the
- * previous setting, or TC_ERR_ARG for an unknown value. */
+ * read when a contraction is issued or a plan is created, with the same
+ * caveat as tc_set_access for host threads that change it concurrently.
+ * Returns the previous setting, or TC_ERR_ARG for an unknown value. */
 typedef enum { TC_REDUCE_COMPENSATED = 0, TC_REDUCE_F64 = 1 } tc_reduce;
 TC_API int tc_set_split_reduction(int reduce);
 
