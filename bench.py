@@ -1060,7 +1060,11 @@ def run_ours(args, ws, rank, local):
 
 # ---- the other configurations, on the default line --------------------------------------------
 
-TOL = {"f64": 1e-12, "bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24, "bf16x6": 1e-5}
+# normalised-error bars: FP64 path on FP64 data; on FP32 data the FP64 result
+# is rounded once to FP32 (2^-24 of |C| <= the magnitude); BF16x3's derived
+# bound (two bf16 pieces keep 16 significand bits); BF16x6 the stated 1e-5
+TOL = {"f64": 1e-12, "f64_on_f32": 2.0 ** -24 + 1e-12, "bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24,
+       "bf16x6": 1e-5}
 
 
 def secondary_configs(args, ws, rank, local):
@@ -1089,8 +1093,9 @@ def secondary_configs(args, ws, rank, local):
         r["wall_s"] = round(time.perf_counter() - t0, 1)
         chk = r.get("oracle_check")
         if chk is not None:
-            chk["tolerance"] = TOL[mode]
-            chk["within_tolerance"] = chk["max_normalised_err_vs_oracle"] <= TOL[mode]
+            tol = TOL["f64_on_f32" if mode == "f64" and wl in ("spiky_f32", "grad_f32") else mode]
+            chk["tolerance"] = tol
+            chk["within_tolerance"] = chk["max_normalised_err_vs_oracle"] <= tol
         out[key] = r
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
