@@ -72,7 +72,7 @@ enum {
   TC_ERR_CUDA = -6,           /* a CUDA runtime call failed */
   TC_ERR_DEVICE_TIMEOUT = -7, /* a kernel's bounded wait expired (device error word) */
   TC_ERR_UNSUPPORTED = -8,    /* combination not provided (e.g. BF16X3 on F64 data) */
-  TC_ERR_DEVICE_BOUNDS = -9,  /* a kernel computed an offset outside an operand */
+  TC_ERR_DEVICE_BOUNDS = -9,  /* checked launch: a scatter vector reached outside its operand */
   TC_ERR_SCRATCH_LIMIT = -10  /* tc_contract_noalloc: problem needs more than its fixed scratch */
 };
 
@@ -272,12 +272,36 @@ TC_API int tc_build_scatter(const tc_tensor* A, const tc_tensor* B, const tc_ten
  * capture.  All calls share the one array: calls whose kernels overlap on the
  * GPU (different streams, or different host threads, without ordering between
  * them) race on it and must be serialised by the caller.  Nothing in the array
- * needs to start at zero: each call writes every entry it reads. */
+ * needs to start at zero: each call writes every entry it reads.  The cached
+ * address belongs to the device's current context: after a cudaDeviceReset of
+ * that device the process must not call this entry point on it again (the
+ * library keeps other per-device state the same way).  Device-side faults are
+ * reported through tc_get_device_error like every other call. */
 #define TC_NOALLOC_SCRATCH_BYTES (2u << 20)
 TC_API int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor* A,
                                const tc_tensor* B, double beta, const tc_tensor* C, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------------ */
+
+/* Device-side checks, a debugging mode (the paper has none; it stands in for a
+ * bounds-checking sanitizer).  With on = 1, every contraction issued and every
+ * plan created afterwards (tc_contract, tc_contract_noalloc, tc_plan_create,
+ * tc_contract_batched) adds one launch after the scatter-vector builder that
+ * verifies what every later address rests on: each entry of each scatter
+ * vector (Section 6.1) lies between the least and the largest offset its
+ * bundle's dims reach in the operand (computed on the host from the operand's
+ * own lengths and strides, so rscat + cscat stays inside the operand), and
+ * each block-scatter entry s > 0 (Section 6.2) is the common difference of its
+ * block.  A failure raises the device error word to TC_ERR_DEVICE_BOUNDS
+ * (tc_get_device_error) without a trap; the mainloop, epilogue and reduction
+ * launches of checked work read that word first and do nothing while it holds
+ * the bounds error, so no access outside an operand is made and C is left
+ * untouched.  The word stays set until tc_get_device_error reads and clears
+ * it: until then every checked contraction skips its work.  Process-wide, with
+ * the caveat of tc_set_access; a plan keeps the setting it was created with.
+ * Results are bit-identical with and without checks.  Returns the previous
+ * setting, or TC_ERR_ARG for a value other than 0 or 1. */
+TC_API int tc_set_checks(int on);
 
 /* Synchronise `stream`, read and clear the library's device error word.
  * *code is TC_OK, TC_ERR_DEVICE_TIMEOUT or TC_ERR_DEVICE_BOUNDS. */

@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import TcError  # noqa: F401
 
 __all__ = ["contract", "workspace_size", "plan_describe", "build_scatter", "device_error",
-           "set_access", "access", "box_access", "set_split_reduction", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
+           "set_access", "access", "box_access", "set_split_reduction", "set_checks", "checks", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
 
 _MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3, "bf16x6": L.TC_MODE_BF16X6}
 
@@ -155,6 +155,32 @@ def set_split_reduction(form: str) -> str:
     if prev < 0:
         L.check(prev, "tc_set_split_reduction")
     return {v: k for k, v in _REDUCE.items()}[prev]
+
+
+def set_checks(on: bool) -> bool:
+    """Device-side checks of the scatter vectors every address rests on
+    (tc_set_checks): a failed check makes the contraction do nothing and
+    ``device_error()`` return TC_ERR_DEVICE_BOUNDS.  Process-wide; returns the
+    previous setting."""
+    prev = L.lib().tc_set_checks(1 if on else 0)
+    if prev < 0:
+        L.check(prev, "tc_set_checks")
+    return bool(prev)
+
+
+class checks:
+    """Context manager: ``with checks(True): ...`` restores the previous setting."""
+
+    def __init__(self, on: bool = True):
+        self.on = on
+
+    def __enter__(self):
+        self.prev = set_checks(self.on)
+        return self
+
+    def __exit__(self, *exc):
+        set_checks(self.prev)
+        return False
 
 
 def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):

@@ -58,6 +58,7 @@ SIGNATURES = {
                                     ctypes.POINTER(TcTensor), c_vp]),
     "tc_set_access": (c_i32, [c_i32]),
     "tc_set_split_reduction": (c_i32, [c_i32]),
+    "tc_set_checks": (c_i32, [c_i32]),
     "tc_box_access": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
                       [ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     "tc_set_mainloop_events": (c_i32, [c_vp, c_vp]),

@@ -189,9 +189,16 @@ bool box_encoder_available() { return encoder() != nullptr; }
 namespace tc {
 namespace {
 std::atomic<int> g_reduce{TC_REDUCE_COMPENSATED};
+std::atomic<int> g_checks{0};
 }
 bool split_reduction_f64() { return g_reduce.load() == TC_REDUCE_F64; }
+bool checks_on() { return g_checks.load() != 0; }
 }  // namespace tc
+
+extern "C" int tc_set_checks(int on) {
+  if (on != 0 && on != 1) return TC_ERR_ARG;
+  return tc::g_checks.exchange(on);
+}
 
 extern "C" int tc_set_split_reduction(int reduce) {
   if (reduce != TC_REDUCE_COMPENSATED && reduce != TC_REDUCE_F64) return TC_ERR_ARG;

@@ -145,9 +145,18 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   int64_t* scat = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + w.scatter_off);
   const ScatterOffsets o = scatter_offsets(L, kBsBlock);
   if (launch_build_scatter(L, kBsBlock, scat, s) != cudaSuccess) return TC_ERR_CUDA;
+  // checks on: validate the vectors, and let every later kernel skip its work
+  // once the error word holds a bounds error
+  const int32_t* gate = nullptr;
+  if (checks_on()) {
+    int32_t* e = err_word();
+    if (!e || launch_check_scatter(L, kBsBlock, scat, check_bounds(L), e, s) != cudaSuccess)
+      return TC_ERR_CUDA;
+    gate = e;
+  }
   const ScatterPtrs sp = scatter_ptrs(scat, o);
   if (L.k == 0 || alpha == 0.0)
-    return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+    return launch_scale_c(dt, p.c, sp, L.m, L.n, beta, s, gate) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
   if (mode != TC_MODE_F64) {
     TcLaunch q;
     std::memset(&q, 0, sizeof q);
@@ -173,6 +182,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     q.reduce_f64 = split_reduction_f64() ? 1 : 0;
     q.ctas = sm_count();
     q.err = err_word();
+    q.gate = gate;
     // TC_FAULT=timeout: test hook that makes the kernel's first wait expire
     if (const char* f = std::getenv("TC_FAULT")) q.fault = std::strcmp(f, "timeout") == 0 ? 1 : 0;
     return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
@@ -194,6 +204,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
                               : nullptr;
   f.max_ctas = sm_count();
   f.err = err_word();
+  f.gate = gate;
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
@@ -317,7 +328,11 @@ int tc_get_device_error(void* stream, int32_t* code) {
   if (cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return TC_ERR_CUDA;
   const int32_t zero = 0;
   if (cudaMemcpy(w, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return TC_ERR_CUDA;
-  *code = v == kDevOk ? TC_OK : v == kDevTimeout ? TC_ERR_DEVICE_TIMEOUT : TC_ERR_DEVICE_BOUNDS;
+  // a bounds error outranks a timeout (the check kernels raise the word to it)
+  *code = v == kDevOk        ? TC_OK
+          : v == kDevTimeout ? TC_ERR_DEVICE_TIMEOUT
+          : v == kDevBounds  ? TC_ERR_DEVICE_BOUNDS
+                             : TC_ERR_CUDA;
   return TC_OK;
 }
 

@@ -238,6 +238,8 @@ struct tc_plan {
   int64_t max_m_split = 0, max_n_split = 0;
   int pieces = 2;
   int reduce_f64 = 0;  // the split-reduction setting when the plan was created
+  bool checks = false;  // tc_set_checks was on when the plan was created
+  CheckBounds* d_bounds = nullptr;  // checked plans: per-problem scatter-vector ranges
   int64_t ctas = 152;
   int64_t sms = 152;
 };
@@ -250,6 +252,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->ctas = sms;
   pl->sms = sms;
   pl->reduce_f64 = split_reduction_f64() ? 1 : 0;
+  pl->checks = checks_on();
   pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
   std::vector<double> alpha, beta;
   for (const tc_problem& pr : probs) {
@@ -428,6 +431,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   const size_t o_part = take(es * std::max<int64_t>(1, part_elems));
   const size_t o_tmap = take(sizeof(CUtensorMap) * 2 * std::max(np, 1));
   const size_t o_ctr = take(sizeof(unsigned long long) * kF64BatchClasses);
+  const size_t o_cb = take(pl->checks ? sizeof(CheckBounds) * std::max(np, 1) : 0);
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -442,6 +446,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->d_counter = reinterpret_cast<unsigned long long*>(base + o_ctr);
   pl->d_split = reinterpret_cast<int32_t*>(base + o_split);
   pl->d_split_cols = reinterpret_cast<int64_t*>(base + o_scols);
+  if (pl->checks) pl->d_bounds = reinterpret_cast<CheckBounds*>(base + o_cb);
   std::vector<int64_t> scols(pl->n_split + 1, 0);
   for (int i = 0; i < pl->n_split; ++i) scols[i + 1] = scols[i] + pl->planned[splitp[i]].L.n;
   pl->split_cols = scols[pl->n_split];
@@ -491,6 +496,11 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       !up(pl->d_split_cols, scols.data(), sizeof(int64_t) * scols.size()) ||
       !up(base + o_tmap, maps.data(), sizeof(CUtensorMap) * maps.size()))
     return TC_ERR_CUDA;
+  if (pl->checks) {
+    std::vector<CheckBounds> cb(np);
+    for (int i = 0; i < np; ++i) cb[i] = check_bounds(lay[i]);
+    if (!up(pl->d_bounds, cb.data(), sizeof(CheckBounds) * np)) return TC_ERR_CUDA;
+  }
   return TC_OK;
 }
 
@@ -532,6 +542,15 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
   if (launch_build_scatter_batched(plan->d_layouts, plan->d_offs, np, plan->total_scatter,
                                    kBsBlock, plan->d_scat, s) != cudaSuccess)
     return TC_ERR_CUDA;
+  const int32_t* gate = nullptr;
+  if (plan->checks) {
+    int32_t* ew = err_word();
+    if (!ew || launch_check_scatter_batched(plan->d_layouts, plan->d_offs, plan->d_bounds, np,
+                                            plan->total_scatter, kBsBlock, plan->d_scat, ew,
+                                            s) != cudaSuccess)
+      return TC_ERR_CUDA;
+    gate = ew;
+  }
   cudaError_t e;
   if (plan->mode == TC_MODE_F64) {
     F64BatchLaunch q;
@@ -548,6 +567,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.max_m_split = plan->max_m_split;
     q.max_n_split = plan->max_n_split;
     q.counter = plan->d_counter;
+    q.gate = gate;
     e = launch_f64_batched(q, s);
   } else {
     TcLaunch q;
@@ -567,6 +587,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.max_n_split = plan->max_n_split;
     q.counter = plan->d_counter;
     q.err = err_word();
+    q.gate = gate;
     e = launch_tc(q, s);
   }
   return e == cudaSuccess ? TC_OK : TC_ERR_CUDA;

@@ -49,6 +49,16 @@ using F1 = FT<128, 64>;  // single contractions
 constexpr int BM = F1::BM, BN = F1::BN, NT = F1::NT;
 constexpr size_t kSmem = F1::SMEM;
 
+// Checked launches: the whole CTA skips its work when the device error word
+// (`gate`) holds a bounds error from the scatter-vector check (thread 0 reads
+// it once, so the CTA takes one decision).
+__device__ __forceinline__ bool gate_closed(const int32_t* gate) {
+  __shared__ int s_closed;
+  if (threadIdx.x == 0) s_closed = *gate == kDevBounds;
+  __syncthreads();
+  return s_closed != 0;
+}
+
 __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                : "+d"(d[0]), "+d"(d[1])
@@ -236,8 +246,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT, 1)
     k_f64(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ c, const ScatterPtrs sp,
           const int64_t M, const int64_t N, const int64_t K, const double alpha, const double beta,
-          const int a_kc, const int b_kc, const SkArgs sk) {
+          const int a_kc, const int b_kc, const SkArgs sk, const int32_t* gate) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (gate && gate_closed(gate)) return;
   const F64Smem S = f64_smem<F1>(smem);
   F64Ctx<T> P{a, b, c, sp, M, N, K, alpha, beta, a_kc, b_kc};
   const int64_t Tt = sk.tiles * sk.KT;
@@ -268,11 +279,13 @@ struct FBatch {
 template <typename T, class FBt>
 __global__ void __launch_bounds__(FBt::F::NT, FBt::CTAS_PER_SM)
     k_f64_batched(const DevProblem* __restrict__ probs, const WorkItem* __restrict__ items,
-                  int64_t nitems, unsigned long long* __restrict__ counter) {
+                  int64_t nitems, unsigned long long* __restrict__ counter,
+                  const int32_t* gate) {
   using FB = typename FBt::F;
   constexpr int BM = FB::BM, BN = FB::BN;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t next_w;
+  if (gate && gate_closed(gate)) return;
   const F64Smem S = f64_smem<FB>(smem);
   for (int64_t w = blockIdx.x; w < nitems;) {
     const WorkItem wi = items[w];
@@ -297,7 +310,9 @@ __global__ void __launch_bounds__(FBt::F::NT, FBt::CTAS_PER_SM)
 template <typename T>
 __global__ void k_f64_batched_reduce(const DevProblem* __restrict__ probs,
                                      const int32_t* __restrict__ split_probs,
-                                     const int64_t* __restrict__ col_prefix, int32_t n_split) {
+                                     const int64_t* __restrict__ col_prefix, int32_t n_split,
+                                     const int32_t* __restrict__ gate) {
+  if (gate && *gate == kDevBounds) return;
   const int64_t total = col_prefix[n_split];
   for (int64_t r = blockIdx.y; r < total; r += gridDim.y) {
     int lo = 0, hi = n_split;
@@ -328,7 +343,8 @@ __global__ void k_f64_batched_reduce(const DevProblem* __restrict__ probs,
 template <typename T>
 __global__ void __launch_bounds__(NT)
     k_f64_fixup(T* __restrict__ c, const ScatterPtrs sp, const int64_t M, const int64_t N,
-                const double alpha, const double beta, const SkArgs sk) {
+                const double alpha, const double beta, const SkArgs sk, const int32_t* gate) {
+  if (gate && *gate == kDevBounds) return;
   const int64_t Tt = sk.tiles * sk.KT;
   const int64_t f = blockIdx.x;
   if (f + 1 >= sk.G) return;
@@ -379,10 +395,11 @@ cudaError_t launch_t(const F64Launch& p, cudaStream_t s) {
   mainloop_event_before(s);
   k_f64<T><<<(unsigned)sk.G, NT, kSmem, s>>>((const T*)p.a, (const T*)p.b, (T*)p.c, p.sp, p.m,
                                               p.n, p.k, p.alpha, p.beta, p.a_k_contig,
-                                              p.b_k_contig, sk);
+                                              p.b_k_contig, sk, p.gate);
   note_launch();
   if (sk.G != sk.tiles) {
-    k_f64_fixup<T><<<(unsigned)sk.G, NT, 0, s>>>((T*)p.c, p.sp, p.m, p.n, p.alpha, p.beta, sk);
+    k_f64_fixup<T><<<(unsigned)sk.G, NT, 0, s>>>((T*)p.c, p.sp, p.m, p.n, p.alpha, p.beta, sk,
+                                                 p.gate);
     note_launch();
   }
   mainloop_event_after(s);
@@ -410,7 +427,7 @@ cudaError_t launch_class(const F64BatchLaunch& q, int cls, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.sms * FBt::CTAS_PER_SM, n));
   k_f64_batched<T, FBt><<<(unsigned)grid, F::NT, F::SMEM, s>>>(q.probs, q.items + q.class_off[cls],
-                                                               n, q.counter + cls);
+                                                               n, q.counter + cls, q.gate);
   note_launch();
   return cudaSuccess;
 }
@@ -432,7 +449,8 @@ cudaError_t launch_batched_t(const F64BatchLaunch& q, cudaStream_t s) {
       const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((q.max_m_split + 255) / 256, 16));
       const unsigned by = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q.split_cols, 16384));
       k_f64_batched_reduce<T><<<dim3(bx, by), 256, 0, s>>>(q.probs, q.split_probs,
-                                                           q.split_col_prefix, q.n_split_probs);
+                                                           q.split_col_prefix, q.n_split_probs,
+                                                           q.gate);
       note_launch();
     }
     mainloop_event_after(s);

@@ -25,8 +25,35 @@ struct ScatterPtrs {
 ScatterPtrs scatter_ptrs(const int64_t* base, const ScatterOffsets& o);
 
 // C := beta * C over the m x n matrix view (alpha == 0 or an empty P range).
+// `gate`: see CheckBounds (null when the checks are off).
 cudaError_t launch_scale_c(tc_dtype dt, void* c, const ScatterPtrs& sp, int64_t m, int64_t n,
-                           double beta, cudaStream_t s);
+                           double beta, cudaStream_t s, const int32_t* gate = nullptr);
+
+// ---- device-side checks (tc_set_checks) ----------------------------------------------
+// Every global address the mainloops and the epilogue compute from the scatter
+// vectors is rscat[i] + cscat[j] (Section 6.1); a 16-byte copy at a block the
+// block-scatter vector marks as unit stride reads the four entries of that
+// block (Section 6.2).  With checks on, a check kernel after K1 verifies that
+// every scatter entry lies in its vector's range [lo, hi] -- the least and
+// largest offset its bundle's dims can reach, computed on the host from the
+// operand's own lengths and strides, so that every rscat + cscat stays inside
+// the operand -- and that every block-scatter entry s > 0 is the common
+// difference of its block's entries.  A failure sets kDevBounds in the device
+// error word (never a trap); every later kernel of a checked launch reads that
+// word (its `gate`) first and does nothing when it holds kDevBounds, so no
+// access outside an operand is made.
+struct CheckBounds {
+  int64_t lo[6], hi[6];  // per scatter vector, in the order rA cA rB cB rC cC
+};
+bool checks_on();      // the process-wide setting of tc_set_checks
+CheckBounds check_bounds(const Layout& L);  // also applies the TC_CHECK_SHRINK test hook
+cudaError_t launch_check_scatter(const Layout& L, int32_t b, const int64_t* scat,
+                                 const CheckBounds& cb, int32_t* err, cudaStream_t s);
+// A batch: problem p's bounds in cbs[p] (device).
+cudaError_t launch_check_scatter_batched(const Layout* layouts, const int64_t* offsets,
+                                         const CheckBounds* cbs, int32_t count, int64_t total,
+                                         int32_t b, const int64_t* scat, int32_t* err,
+                                         cudaStream_t s);
 
 // K2 + K5 (f64.cu): FP64 mainloop with the fused scattered alpha/beta epilogue.
 struct F64Launch {
@@ -41,6 +68,7 @@ struct F64Launch {
   double* partial;   // stream-K partial tiles (f64_partial_bytes(max_ctas)), or null
   int64_t max_ctas;  // CTAs for stream-K (one per SM); ignored without `partial`
   int32_t* err;
+  const int32_t* gate = nullptr;  // checked launch: skip all work if *gate == kDevBounds
 };
 cudaError_t launch_f64(const F64Launch& p, cudaStream_t s);
 int64_t f64_grid(int64_t m, int64_t n, int64_t k, int64_t max_ctas, bool can_split);
@@ -137,6 +165,7 @@ struct TcLaunch {
   int32_t* err;
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path
+  const int32_t* gate;  // checked launch: skip all work if *gate == kDevBounds (or null)
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
 
@@ -155,6 +184,7 @@ struct F64BatchLaunch {
   int32_t n_split_probs;
   int64_t max_m_split, max_n_split;
   unsigned long long* counter;  // device work counters, one per tile class
+  const int32_t* gate = nullptr;  // checked launch: skip all work if *gate == kDevBounds
 };
 cudaError_t launch_f64_batched(const F64BatchLaunch& q, cudaStream_t s);
 

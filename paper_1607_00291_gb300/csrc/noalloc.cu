@@ -10,6 +10,7 @@
 // routine it calls.
 #include <mutex>
 
+#include "host_common.h"
 #include "kernels.h"
 
 namespace tc {
@@ -70,9 +71,19 @@ extern "C" int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor
   // Every entry the kernels read below is written by the scatter builder
   // first, in stream order, so nothing in the array has to start at zero.
   if (launch_build_scatter(L, kBsBlock, scat, s) != cudaSuccess) return TC_ERR_CUDA;
+  // the library's device error word (a static array too: no allocation)
+  int32_t* ew = err_word();
+  if (!ew) return TC_ERR_CUDA;
+  const int32_t* gate = nullptr;
+  if (checks_on()) {
+    if (launch_check_scatter(L, kBsBlock, scat, check_bounds(L), ew, s) != cudaSuccess)
+      return TC_ERR_CUDA;
+    gate = ew;
+  }
   const ScatterPtrs sp = scatter_ptrs(scat, o);
   if (L.k == 0 || alpha == 0.0)
-    return launch_scale_c(dtype, p.c, sp, L.m, L.n, beta, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+    return launch_scale_c(dtype, p.c, sp, L.m, L.n, beta, s, gate) == cudaSuccess ? TC_OK
+                                                                                  : TC_ERR_CUDA;
   F64Launch f;
   f.dtype = dtype;
   f.a = p.a;
@@ -88,6 +99,7 @@ extern "C" int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor
   f.b_k_contig = p.info.b_k_contig;
   f.partial = nullptr;  // plain tiling only: no stream-K partials in the fixed array
   f.max_ctas = 0;
-  f.err = nullptr;
+  f.err = ew;
+  f.gate = gate;
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

@@ -11,6 +11,8 @@
 //
 // GPU form: one thread per output entry; each block-scatter entry recomputes
 // the scatter values of its own block, so the kernel needs no second pass.
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace tc {
@@ -98,9 +100,58 @@ __global__ void k_build_scatter_batched(const Layout* __restrict__ layouts,
   }
 }
 
+// ---- checks: entry t of one problem's vectors against its vector's range,
+// block-scatter entries against the differences of their block -------------
+__device__ __forceinline__ bool entry_ok(const Layout& L, const ScatterOffsets& o, int32_t b,
+                                         const CheckBounds& cb, const int64_t* v, int64_t t) {
+  const int64_t starts[13] = {o.rA,   o.cA,   o.rB,   o.cB,   o.rC,   o.cC,   o.rbsA,
+                              o.cbsA, o.rbsB, o.cbsB, o.rbsC, o.cbsC, o.total};
+  int sec = 0;
+  while (sec < 11 && t >= starts[sec + 1]) ++sec;
+  if (sec < 6) return v[t] >= cb.lo[sec] && v[t] <= cb.hi[sec];
+  const int vs = sec - 6;  // the scatter vector this block-scatter vector describes
+  const int64_t len = starts[vs + 1] - starts[vs];
+  const int64_t lo = (t - starts[sec]) * b, hi = lo + b < len ? lo + b : len;
+  const int64_t st = v[t];
+  if (st < 0) return false;
+  if (st == 0) return true;  // no claim: the kernels gather this block element by element
+  const int64_t* sv = v + starts[vs];
+  for (int64_t j = lo + 1; j < hi; ++j)
+    if (sv[j] - sv[j - 1] != st) return false;
+  return true;
+}
+
+__global__ void k_check_scatter(const Layout L, const int32_t b, const ScatterOffsets o,
+                                const CheckBounds cb, const int64_t* __restrict__ v,
+                                int32_t* __restrict__ err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < o.total;
+       t += (int64_t)gridDim.x * blockDim.x)
+    if (!entry_ok(L, o, b, cb, v, t)) atomicMax(err, kDevBounds);
+}
+
+__global__ void k_check_scatter_batched(const Layout* __restrict__ layouts,
+                                        const int64_t* __restrict__ offsets,
+                                        const CheckBounds* __restrict__ cbs, int32_t count,
+                                        int64_t total, int32_t b, const int64_t* __restrict__ v,
+                                        int32_t* __restrict__ err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= t) lo = mid; else hi = mid;
+    }
+    const Layout& L = layouts[lo];
+    if (!entry_ok(L, scatter_offsets(L, b), b, cbs[lo], v + offsets[lo], t - offsets[lo]))
+      atomicMax(err, kDevBounds);
+  }
+}
+
 template <typename T>
 __global__ void k_scale_c(T* __restrict__ c, const int64_t* __restrict__ rC,
-                          const int64_t* __restrict__ cC, int64_t m, int64_t n, double beta) {
+                          const int64_t* __restrict__ cC, int64_t m, int64_t n, double beta,
+                          const int32_t* __restrict__ gate) {
+  if (gate && *gate == kDevBounds) return;
   const int64_t total = m * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -151,14 +202,67 @@ cudaError_t launch_build_scatter_batched(const Layout* layouts, const int64_t* o
 }
 
 cudaError_t launch_scale_c(tc_dtype dt, void* c, const ScatterPtrs& sp, int64_t m, int64_t n,
-                           double beta, cudaStream_t s) {
+                           double beta, cudaStream_t s, const int32_t* gate) {
   if (beta == 1.0 || m == 0 || n == 0) return cudaSuccess;
   int64_t blocks = (m * n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (dt == TC_F64)
-    k_scale_c<double><<<(int)blocks, 256, 0, s>>>((double*)c, sp.rC, sp.cC, m, n, beta);
+    k_scale_c<double><<<(int)blocks, 256, 0, s>>>((double*)c, sp.rC, sp.cC, m, n, beta, gate);
   else
-    k_scale_c<float><<<(int)blocks, 256, 0, s>>>((float*)c, sp.rC, sp.cC, m, n, beta);
+    k_scale_c<float><<<(int)blocks, 256, 0, s>>>((float*)c, sp.rC, sp.cC, m, n, beta, gate);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Least and largest entry of each scatter vector: over the bundle's dims,
+// sum of (len - 1) * stride where negative, resp. positive -- the range of
+// offsets the dims can reach in the operand (the vectors of one operand add
+// up to the operand's whole span; folded dims reach what their parts reach).
+CheckBounds check_bounds(const Layout& L) {
+  CheckBounds cb;
+  const Bundle* bs[6] = {&L.I, &L.P, &L.P, &L.J, &L.I, &L.J};
+  const bool first[6] = {true, true, false, true, false, false};  // s0 or s1
+  for (int v = 0; v < 6; ++v) {
+    int64_t lo = 0, hi = 0;
+    for (int d = 0; d < bs[v]->nd; ++d) {
+      const int64_t reach = (bs[v]->len[d] - 1) * (first[v] ? bs[v]->s0[d] : bs[v]->s1[d]);
+      if (reach < 0) lo += reach; else hi += reach;
+    }
+    cb.lo[v] = lo;
+    cb.hi[v] = hi;
+  }
+  // TC_CHECK_SHRINK=v (0..5): test hook that hands the checker a range one
+  // element short at the top for vector v (the operands stay whole), so that
+  // the check fires without any access outside an operand
+  if (const char* e = std::getenv("TC_CHECK_SHRINK")) {
+    const int v = std::atoi(e);
+    if (e[0] >= '0' && e[0] <= '5' && e[1] == 0) cb.hi[v] -= 1;
+  }
+  return cb;
+}
+
+cudaError_t launch_check_scatter(const Layout& L, int32_t b, const int64_t* scat,
+                                 const CheckBounds& cb, int32_t* err, cudaStream_t s) {
+  const ScatterOffsets o = scatter_offsets(L, b);
+  if (o.total == 0) return cudaSuccess;
+  if (!err) return cudaErrorInvalidValue;
+  int64_t blocks = (o.total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_check_scatter<<<(int)blocks, 256, 0, s>>>(L, b, o, cb, scat, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_scatter_batched(const Layout* layouts, const int64_t* offsets,
+                                         const CheckBounds* cbs, int32_t count, int64_t total,
+                                         int32_t b, const int64_t* scat, int32_t* err,
+                                         cudaStream_t s) {
+  if (total == 0 || count == 0) return cudaSuccess;
+  if (!err) return cudaErrorInvalidValue;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  k_check_scatter_batched<<<(int)blocks, 256, 0, s>>>(layouts, offsets, cbs, count, total, b,
+                                                      scat, err);
   note_launch();
   return cudaGetLastError();
 }

@@ -155,6 +155,7 @@ struct Args {
   int32_t* err;
   int fault;  // 1: injected timeout (see TcLaunch::fault)
   unsigned long long* counter;  // batch: the shared work counter (dynamic items), or null
+  const int32_t* gate;  // checked launch: no work if *gate == kDevBounds (or null)
 };
 
 __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err) {
@@ -470,7 +471,9 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       mbar_init(&wq_full[q], 1);
       mbar_init(&wq_empty[q], NWQ);
     }
-    *abort = 0;
+    // a checked launch whose scatter-vector check failed starts aborted: every
+    // role leaves its loop at once, nothing is loaded or stored
+    *abort = (a.gate && *a.gate == kDevBounds) ? 2 : 0;
     *sProb = a.single;
     fence_mbar_init();
   }
@@ -978,7 +981,8 @@ __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int6
 template <bool F64>
 __global__ void k_reduce_partials(const DevProblem single, const DevProblem* probs,
                                   const int32_t* split_probs, const int64_t* col_prefix,
-                                  int32_t n_split) {
+                                  int32_t n_split, const int32_t* gate) {
+  if (gate && *gate == kDevBounds) return;
   if (!probs) {
     reduce_one<F64>(single, 0, single.n);
     return;
@@ -1015,6 +1019,7 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   a.err = q.err;
   a.fault = q.fault;
   a.counter = q.probs && !BOX ? q.counter : nullptr;
+  a.gate = q.gate;
   if (q.probs) {
     a.nitems = q.nitems;
     a.tiles_single = 1;
@@ -1040,11 +1045,13 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
     if (q.reduce_f64)
       k_reduce_partials<true><<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
                                                            q.split_col_prefix,
-                                                           single_split ? 0 : q.n_split_probs);
+                                                           single_split ? 0 : q.n_split_probs,
+                                                           q.gate);
     else
       k_reduce_partials<false><<<dim3(bx, by), 256, 0, s>>>(q.single, q.probs, q.split_probs,
                                                             q.split_col_prefix,
-                                                            single_split ? 0 : q.n_split_probs);
+                                                            single_split ? 0 : q.n_split_probs,
+                                                            q.gate);
     note_launch();
   }
   mainloop_event_after(s);

@@ -27,7 +27,8 @@ def noalloc(alpha, A, lA, B, lB, beta, C, lC):
     d = [L.make_tensor(tuple(t.shape), t.stride(), lab, t.data_ptr(), keep)
          for t, lab in ((A, lA), (B, lB), (C, lC))]
     s = torch.cuda.current_stream()
-    return L.lib().tc_contract_noalloc(L.TC_F64, float(alpha), d[0], d[1], float(beta), d[2],
+    dt = L.TC_F64 if C.dtype == torch.float64 else L.TC_F32
+    return L.lib().tc_contract_noalloc(dt, float(alpha), d[0], d[1], float(beta), d[2],
                                        L.c_vp(s.cuda_stream))
 
 
@@ -46,12 +47,37 @@ def test_noalloc_matches_tc_contract_two_calls_in_a_row():
         tc.contract(A, lA, B, lB, ref_C, lC, alpha=alpha, beta=beta)
         torch.cuda.synchronize()
         ref = ref_C.cpu().numpy()
-        _, mag = oracle_ref(alpha, h["A"], lA, h["B"], lB, beta, h["C"], lC)
+        oref, mag = oracle_ref(alpha, h["A"], lA, h["B"], lB, beta, h["C"], lC)
         for _ in range(2):
             C = to_device(h["C"])
             assert noalloc(alpha, A, lA, B, lB, beta, C, lC) == 0
             torch.cuda.synchronize()
-            assert norm_err(C.cpu().numpy(), ref, mag) <= TOL_F64
+            assert tc.device_error() == 0
+            got = C.cpu().numpy()
+            assert norm_err(got, ref, mag) <= TOL_F64   # against the ordinary entry point
+            assert norm_err(got, oref, mag) <= TOL_F64  # and against the oracle itself
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.75, 1.25), (0.0, 0.5)])
+def test_noalloc_f32_data_and_alpha_zero_against_the_oracle(alpha, beta):
+    # FP32 data widened to FP64 (one FP32 rounding of the result), and
+    # alpha == 0, where only C := beta * C runs (A and B are not read)
+    rng = np.random.default_rng(78)
+    p = W.random_problem(rng, ext=(3, 30), max_elems=1 << 18, max_flops=2.0 ** 27)
+    h = W.make_random_inputs(p, seed=78, dtype=torch.float32)
+    for dt, tol in ((torch.float32, TOL_F64 + 2.0 ** -24), (torch.float64, TOL_F64)):
+        A, B = to_device(h["A"], dt), to_device(h["B"], dt)
+        oref, mag = oracle_ref(alpha, h["A"], p.labA, h["B"], p.labB, beta, h["C"], p.labC)
+        ref_C = to_device(h["C"], dt)
+        tc.contract(A, p.labA, B, p.labB, ref_C, p.labC, alpha=alpha, beta=beta)
+        for _ in range(2):
+            C = to_device(h["C"], dt)
+            assert noalloc(alpha, A, p.labA, B, p.labB, beta, C, p.labC) == 0
+            torch.cuda.synchronize()
+            assert tc.device_error() == 0
+            got = C.cpu().double().numpy()
+            assert norm_err(got, oref, mag) <= tol
+            assert norm_err(got, ref_C.cpu().double().numpy(), mag) <= tol
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
