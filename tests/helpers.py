@@ -55,3 +55,45 @@ def raw_contract(dtype_code, mode_code, alpha, A, beta, C, B, ws=None):
                              L.c_vp(ws.data_ptr()), n.value, L.c_vp(s.cuda_stream))
     torch.cuda.synchronize()
     return rc
+
+
+def matrix_view_offsets(pl, which="C"):
+    """rscat and cscat of C (Section 6.1) from a plan description: the offsets
+    of C's rows (I bundle) and columns (J bundle) in the planner's matrix view,
+    built by the oracle's scatter routine."""
+    r = oracle.scatter([d["n"] for d in pl["I"]], [d["s"][1] for d in pl["I"]])
+    c = oracle.scatter([d["n"] for d in pl["J"]], [d["s"][1] for d in pl["J"]])
+    return r, c
+
+
+def tile_offsets(rC, cC, m0, n0, bm, bn):
+    """C offsets of the output tile rows m0..m0+bm-1, columns n0..n0+bn-1 of
+    the matrix view (clipped at its edges)."""
+    r = rC[m0:m0 + bm]
+    c = cC[n0:n0 + bn]
+    return (r[:, None] + c[None, :]).ravel()
+
+
+def oracle_at(alpha, hA, lA, hB, lB, beta, hC0, lC, offsets):
+    """Oracle values and magnitudes at the given offsets of a column-major
+    (colexicographically dense) C, whose offsets are its colexicographic
+    positions: each run of consecutive offsets is one window of the oracle.
+    An element reads only its own old value of C, so all windows share one
+    copy of C.  The magnitudes |alpha| sum|A||B| + |beta||C| are the same
+    oracle contraction on absolute values (the products' absolute values are
+    exact), so no full-size magnitude array is made per window."""
+    a = np.asarray(hA, dtype=np.float64)
+    b = np.asarray(hB, dtype=np.float64)
+    c0 = np.asarray(hC0, dtype=np.float64)
+    offs = np.unique(np.asarray(offsets, dtype=np.int64))
+    c = np.array(c0, copy=True)
+    cm = np.abs(c0)
+    aa, ba = np.abs(a), np.abs(b)
+    breaks = np.flatnonzero(np.diff(offs) != 1) + 1
+    starts = np.concatenate([[0], breaks]).astype(np.int64)
+    ends = np.concatenate([breaks, [offs.size]]).astype(np.int64)
+    for s0, e0 in zip(starts, ends):
+        lo, hi = int(offs[s0]), int(offs[e0 - 1]) + 1
+        oracle.contract_(alpha, a, lA, b, lB, beta, c, lC, mag=False, begin=lo, end=hi)
+        oracle.contract_(abs(alpha), aa, lA, ba, lB, abs(beta), cm, lC, mag=False, begin=lo, end=hi)
+    return offs, c.ravel(order="F")[offs], cm.ravel(order="F")[offs]

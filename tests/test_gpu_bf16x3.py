@@ -18,7 +18,7 @@ import oracle
 import paper_1607_00291_gb300 as tc
 from paper_1607_00291_gb300 import workloads as W
 
-from helpers import norm_err, oracle_ref, to_device
+from helpers import matrix_view_offsets, norm_err, oracle_at, oracle_ref, tile_offsets, to_device
 
 pytestmark = pytest.mark.gpu
 TOLS = {"bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24, "bf16x6": 1e-5}
@@ -182,6 +182,18 @@ def sampled_check(spec, seed, mode, ranges=4, width=400):
                                begin=int(start), end=int(start) + width)
         sel = slice(int(start), int(start) + width)
         worst = max(worst, norm_err(got[sel], c.ravel(order="F")[sel], mag.ravel(order="F")[sel]))
+    # whole output tiles of the matrix view (128 rows x the tile width): the
+    # first, the last (ragged where m or n is not a multiple of the tile), and
+    # four seeded ones
+    pl = tc.plan_describe(dA, spec.labA, dB, spec.labB, dC, spec.labC)
+    rC, cC = matrix_view_offsets(pl)
+    bn = min(128, (pl["n"] + 15) // 16 * 16)
+    tm, tn = (pl["m"] + 127) // 128, (pl["n"] + bn - 1) // bn
+    picks = [(0, 0), (tm - 1, tn - 1)] + [(int(rng.integers(tm)), int(rng.integers(tn))) for _ in range(4)]
+    offs = np.concatenate([tile_offsets(rC, cC, i * 128, j * bn, 128, bn) for i, j in picks])
+    o, ref, mag = oracle_at(spec.alpha, a, spec.labA, b, spec.labB, spec.beta, h["C"].numpy(),
+                            spec.labC, offs)
+    worst = max(worst, norm_err(got[o], ref, mag))
     assert worst <= TOLS[mode], worst
     return worst
 

@@ -10,7 +10,8 @@ import paper_1607_00291_gb300 as tc
 from paper_1607_00291_gb300 import _lib as L
 from paper_1607_00291_gb300 import workloads as W
 
-from helpers import norm_err, oracle_ref, raw_contract, to_device
+from helpers import (matrix_view_offsets, norm_err, oracle_at, oracle_ref, raw_contract,
+                     tile_offsets, to_device)
 
 pytestmark = pytest.mark.gpu
 TOL_F64 = 1e-12
@@ -213,3 +214,19 @@ def test_cc4x4_full_size_sampled():
         sel = slice(int(start), int(start) + 600)
         e = norm_err(got[sel], c.ravel(order="F")[sel], mag.ravel(order="F")[sel])
         assert e <= TOL_F64, e
+    # every output of every tile that the stream-K schedule cuts (128 x 64
+    # tiles; the (tile, k-tile) iterations dealt evenly over one CTA per SM):
+    # those tiles are finished by the fix-up kernel from FP64 partials
+    pl = tc.plan_describe(dA, s.labA, dB, s.labB, dC, s.labC)
+    rC, cC = matrix_view_offsets(pl)
+    m, nn, k = pl["m"], pl["n"], pl["k"]
+    tiles_n = (nn + 63) // 64
+    tiles, KT = ((m + 127) // 128) * tiles_n, (k + 15) // 16
+    G = min(torch.cuda.get_device_properties(0).multi_processor_count, tiles * KT // 4)
+    cut = sorted({(c * tiles * KT // G) // KT for c in range(1, G) if (c * tiles * KT // G) % KT})
+    assert len(cut) > 100  # the schedule cuts tiles on this workload
+    offs = np.concatenate([tile_offsets(rC, cC, (t // tiles_n) * 128, (t % tiles_n) * 64, 128, 64)
+                           for t in cut])
+    o, ref, mag = oracle_at(s.alpha, a, s.labA, b, s.labB, s.beta, h["C"].numpy(), s.labC, offs)
+    e = norm_err(got[o], ref, mag)
+    assert e <= TOL_F64, e
