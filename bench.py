@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cc4x4_f64",
-                    choices=sorted(W.SPECS) + ["batch512"] + sorted(W.PAPER_SHAPES))
+                    choices=sorted(W.SPECS) + ["batch512", "tccg"] + sorted(W.PAPER_SHAPES))
     ap.add_argument("--mode", choices=["f64", "bf16x3", "bf16x6"], default=None,
                     help="override the workload's arithmetic")
     ap.add_argument("--access", choices=["box", "block", "scatter"], default="box",
@@ -303,8 +303,8 @@ def ttgt_contract(A, labA, B, labB, C, labC, alpha, beta, gemm=torch.matmul):
 
 def time_ttgt(problems, warm: int, K: int, flops: float, ws: int, gemm=torch.matmul):
     """Device time of the TTGT form of one step (all `problems`), with the
-    temporaries' bytes; FP32 GEMMs in full FP32 (no TF32) unless `gemm` says
-    otherwise."""
+    temporaries' bytes and the time of each problem; FP32 GEMMs in full FP32
+    (no TF32) unless `gemm` says otherwise."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
@@ -312,18 +312,20 @@ def time_ttgt(problems, warm: int, K: int, flops: float, ws: int, gemm=torch.mat
         for _ in range(warm):
             extra = sum(ttgt_contract(*p, gemm=gemm) for p in problems)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(K):
-            for p in problems:
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(problems) + 1)] for _ in range(K)]
+        for i in range(K):
+            for j, p in enumerate(problems):
+                ev[i][j].record()
                 ttgt_contract(*p, gemm=gemm)
-        e1.record()
+            ev[i][-1].record()
         torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
+        ms = max_over_ranks(float(np.mean([row[0].elapsed_time(row[-1]) for row in ev])), ws)
+        per = [round(float(np.mean([row[j].elapsed_time(row[j + 1]) for row in ev])), 4)
+               for j in range(len(problems))]
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     return {"value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
-            "ms_per_step": round(ms, 4), "temporary_bytes": int(extra),
+            "ms_per_step": round(ms, 4), "ms_per_problem": per, "temporary_bytes": int(extra),
             "what": "torch permute().contiguous() + torch.matmul (cuBLAS, FP64 or full FP32) + "
                     "strided copy back, same inputs, device time"}
 
@@ -625,14 +627,19 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
     clocks.start()
     time.sleep(0.3)
     launches0 = lib.tc_launch_count()
+    cev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(K)]
     e0.record()
     for i in range(K):
-        for (c, w), (ka, kb) in zip(zip(calls, works), kev[i]):
+        for j, ((c, w), (ka, kb)) in enumerate(zip(zip(calls, works), kev[i])):
+            cev[i][j].record()
             lib.tc_set_mainloop_events(L.c_vp(ka.cuda_event), L.c_vp(kb.cuda_event))
             tc.contract(c[0], c[1], c[2], c[3], c[4], c[5], alpha=c[6], beta=c[7], mode=mode, workspace=w)
+        cev[i][-1].record()
     e1.record()
     torch.cuda.synchronize()
     launches = lib.tc_launch_count() - launches0
+    call_ms = [round(float(np.mean([row[j].elapsed_time(row[j + 1]) for row in cev])), 4)
+               for j in range(len(calls))]
     clk = clocks.stop()
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1) / K, ws)
@@ -692,6 +699,7 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
         kname = "k_f64" if mode == "f64" else "k_tc"
         line["roofline"].update({"kernel": kname, "kernel_ms": round(kms, 4), "kernel_ms_per_call": per_call,
                                  "traffic": traffic_for(kname, getattr(args, "traffic_key", ""))})
+        line["call_ms"] = call_ms
         if check:
             line["oracle_check"] = check
         return line
@@ -711,17 +719,19 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
         for t, o in zip(outputs, outs):
             o.copy_(t, non_blocking=True)
 
-    for _ in range(warm):
+    # many gigabytes per step (the benchmark strings): fewer end-to-end steps
+    ew, ek = (1, min(K, 3)) if bi + bo > 4e9 else (warm, K)
+    for _ in range(ew):
         e2e_step()
     torch.cuda.synchronize()
     barrier(ws)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
-    for _ in range(K):
+    for _ in range(ek):
         e2e_step()
     f1.record()
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / K, ws)
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / ek, ws)
 
     prods = 1 if mode == "f64" else (3 if mode == "bf16x3" else 6)
     kname = "k_f64" if mode == "f64" else "k_tc"
@@ -750,6 +760,7 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
     cfg = {"workload": desc}
     cfg.update(cfg_extra)
     cfg["parallelism"] = f"replicas x{ws}"
+    roof["call_ms"] = call_ms
     line = {
         "metric": METRIC, "value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
         "n_gpus": ws, "steps": K, "warmup": warm, "ms_per_step": round(ms, 4), "higher_is_better": True,
@@ -823,6 +834,62 @@ def run_paper(args, ws, rank, local):
                      flops=flops, mode=mode, desc=desc, cfg_extra=extra, cpu=(spec0, host[0], 0))
 
 
+# The paper's BSMTC on one Haswell core for the benchmark strings (GFLOP/s,
+# Section 9.3's benchmark figure, single-core panel), in the order of
+# W.TCCG_STRINGS: context only -- the paper's extents are not known here, and
+# the hardware is a CPU core.
+PAPER_BSMTC_1CORE_GFLOPS = [3.67, 3.63, 2.32, 2.03, 6.77, 6.34, 17.25, 21.99, 20.68, 20.69, 17.33,
+                            19.84, 27.52, 27.85, 23.32, 28.51, 27.85, 25.62, 36.45, 37.37, 42.57,
+                            40.70, 41.75, 40.32]
+
+
+def run_tccg(args, ws, rank, local):
+    """The Tensor Contraction Benchmark's 24 contraction strings (Section 9.3)
+    with synthetic extents (every index of a contraction the same extent, about
+    2^34 flops each; column-major; uniform[-1,1], drawn on the device from a
+    seed); one step = the 24 tc_contract calls.  Per string: our time, the
+    TTGT form's time and the ratio, beside the paper's single-core BSMTC rate."""
+    mode = args.mode or "f64"
+    lean = getattr(args, "lean", False)
+    dt = torch.float64 if mode == "f64" else torch.float32
+    probs = W.tccg_problems()
+    dev = [W.make_random_inputs_on(p, seed=2000 + i, dtype=dt, device="cuda") for i, p in enumerate(probs)]
+    calls = [(d["A"], p.labA, d["B"], p.labB, d["C"], p.labC, 1.0, 0.0) for p, d in zip(probs, dev)]
+    flops = sum(p.flops() for p in probs)
+    desc = (f"tccg: the 24 contraction strings of the paper's Tensor Contraction Benchmark figure "
+            f"(C-A-B), synthetic extents (one extent per contraction, e = round((2^33)^(1/L)) for "
+            f"L indices: about 2^34 flops each), column-major, uniform[-1,1]; mode={mode}")
+    extra = {"strings": W.TCCG_STRINGS, "extents": [p.ext[p.labC[0]] for p in probs],
+             "l2": "operands larger than L2 in most strings", "mode": mode}
+    host = lambda i: {k: v.cpu().double() for k, v in dev[i].items()}  # noqa: E731
+    checks = None
+    if lean:
+        # every third string (eight of them, both ends of the figure included)
+        checks = []
+        for i in range(0, len(probs), 3):
+            h = host(i)
+            checks.append((i, h["A"].numpy(), h["B"].numpy(), np.zeros(tuple(dev[i]["C"].shape), order="F")))
+    p0 = probs[0]
+    spec0 = W.Spec("tccg", p0.labA, p0.labB, p0.labC, dict(p0.ext), dt, 1.0, 0.0)
+    line = run_calls(args, ws, rank, local, calls=calls,
+                     inputs=[t for c in calls for t in (c[0], c[2], c[4])], outputs=[c[4] for c in calls],
+                     flops=flops, mode=mode, desc=desc, cfg_extra=extra,
+                     cpu=None if lean else (spec0, host(0), 0), checks=checks)
+    call_ms = line.get("call_ms") or line["roofline"].get("call_ms")
+    tt = (line.get("ttgt") or {}).get("ms_per_problem")
+    rows = []
+    for i, (s_, p) in enumerate(zip(W.TCCG_STRINGS, probs)):
+        r = {"string": s_, "extent": p.ext[p.labC[0]], "ms": call_ms[i],
+             "tflops": round(p.flops() / (call_ms[i] * 1e-3) / 1e12, 4),
+             "paper_bsmtc_1core_gflops": PAPER_BSMTC_1CORE_GFLOPS[i]}
+        if tt:
+            r["ttgt_ms"] = tt[i]
+            r["ttgt_time_over_ours"] = round(tt[i] / call_ms[i], 3)
+        rows.append(r)
+    line["per_string"] = rows
+    return line
+
+
 def run_grad(args, ws, rank, local):
     """The gradient workload forward and backward (autograd's three
     contractions): C = A.B, dA = dC . B over J, dB = A . dC over I, each a
@@ -865,6 +932,8 @@ def run_grad(args, ws, rank, local):
 def run_ours(args, ws, rank, local):
     if args.workload == "batch512":
         return run_batch(args, ws, rank, local)
+    if args.workload == "tccg":
+        return run_tccg(args, ws, rank, local)
     if args.workload in W.PAPER_SHAPES:
         return run_paper(args, ws, rank, local)
     if args.workload == "grad_f32":
@@ -1076,7 +1145,8 @@ def secondary_configs(args, ws, rank, local):
     out = {}
     runs = [("spiky_f32_bf16x3", "spiky_f32", "bf16x3"), ("spiky_f32_bf16x6", "spiky_f32", "bf16x6"),
             ("spiky_f32_f64", "spiky_f32", "f64"), ("grad_f32_bf16x3", "grad_f32", "bf16x3"),
-            ("batch512_bf16x3", "batch512", "bf16x3"), ("batch512_f64", "batch512", "f64")]
+            ("batch512_bf16x3", "batch512", "bf16x3"), ("batch512_f64", "batch512", "f64"),
+            ("tccg_bf16x3", "tccg", "bf16x3"), ("tccg_f64", "tccg", "f64")]
     for key, wl, mode in runs:
         a = copy.copy(args)
         a.workload, a.mode, a.lean = wl, mode, True
@@ -1094,6 +1164,8 @@ def secondary_configs(args, ws, rank, local):
         chk = r.get("oracle_check")
         if chk is not None:
             tol = TOL["f64_on_f32" if mode == "f64" and wl in ("spiky_f32", "grad_f32") else mode]
+            if mode != "f64" and wl == "tccg":
+                tol = TOL[mode]
             chk["tolerance"] = tol
             chk["within_tolerance"] = chk["max_normalised_err_vs_oracle"] <= tol
         out[key] = r

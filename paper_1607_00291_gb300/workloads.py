@@ -164,6 +164,19 @@ def dense_permuted(flat: torch.Tensor, labels: str, order: str, ext: Dict[str, i
     return base.permute(*perm)
 
 
+def make_random_inputs_on(p: RandomProblem, seed: int, dtype, device):
+    """As make_random_inputs with uniform[-1, 1] values, drawn on `device`
+    from its own seeded generator (large workloads: no host round trip).
+    Returns tensors of `dtype` on the device."""
+    g = torch.Generator(device=device).manual_seed(seed)
+    out = {}
+    for name, lab, order in (("A", p.labA, p.orderA), ("B", p.labB, p.orderB), ("C", p.labC, p.orderC)):
+        n = int(np.prod([p.ext[x] for x in lab])) if lab else 1
+        flat = (torch.rand(n, generator=g, dtype=torch.float64, device=device) * 2 - 1).to(dtype)
+        out[name] = dense_permuted(flat, lab, order or lab, p.ext)
+    return out
+
+
 def make_random_inputs(p: RandomProblem, seed: int, dtype=torch.float64, dist: str = "uniform"):
     g = torch.Generator().manual_seed(seed)
     out = {}
@@ -245,3 +258,36 @@ def paper_problems(name: str) -> List[RandomProblem]:
     s = PAPER_SHAPES[name]
     rng = np.random.default_rng(s["seed"])
     return [shaped_problem(rng, s["m"], s["n"], s["k"]) for _ in range(s["count"])]
+
+
+# ---- the Tensor Contraction Benchmark's contraction strings (Section 9.3) ------------
+# The 24 contractions the paper runs from the Tensor Contraction Benchmark, as
+# printed on its benchmark figure: index strings C-A-B ("abc-adec-ebd" is
+# C_abc := A_adec B_ebd), from the communication-bound to the compute-bound
+# end.  The paper gives no extents and no data.  Synthetic stand-ins: every
+# index of a contraction gets the same extent e, the integer nearest to
+# (F / 2)^(1 / L) for L distinct indices, so that each contraction performs
+# about F flops (2 e^L); the label structure alone then decides the matrix
+# shape (a lone contracted index makes a rank-k-like update, two indices per
+# bundle a square-like product).  Every tensor is column-major in its own
+# label order (the first index has stride 1); values uniform[-1, 1].
+TCCG_STRINGS = [
+    "abcde-efbad-cf", "abcde-efcad-bf", "abcd-dbea-ec", "abcde-ecbfa-fd", "abcd-deca-be",
+    "abc-bda-dc", "abcd-ebad-ce", "abcdef-dega-gfbc", "abcdef-dfgb-geac", "abcdef-degb-gfac",
+    "abcdef-degc-gfab", "abc-dca-bd", "abcd-ea-ebcd", "abcd-eb-aecd", "abcd-ec-abed",
+    "abc-adec-ebd", "ab-cad-dcb", "ab-acd-dbc", "abc-acd-db", "abc-adc-bd", "ab-ac-cb",
+    "abcd-aebf-fdec", "abcd-eafd-fbec", "abcd-aebf-dfce",
+]
+
+
+def tccg_problem(index_string: str, flops: float = 2.0 ** 34) -> RandomProblem:
+    """One contraction of the benchmark's strings with the synthetic extents
+    described above (column-major storage in each tensor's label order)."""
+    labC, labA, labB = index_string.split("-")
+    labels = sorted(set(labA + labB + labC))
+    e = max(2, int(round((flops / 2.0) ** (1.0 / len(labels)))))
+    return RandomProblem(labA, labB, labC, {x: e for x in labels}, labA, labB, labC)
+
+
+def tccg_problems(flops: float = 2.0 ** 34) -> List[RandomProblem]:
+    return [tccg_problem(s, flops) for s in TCCG_STRINGS]

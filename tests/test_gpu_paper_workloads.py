@@ -78,3 +78,50 @@ def test_ttgt_comparison_form_matches_oracle(dt):
         assert norm_err(dC.cpu().double().numpy(), ref, mag) <= tol
         es = dA.element_size()
         assert extra == (dA.numel() + dB.numel() + dC.numel()) * es
+
+
+@pytest.mark.parametrize("mode", sorted(TOLS))
+def test_benchmark_strings_small_every_element(mode):
+    # the 24 contraction strings of the paper's benchmark figure, every index
+    # of a contraction the same small extent (about 2^18 flops each), every
+    # output element against the oracle
+    dt = torch.float64 if mode == "f64" else torch.float32
+    for i, p in enumerate(W.tccg_problems(2.0 ** 18)):
+        h = W.make_random_inputs(p, seed=900 + i, dtype=dt)
+        dA, dB, dC = (to_device(h[x], dt) for x in "ABC")
+        tc.contract(dA, p.labA, dB, p.labB, dC, p.labC, alpha=0.5, beta=-1.0, mode=mode)
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
+        ref, mag = oracle_ref(0.5, h["A"], p.labA, h["B"], p.labB, -1.0, h["C"], p.labC)
+        assert norm_err(dC.cpu().double().numpy(), ref, mag) <= TOLS[mode], W.TCCG_STRINGS[i]
+
+
+@pytest.mark.parametrize("mode", sorted(TOLS))
+def test_benchmark_strings_full_size_sampled(mode):
+    # the benchmark workload of bench.py (about 2^34 flops per string, inputs
+    # drawn on the device from the same seeds): per string, whole output tiles
+    # of the matrix view (first, last, one seeded) and the first and last
+    # output elements against the oracle
+    from helpers import matrix_view_offsets, oracle_at, tile_offsets
+    dt = torch.float64 if mode == "f64" else torch.float32
+    rng = np.random.default_rng(11)
+    for i, p in enumerate(W.tccg_problems()):
+        d = W.make_random_inputs_on(p, seed=2000 + i, dtype=dt, device="cuda")
+        dC = torch.zeros_like(d["C"])
+        tc.contract(d["A"], p.labA, d["B"], p.labB, dC, p.labC, mode=mode)
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
+        got = dC.cpu().double().numpy().ravel(order="F")
+        a, b = d["A"].cpu().double().numpy(), d["B"].cpu().double().numpy()
+        pl = tc.plan_describe(d["A"], p.labA, d["B"], p.labB, dC, p.labC)
+        rC, cC = matrix_view_offsets(pl)
+        bm, bn = (128, 64) if mode == "f64" else (128, min(128, (pl["n"] + 15) // 16 * 16))
+        tm, tn = (pl["m"] + bm - 1) // bm, (pl["n"] + bn - 1) // bn
+        picks = [(0, 0), (tm - 1, tn - 1), (int(rng.integers(tm)), int(rng.integers(tn)))]
+        offs = np.concatenate([tile_offsets(rC, cC, r * bm, c * bn, bm, bn) for r, c in picks] +
+                              [np.arange(min(256, got.size)), np.arange(max(0, got.size - 256), got.size)])
+        zeros = np.zeros(tuple(dC.shape), order="F")
+        o, ref, mag = oracle_at(1.0, a, p.labA, b, p.labB, 0.0, zeros, p.labC, offs)
+        assert norm_err(got[o], ref, mag) <= TOLS[mode], W.TCCG_STRINGS[i]
+        del d, dC, a, b
+        torch.cuda.empty_cache()

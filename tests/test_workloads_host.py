@@ -49,3 +49,22 @@ def test_paper_problem_sets_are_seeded():
         a, b = W.paper_problems(name), W.paper_problems(name)
         assert [(p.labA, p.labB, p.labC, p.ext) for p in a] == [(p.labA, p.labB, p.labC, p.ext) for p in b]
         assert len(a) == W.PAPER_SHAPES[name]["count"]
+
+
+def test_benchmark_strings_parse_and_follow_the_extent_rule():
+    import oracle.bundle as ob
+    assert len(W.TCCG_STRINGS) == 24
+    for s in W.TCCG_STRINGS:
+        p = W.tccg_problem(s)
+        labC, labA, labB = s.split("-")
+        assert (p.labA, p.labB, p.labC) == (labA, labB, labC)
+        I, J, P = ob.classify(labA, labB, labC)  # each label in exactly two tensors
+        assert I and J and P
+        L = len(set(labA + labB + labC))
+        e = p.ext[labC[0]]
+        assert set(p.ext.values()) == {e}
+        # the integer extent nearest to (2^33)^(1/L): about 2^34 flops
+        assert abs(e - 2 ** (33 / L)) <= 0.5
+        assert 0.5 * 2 ** 34 < p.flops() < 2 * 2 ** 34
+    # the small form of the same rule
+    assert all(W.tccg_problem(s, 2.0 ** 16).flops() < 2 ** 18 for s in W.TCCG_STRINGS)
