@@ -165,14 +165,29 @@ TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, cons
                         void* workspace, size_t ws_bytes, void* stream);
 
 /* Plan form for repeated batches: tc_plan_create validates and plans every
- * problem, chooses tiles (from the autotune table), and copies the
- * descriptors into a device buffer that the plan owns (cudaMalloc at create,
- * cudaFree at destroy).  tc_plan_execute only enqueues work -- kernels and
+ * problem, chooses tiles and k-splits, and copies the descriptors into a
+ * device buffer that the plan owns (cudaMalloc at create, cudaFree at
+ * destroy).  Autotuning (on with TC_AUTOTUNE=1, or whenever the environment
+ * names a cache file in TC_AUTOTUNE_CACHE, unless TC_AUTOTUNE=0): per shape
+ * class (rounded log2 of m, n, k and the access flags) the output tile is
+ * chosen by timing the candidates on one SM's worth of CTAs, and per batch the
+ * balance divisor D of the k-split rule by timing the whole batch with each of
+ * 2, 4, 8 and 16; the timed runs write scratch copies of the outputs (the
+ * caller's C is not touched) and their results are kept for the process and
+ * in the cache file.  Untuned: least-padding FP64 tiles, tensor-core tiles
+ * covering n, D = 4.  tc_plan_execute only enqueues work -- kernels and
  * the memset of the work counters -- with no host synchronisation and no
  * allocation, so it can be captured in a CUDA graph. */
 TC_API int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
                    tc_plan** out);
 TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);
+/* What the plan chose for the caller's problem `index` (0-based, as passed to
+ * tc_plan_create): out[0] = tile rows, out[1] = tile columns, out[2] = pieces
+ * of its contracted range (k-splits), out[3] = the balance divisor D of the
+ * batch (a problem is split along k until no work item exceeds 1/D of a CTA's
+ * fair share).  A problem with an empty output gets zeros in out[0..2].
+ * Host only.  TC_ERR_ARG for a null pointer or an index out of range. */
+TC_API int tc_plan_config(const tc_plan* plan, int32_t index, int32_t* out);
 TC_API int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream);
 TC_API void tc_plan_destroy(tc_plan* plan);
 

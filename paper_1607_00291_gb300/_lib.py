@@ -49,6 +49,7 @@ SIGNATURES = {
     "tc_contract_batched": (c_i32, [c_i32, c_i32, c_i32, ctypes.POINTER(TcProblem), c_vp, c_sz, c_vp]),
     "tc_plan_create": (c_i32, [c_i32, c_i32, c_i32, ctypes.POINTER(TcProblem), ctypes.POINTER(c_vp)]),
     "tc_plan_workspace_size": (c_i32, [c_vp, ctypes.POINTER(c_sz)]),
+    "tc_plan_config": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i32)]),
     "tc_plan_execute": (c_i32, [c_vp, c_vp, c_sz, c_vp]),
     "tc_plan_destroy": (None, [c_vp]),
     "tc_scatter_count": (c_i32, [ctypes.POINTER(TcTensor)] * 3 + [c_i32, ctypes.POINTER(c_i64)]),

@@ -1,9 +1,9 @@
 """Batches of contractions: one persistent launch over many problems.
 
 ``Plan`` wraps tc_plan_create / tc_plan_execute / tc_plan_destroy: the plan is
-built once (validation, layouts, tile and split choice -- from the autotuner
-when the environment has TC_AUTOTUNE=1 -- and a device copy of every
-descriptor), and ``execute`` only launches kernels on the current stream, so it
+built once (validation, layouts, tile and split choice -- timed by the
+autotuner when the environment has TC_AUTOTUNE=1 or names a cache file in
+TC_AUTOTUNE_CACHE -- and a device copy of every descriptor), and ``execute`` only launches kernels on the current stream, so it
 can be captured in a CUDA graph.  ``contract_batched`` is the one-shot form.
 """
 import torch
@@ -57,6 +57,13 @@ class Plan:
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
             L.check(L.lib().tc_plan_execute(self._plan, None, 0, L.c_vp(s.cuda_stream)),
                     "tc_plan_execute")
+
+    def config(self, index: int) -> dict:
+        """What the plan chose for problem `index`: tile rows and columns, the
+        number of k-splits, and the batch's balance divisor (tc_plan_config)."""
+        out = (L.c_i32 * 4)()
+        L.check(L.lib().tc_plan_config(self._plan, int(index), out), "tc_plan_config")
+        return {"bm": out[0], "bn": out[1], "splits": out[2], "balance": out[3]}
 
     def close(self):
         if getattr(self, "_plan", None):

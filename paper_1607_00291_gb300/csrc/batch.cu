@@ -15,6 +15,7 @@
 // the reduction -- no host synchronisation and no allocation, so it can be
 // captured in a CUDA graph.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -41,27 +42,42 @@ struct ProbCfg {
 };
 
 // ---- K7: autotuner ------------------------------------------------------------------------
-// Shape class: mode, rounded log2 of m, n, k, and the two access flags.
-// Candidates (tensor-core path): tile widths around n.  Each is timed on the
-// first problem of its class in the batch running on ONE persistent CTA --
-// in a batch the other problems keep the other SMs busy, so the SM-time a
-// problem costs is what the choice should minimise -- writing into a scratch
-// copy of that problem's output (the caller's C is never touched).  The
-// fastest is kept for the rest of the process (and in the file named by
-// TC_AUTOTUNE_CACHE, when set).
+// Two decisions of a batch plan are timed rather than estimated.
+//  (1) Per shape class -- mode, rounded log2 of m, n and k, the two access
+//      flags -- the output tile: on the tensor cores the tile width (the one
+//      covering n up to 128, and half of it); on the FP64 path the tile class
+//      (64 x 64, 32 x 64, 64 x 32).  Each candidate runs the class's first
+//      problem of the batch on one SM's worth of CTAs (one persistent CTA;
+//      on the FP64 path the class's CTAs per SM) into a scratch copy of its
+//      output; the least time wins: in a batch the other problems keep the
+//      other SMs busy, so the SM-time a problem costs is what to minimise.
+//  (2) Per batch -- a signature of its problems' shapes and layout classes --
+//      the split of long contracted ranges: a problem is split along k until
+//      no work item exceeds 1/D of a CTA's (FP64: a warp's) fair share of the
+//      batch, and D is chosen among 2, 4, 8 and 16 by running the whole batch
+//      with each into scratch outputs (CUDA events, best of two).  A split's
+//      benefit is balance across the SMs, which only the whole batch shows.
+// Results are kept for the process and, when TC_AUTOTUNE_CACHE names a file,
+// read from it and written back (one record per line).  Tuning is on when
+// TC_AUTOTUNE=1, or when TC_AUTOTUNE_CACHE is set and TC_AUTOTUNE is not 0;
+// otherwise the plan uses the estimates (least padding, D = 4).  Tile timing
+// of one plan stops after about two seconds (the remaining classes keep the
+// estimate and are tuned by a later plan).
 struct TuneKey {
   int mode, lm, ln, lk, akc, bkc;
   bool operator<(const TuneKey& o) const {
     return std::memcmp(this, &o, sizeof o) < 0;
   }
 };
-struct TuneVal {
-  int bn, split_mult;
-};
 
 std::mutex g_tune_mu;
-std::map<TuneKey, TuneVal> g_tune;
+std::map<TuneKey, int> g_tile;          // tensor cores: tile width; FP64: tile class
+std::map<uint64_t, int> g_balance;      // batch signature -> D
 bool g_tune_loaded = false;
+std::string g_tune_path;  // the cache file the tables were read from ("" for none)
+constexpr double kTileTuneBudgetMs = 2000.0;
+constexpr int kBalanceCandidates[] = {2, 4, 8, 16};
+constexpr int kBalanceDefault = 4;
 
 int ilog2r(int64_t x) { return x <= 1 ? 0 : (int)std::lround(std::log2((double)x)); }
 
@@ -77,19 +93,57 @@ TuneKey tune_key(tc_mode mode, const Planned& p) {
   return k;
 }
 
+// FNV-1a over the mode and, per problem, m, n, k and the access flags.
+uint64_t batch_signature(tc_mode mode, const std::vector<Planned>& ps) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  mix((int64_t)mode);
+  mix((int64_t)ps.size());
+  for (const Planned& p : ps) {
+    mix(p.L.m);
+    mix(p.L.n);
+    mix(p.L.k);
+    mix(p.info.a_k_contig * 2 + p.info.b_k_contig);
+  }
+  return h;
+}
+
+bool tile_record_ok(int mode, int v) {
+  if (mode == TC_MODE_F64) return v >= 0 && v < kF64BatchClasses;
+  return v >= 16 && v <= tc_bn_max() && v % 16 == 0;
+}
+
+// The tables belong to one cache file: when TC_AUTOTUNE_CACHE names another
+// file (or none) than the one loaded, they are emptied and read again.
 void tune_load_file() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
   const char* path = std::getenv("TC_AUTOTUNE_CACHE");
+  const std::string now = path ? path : "";
+  if (g_tune_loaded && now == g_tune_path) return;
+  g_tune_loaded = true;
+  g_tune_path = now;
+  g_tile.clear();
+  g_balance.clear();
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  TuneKey k;
-  TuneVal v;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.mode, &k.lm, &k.ln, &k.lk, &k.akc, &k.bkc,
-                     &v.bn, &v.split_mult) == 8) {
-    if (v.bn >= 16 && v.bn <= 256 && v.bn % 16 == 0 && v.split_mult >= 1 && v.split_mult <= 8)
-      g_tune[k] = v;  // a corrupt line is skipped; a malformed file stops the read
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    TuneKey k;
+    std::memset(&k, 0, sizeof k);
+    int v = 0;
+    unsigned long long sig = 0;
+    if (std::sscanf(line, "tile %d %d %d %d %d %d %d", &k.mode, &k.lm, &k.ln, &k.lk, &k.akc, &k.bkc,
+                    &v) == 7) {
+      if (tile_record_ok(k.mode, v)) g_tile[k] = v;  // a corrupt record is skipped
+    } else if (std::sscanf(line, "balance %llx %d", &sig, &v) == 2) {
+      for (int c : kBalanceCandidates)
+        if (c == v) g_balance[(uint64_t)sig] = v;
+    }
   }
   std::fclose(f);
 }
@@ -99,31 +153,117 @@ void tune_save_file() {
   if (!path) return;
   FILE* f = std::fopen(path, "w");
   if (!f) return;
-  for (const auto& kv : g_tune)
-    std::fprintf(f, "%d %d %d %d %d %d %d %d\n", kv.first.mode, kv.first.lm, kv.first.ln,
-                 kv.first.lk, kv.first.akc, kv.first.bkc, kv.second.bn, kv.second.split_mult);
+  for (const auto& kv : g_tile)
+    std::fprintf(f, "tile %d %d %d %d %d %d %d\n", kv.first.mode, kv.first.lm, kv.first.ln,
+                 kv.first.lk, kv.first.akc, kv.first.bkc, kv.second);
+  for (const auto& kv : g_balance)
+    std::fprintf(f, "balance %llx %d\n", (unsigned long long)kv.first, kv.second);
   std::fclose(f);
 }
 
 bool autotune_enabled() {
   const char* e = std::getenv("TC_AUTOTUNE");
-  return e && e[0] == '1';
+  if (e && e[0] == '1') return true;
+  if (e && e[0] == '0') return false;
+  return std::getenv("TC_AUTOTUNE_CACHE") != nullptr;
 }
 
-// Time one tensor-core configuration of problem p on scratch buffers.
-float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, int bn, int sm,
-                     int64_t* scat, float* partial, void* cscratch, int64_t c_off, cudaStream_t st) {
+// [lo, hi] element offsets of C's span (relative to its data pointer).
+void c_span(const tc_plan_info& in, int64_t* lo, int64_t* hi) {
+  int64_t cmin = 0, cmax = 0;
+  for (int i = 0; i < in.nI; ++i) {
+    const int64_t e = (in.I_len[i] - 1) * in.I_sC[i];
+    if (e < 0) cmin += e; else cmax += e;
+  }
+  for (int j = 0; j < in.nJ; ++j) {
+    const int64_t e = (in.J_len[j] - 1) * in.J_sC[j];
+    if (e < 0) cmin += e; else cmax += e;
+  }
+  *lo = cmin;
+  *hi = cmax;
+}
+
+// Best of two timed runs (after one untimed) of `launch` on stream st.
+template <class F>
+float time_best(cudaStream_t st, F launch) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 1e30f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return 1e30f;
+  }
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(e0, st);
+    if (!launch()) {
+      best = 1e30f;
+      break;
+    }
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      best = 1e30f;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// Scratch for timing one problem: its scatter vectors and a zeroed copy of
+// C's span (the caller's C is never touched).
+struct TuneScratch {
+  int64_t* scat = nullptr;
+  void* c = nullptr;
+  void* partial = nullptr;
+  void* dev = nullptr;  // FP64: descriptor, items, counter
+  int64_t c_off = 0;    // element offset of C's data pointer inside `c`
+  cudaStream_t st = nullptr;
+  bool ok = false;
+  ~TuneScratch() {
+    if (st) cudaStreamDestroy(st);
+    cudaFree(scat);
+    cudaFree(c);
+    cudaFree(partial);
+    cudaFree(dev);
+    cudaGetLastError();
+  }
+};
+
+bool make_scratch(const Planned& p, size_t es, size_t partial_bytes, size_t dev_bytes,
+                  TuneScratch& t) {
+  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
+  int64_t lo, hi;
+  c_span(p.info, &lo, &hi);
+  const size_t cbytes = (size_t)(hi - lo + 1) * es;
+  t.c_off = -lo;
+  t.ok = cudaMalloc(&t.scat, (size_t)std::max<int64_t>(1, o.total) * 8) == cudaSuccess &&
+         cudaMalloc(&t.c, cbytes) == cudaSuccess && cudaMemset(t.c, 0, cbytes) == cudaSuccess &&
+         (partial_bytes == 0 || cudaMalloc(&t.partial, partial_bytes) == cudaSuccess) &&
+         (dev_bytes == 0 || cudaMalloc(&t.dev, dev_bytes) == cudaSuccess) &&
+         cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking) == cudaSuccess &&
+         launch_build_scatter(p.L, kBsBlock, t.scat, t.st) == cudaSuccess;
+  if (!t.ok) cudaGetLastError();
+  return t.ok;
+}
+
+// Tensor cores: time tile width bn for problem p on one persistent CTA.
+float time_tc_width(const Planned& p, tc_mode mode, double alpha, double beta, int bn,
+                    TuneScratch& t) {
   const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
-  const TcChoice c = choose_tc(p.L, pieces, 1, bn, sm);
+  const TcChoice c = choose_tc(p.L, pieces, 1, bn, 1);
   const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
   TcLaunch q;
   std::memset(&q, 0, sizeof q);
   DevProblem& d = q.single;
   d.a = p.a;
   d.b = p.b;
-  d.c = static_cast<float*>(cscratch) + c_off;
-  d.partial = c.splits > 1 ? partial : nullptr;
-  d.sp = scatter_ptrs(scat, o);
+  d.c = static_cast<float*>(t.c) + t.c_off;
+  d.partial = c.splits > 1 ? t.partial : nullptr;
+  d.sp = scatter_ptrs(t.scat, o);
   d.m = p.L.m;
   d.n = p.L.n;
   d.k = p.L.k;
@@ -139,29 +279,86 @@ float time_tc_config(const Planned& p, tc_mode mode, double alpha, double beta, 
   q.pieces = pieces;
   q.ctas = 1;
   q.err = err_word();
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  for (int r = 0; r < 4; ++r) {
-    cudaEventRecord(e0, st);
-    if (launch_tc(q, st) != cudaSuccess) {
-      best = 1e30f;
-      break;
-    }
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (r > 0) best = std::min(best, ms);  // first run warms up
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return best;
+  return time_best(t.st, [&] { return launch_tc(q, t.st) == cudaSuccess; });
 }
 
-TuneVal tune_tc(const Planned& p, tc_mode mode, double alpha, double beta) {
-  const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+// FP64: time tile class cls for problem p on one SM's worth of its CTAs.
+float time_f64_class(const Planned& p, tc_dtype dt, double alpha, double beta, int cls,
+                     TuneScratch& t) {
+  int bm, bn;
+  f64_batch_tile(cls, &bm, &bn);
+  const int64_t tiles = ((p.L.m + bm - 1) / bm) * ((p.L.n + bn - 1) / bn);
+  DevProblem d;
+  std::memset(&d, 0, sizeof d);
+  d.a = p.a;
+  d.b = p.b;
+  d.c = static_cast<char*>(t.c) + t.c_off * (int64_t)elem_size(dt);
+  d.sp = scatter_ptrs(t.scat, scatter_offsets(p.L, kBsBlock));
+  d.m = p.L.m;
+  d.n = p.L.n;
+  d.k = p.L.k;
+  d.alpha = alpha;
+  d.beta = beta;
+  d.a_kc = p.info.a_k_contig;
+  d.b_kc = p.info.b_k_contig;
+  d.bn = bn;
+  d.tiles_n = (int32_t)((p.L.n + bn - 1) / bn);
+  d.splits = 1;
+  d.kps = std::max<int64_t>(1, (p.L.k + f64_tile_k() - 1) / f64_tile_k()) * f64_tile_k();
+  std::vector<WorkItem> items((size_t)tiles);
+  for (int64_t i = 0; i < tiles; ++i) items[(size_t)i] = WorkItem{0, (int32_t)i, 0, 0};
+  char* base = static_cast<char*>(t.dev);
+  DevProblem* dprob = reinterpret_cast<DevProblem*>(base);
+  WorkItem* ditems = reinterpret_cast<WorkItem*>(base + align_up(sizeof(DevProblem), 256));
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(
+      base + align_up(sizeof(DevProblem), 256) + align_up(sizeof(WorkItem) * items.size(), 256));
+  if (cudaMemcpy(dprob, &d, sizeof d, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ditems, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return 1e30f;
+  F64BatchLaunch q;
+  q.dtype = dt;
+  q.probs = dprob;
+  q.items = ditems;
+  q.nitems = tiles;
+  for (int c = 0; c <= kF64BatchClasses; ++c) q.class_off[c] = c <= cls ? 0 : tiles;
+  q.sms = 1;
+  q.split_probs = nullptr;
+  q.split_col_prefix = nullptr;
+  q.split_cols = 0;
+  q.n_split_probs = 0;
+  q.max_m_split = q.max_n_split = 0;
+  q.counter = ctr;
+  return time_best(t.st, [&] { return launch_f64_batched(q, t.st) == cudaSuccess; });
+}
+
+size_t f64_tune_dev_bytes(const Planned& p) {
+  int64_t most = 0;
+  for (int c = 0; c < kF64BatchClasses; ++c) {
+    int bm, bn;
+    f64_batch_tile(c, &bm, &bn);
+    most = std::max<int64_t>(most, ((p.L.m + bm - 1) / bm) * ((p.L.n + bn - 1) / bn));
+  }
+  return align_up(sizeof(DevProblem), 256) + align_up(sizeof(WorkItem) * (size_t)most, 256) +
+         align_up(sizeof(unsigned long long) * kF64BatchClasses, 256);
+}
+
+// The timed tile choice for one problem (-1: keep the estimate).
+int tune_tile(const Planned& p, tc_dtype dt, tc_mode mode, double alpha, double beta) {
+  TuneScratch t;
+  if (mode == TC_MODE_F64) {
+    if (!make_scratch(p, elem_size(dt), 0, f64_tune_dev_bytes(p), t)) return -1;
+    int best = -1;
+    float tb = 1e30f;
+    for (int c = 0; c < kF64BatchClasses; ++c) {
+      const float ms = time_f64_class(p, dt, alpha, beta, c, t);
+      if (ms < tb) {
+        tb = ms;
+        best = c;
+      }
+    }
+    return best;
+  }
   std::vector<int> bns;
   if (p.L.n < 128) {
     const int b0 = (int)std::max<int64_t>(16, (p.L.n + 15) / 16 * 16);
@@ -171,45 +368,20 @@ TuneVal tune_tc(const Planned& p, tc_mode mode, double alpha, double beta) {
     bns.push_back(128);
     bns.push_back(64);
   }
-  // scratch: scatter vectors, partials for the largest split, a copy of C's span
-  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
+  const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
   int64_t max_split = 1;
   for (int bn : bns) max_split = std::max<int64_t>(max_split, choose_tc(p.L, pieces, 1, bn, 1).splits);
-  int64_t cmin = 0, cmax = 0;
-  for (int i = 0; i < p.info.nI; ++i) {
-    const int64_t e = (p.info.I_len[i] - 1) * p.info.I_sC[i];
-    if (e < 0) cmin += e; else cmax += e;
-  }
-  for (int j = 0; j < p.info.nJ; ++j) {
-    const int64_t e = (p.info.J_len[j] - 1) * p.info.J_sC[j];
-    if (e < 0) cmin += e; else cmax += e;
-  }
-  const size_t cbytes = (size_t)(cmax - cmin + 1) * sizeof(float);
-  int64_t* scat = nullptr;
-  float* partial = nullptr;
-  void* cs = nullptr;
-  TuneVal best{bns[0], 1};
-  cudaStream_t st = nullptr;
-  if (cudaMalloc(&scat, (size_t)o.total * 8) != cudaSuccess ||
-      cudaMalloc(&partial, (size_t)max_split * p.L.m * p.L.n * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&cs, cbytes) != cudaSuccess || cudaMemset(cs, 0, cbytes) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-  } else if (launch_build_scatter(p.L, kBsBlock, scat, st) == cudaSuccess) {
-    float tbest = 1e30f;
-    for (int bn : bns) {
-      const float t = time_tc_config(p, mode, alpha, beta, bn, 1, scat, partial, cs, -cmin, st);
-      if (t < tbest) {
-        tbest = t;
-        best = TuneVal{bn, 1};
-      }
+  const size_t pbytes = max_split > 1 ? (size_t)max_split * p.L.m * p.L.n * sizeof(float) : 0;
+  if (!make_scratch(p, sizeof(float), pbytes, 0, t)) return -1;
+  int best = -1;
+  float tb = 1e30f;
+  for (int bn : bns) {
+    const float ms = time_tc_width(p, mode, alpha, beta, bn, t);
+    if (ms < tb) {
+      tb = ms;
+      best = bn;
     }
   }
-  if (st) cudaStreamDestroy(st);
-  cudaFree(scat);
-  cudaFree(partial);
-  cudaFree(cs);
-  cudaGetLastError();
   return best;
 }
 
@@ -239,6 +411,9 @@ struct tc_plan {
   int pieces = 2;
   int reduce_f64 = 0;  // the split-reduction setting when the plan was created
   bool checks = false;  // tc_set_checks was on when the plan was created
+  int balance = kBalanceDefault;   // D of the k-split rule (see the autotuner)
+  std::vector<int32_t> orig;       // the caller's index of each planned problem
+  int32_t count = 0;               // problems the caller passed
   CheckBounds* d_bounds = nullptr;  // checked plans: per-problem scatter-vector ranges
   int64_t ctas = 152;
   int64_t sms = 152;
@@ -246,8 +421,10 @@ struct tc_plan {
 
 namespace {
 
-int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
+int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   const int sms = sm_count();
+  pl->balance = balance;
+  pl->count = (int32_t)probs.size();
   const bool f64 = pl->mode == TC_MODE_F64;
   pl->ctas = sms;
   pl->sms = sms;
@@ -255,16 +432,42 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   pl->checks = checks_on();
   pl->pieces = pl->mode == TC_MODE_BF16X6 ? 3 : 2;
   std::vector<double> alpha, beta;
-  for (const tc_problem& pr : probs) {
+  for (size_t q = 0; q < probs.size(); ++q) {
+    const tc_problem& pr = probs[q];
     Planned p;
     int rc = plan_checked(pl->dtype, &pr.A, &pr.B, &pr.C, &p);
     if (rc != TC_OK) return rc;
     if (p.L.m == 0 || p.L.n == 0) continue;  // empty output: nothing to do
     if (pr.alpha == 0.0) p.L.k = 0;          // C := beta * C, A and B not read
     pl->planned.push_back(p);
+    pl->orig.push_back((int32_t)q);
     alpha.push_back(pr.alpha);
     beta.push_back(pr.beta);
   }
+  // the autotuner's tile records (see K7), timed here for classes without one
+  const bool tune = autotune_enabled();
+  double tune_ms = 0.0;
+  auto tuned_tile = [&](int i) -> int {
+    if (!tune || pl->planned[i].L.k == 0) return -1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_file();
+    const TuneKey key = tune_key(pl->mode, pl->planned[i]);
+    auto it = g_tile.find(key);
+    if (it != g_tile.end()) return it->second;
+    if (tune_ms > kTileTuneBudgetMs) return -1;
+    const Layout& L = pl->planned[i].L;
+    // one SM runs the whole problem: skip those too large to time that way
+    const double flops = 2.0 * (double)L.m * (double)L.n * (double)L.k;
+    if (flops > (f64 ? 0x1p27 : 0x1p34)) return -1;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int v = tune_tile(pl->planned[i], pl->dtype, pl->mode, alpha[i], beta[i]);
+    tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (v >= 0) {
+      g_tile[key] = v;
+      tune_save_file();
+    }
+    return v;
+  };
   const int np = (int)pl->planned.size();
   pl->cfg.resize(np);
 
@@ -276,7 +479,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     const Layout& L = pl->planned[i].L;
     ProbCfg& c = pl->cfg[i];
     if (f64) {
-      // the tile class that pads the problem least (ties: the larger tile)
+      // the timed tile class, else the one that pads the problem least (ties:
+      // the larger tile)
       double best = 0;
       for (int cl = 0; cl < kF64BatchClasses; ++cl) {
         int bm, bn;
@@ -289,30 +493,20 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
           c.bn = bn;
         }
       }
+      const int tv = tuned_tile(i);
+      if (tv >= 0) {
+        c.cls = tv;
+        f64_batch_tile(tv, &c.bm, &c.bn);
+      }
       c.tiles = ((L.m + c.bm - 1) / c.bm) * ((L.n + c.bn - 1) / c.bn);
       // in warp x k-tile units (a warp computes 32 x 32)
       cost[i] = (double)c.tiles * (c.bm / 32) * (c.bn / 32) *
                 std::max<int64_t>(1, (L.k + tk_f - 1) / tk_f);
     } else {
-      TuneVal tv{0, 1};
-      // tuning times one CTA: skip problems too large to time quickly that way
-      const double sm_work = (double)((L.m + 127) / 128) * ((L.n + 127) / 128) * ((L.k + 31) / 32);
-      if (autotune_enabled() && L.k > 0 && sm_work <= 4096) {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        tune_load_file();
-        const TuneKey key = tune_key(pl->mode, pl->planned[i]);
-        auto it = g_tune.find(key);
-        if (it == g_tune.end()) {
-          tv = tune_tc(pl->planned[i], pl->mode, alpha[i], beta[i]);
-          g_tune[key] = tv;
-          tune_save_file();
-        } else {
-          tv = it->second;
-        }
-      }
+      const int tv = tuned_tile(i);
       // in a batch the other problems keep the SMs busy: no parallelism split
       // here (long items are split below, for balance)
-      const TcChoice ch = choose_tc(L, pl->pieces, 1, tv.bn, tv.split_mult);
+      const TcChoice ch = choose_tc(L, pl->pieces, 1, tv > 0 ? tv : 0, 1);
       c.bn = ch.bn;
       c.splits = ch.splits;
       c.kps = ch.kps;
@@ -321,9 +515,10 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
     }
     total_cost += cost[i];
   }
-  // Split long-k problems so that no item exceeds a quarter of a CTA's fair
-  // share of the batch (in k-tiles: 16 on the FP64 path, 32 on the tensor
-  // cores).
+  // Split long-k problems so that no item exceeds 1/D of a CTA's fair share
+  // of the batch (in k-tiles: 16 on the FP64 path, 32 on the tensor cores;
+  // D = `balance`, 4 unless the autotuner chose another).
+  const double D = (double)balance;
   if (!f64) {
     const double fair = total_cost / (double)sms;
     for (int i = 0; i < np; ++i) {
@@ -332,8 +527,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       const int64_t KT = (L.k + 31) / 32;
       if (KT == 0) continue;
       const double item = (double)KT / c.splits;
-      if (item <= std::max(8.0, fair / 4.0)) continue;
-      int64_t s = (int64_t)std::ceil((double)KT / std::max(8.0, fair / 4.0));
+      if (item <= std::max(8.0, fair / D)) continue;
+      int64_t s = (int64_t)std::ceil((double)KT / std::max(8.0, fair / D));
       s = std::max<int64_t>(c.splits, std::min<int64_t>(s, KT));
       const int64_t ktps = (KT + s - 1) / s;
       c.kps = ktps * 32;
@@ -350,7 +545,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
       int64_t s = 1;
       if (KT > 0 && fair > 0) {
         const double item = (double)KT;  // k-tiles per tile
-        s = (int64_t)std::ceil(item / std::max(1.0, fair / 4.0));
+        s = (int64_t)std::ceil(item / std::max(1.0, fair / D));
         s = std::max<int64_t>(1, std::min<int64_t>(s, KT));
       }
       const int64_t ktps = KT > 0 ? (KT + s - 1) / s : 0;
@@ -504,6 +699,60 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs) {
   return TC_OK;
 }
 
+// K7 (2): the balance divisor D for this batch, from whole-batch timings of
+// plans whose outputs are scratch copies (the caller's C is never touched).
+int tune_balance(tc_dtype dtype, tc_mode mode, const std::vector<tc_problem>& list) {
+  const size_t es = elem_size(dtype);
+  std::vector<tc_problem> tmp = list;
+  std::vector<size_t> off(list.size());
+  size_t total = 0;
+  for (size_t i = 0; i < list.size(); ++i) {
+    const tc_tensor& C = list[i].C;
+    int64_t lo = 0, hi = 0;
+    bool empty = false;
+    for (int d = 0; d < C.rank; ++d) {
+      if (C.len[d] == 0) empty = true;
+      const int64_t e = (C.len[d] - 1) * C.stride[d];
+      if (e < 0) lo += e; else hi += e;
+    }
+    off[i] = total;
+    if (!empty) total = align_up(total + (size_t)(hi - lo + 1) * es, 256);
+    tmp[i].C.data = reinterpret_cast<void*>(-lo * (int64_t)es);  // relative; rebased below
+  }
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, std::max<size_t>(total, 256)) != cudaSuccess ||
+      cudaMemset(scratch, 0, std::max<size_t>(total, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(scratch);
+    return kBalanceDefault;
+  }
+  for (size_t i = 0; i < tmp.size(); ++i)
+    tmp[i].C.data = static_cast<char*>(scratch) + off[i] + reinterpret_cast<intptr_t>(tmp[i].C.data);
+  cudaStream_t st = nullptr;
+  int best = kBalanceDefault;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
+    float tb = 1e30f;
+    for (int D : kBalanceCandidates) {
+      tc_plan* pl = new tc_plan;
+      pl->dtype = dtype;
+      pl->mode = mode;
+      cudaGetDevice(&pl->device);
+      float ms = 1e30f;
+      if (build_plan(pl, tmp, D) == TC_OK)
+        ms = time_best(st, [&] { return tc_plan_execute(pl, nullptr, 0, st) == TC_OK; });
+      tc_plan_destroy(pl);
+      if (ms < tb) {
+        tb = ms;
+        best = D;
+      }
+    }
+    cudaStreamDestroy(st);
+  }
+  cudaFree(scratch);
+  cudaGetLastError();
+  return best;
+}
+
 }  // namespace
 
 extern "C" {
@@ -513,16 +762,56 @@ int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem
   if (!out || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
   int rc = check_modes(dtype, mode);
   if (rc != TC_OK) return rc;
+  const std::vector<tc_problem> list(probs, probs + count);
+  int balance = kBalanceDefault;
+  if (autotune_enabled()) {
+    std::vector<Planned> ps;
+    for (const tc_problem& pr : list) {
+      Planned p;
+      if ((rc = plan_checked(dtype, &pr.A, &pr.B, &pr.C, &p)) != TC_OK) return rc;
+      if (p.L.m > 0 && p.L.n > 0) ps.push_back(p);
+    }
+    const uint64_t sig = batch_signature(mode, ps);
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_file();
+      auto it = g_balance.find(sig);
+      if (it != g_balance.end()) {
+        balance = it->second;
+        have = true;
+      }
+    }
+    if (!have && !ps.empty()) {
+      balance = tune_balance(dtype, mode, list);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_balance[sig] = balance;
+      tune_save_file();
+    }
+  }
   tc_plan* pl = new tc_plan;
   pl->dtype = dtype;
   pl->mode = mode;
   cudaGetDevice(&pl->device);
-  rc = build_plan(pl, std::vector<tc_problem>(probs, probs + count));
+  rc = build_plan(pl, list, balance);
   if (rc != TC_OK) {
     tc_plan_destroy(pl);
     return rc;
   }
   *out = pl;
+  return TC_OK;
+}
+
+int tc_plan_config(const tc_plan* plan, int32_t index, int32_t* out) {
+  if (!plan || !out || index < 0 || index >= plan->count) return TC_ERR_ARG;
+  out[0] = out[1] = out[2] = 0;
+  out[3] = plan->balance;
+  for (size_t i = 0; i < plan->orig.size(); ++i)
+    if (plan->orig[i] == index) {
+      out[0] = plan->cfg[i].bm;
+      out[1] = plan->cfg[i].bn;
+      out[2] = plan->cfg[i].splits;
+    }
   return TC_OK;
 }
 

@@ -111,7 +111,107 @@ def test_autotuned_batch(monkeypatch, tmp_path):
     assert tc.device_error() == 0
     check_batch(host, dev, "bf16x3")
     lines = cache.read_text().strip().splitlines()
-    assert lines and all(len(l.split()) == 8 for l in lines)
+    assert lines and all(l.split()[0] in ("tile", "balance") for l in lines)
+    assert any(l.startswith("balance ") for l in lines)
+
+
+def _cm_strides(shape):
+    st, acc = [], 1
+    for n in shape:
+        st.append(acc)
+        acc *= n
+    return tuple(st)
+
+
+def _tile_key(mode_code, pl):
+    lg = lambda x: 0 if x <= 1 else int(round(np.log2(x)))  # noqa: E731
+    return (f"{mode_code} {lg(pl['m'])} {lg(pl['n'])} {lg(pl['k'])} "
+            f"{int(pl['a_k_contig'])} {int(pl['b_k_contig'])}")
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3"])
+def test_cached_tile_record_changes_the_choice(monkeypatch, tmp_path, mode):
+    # three problems of one shape class (m = 200, n = 100, k = 96): the
+    # estimate takes the least-padding FP64 tile (64 x 32 pads 200 x 100 least)
+    # or the tensor-core tile covering n (112 columns); a cached record of
+    # the class overrides it, and the results still match the oracle
+    dt = torch.float64 if mode == "f64" else torch.float32
+    g = torch.Generator().manual_seed(5)
+    r = lambda *s: (torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1).to(dt).double()  # noqa: E731
+    cases = [(r(200, 96), r(96, 100), r(200, 100)) for _ in range(3)]
+    dev = [(to_device(A, dt), "ip", to_device(B, dt), "pj", to_device(C, dt), "ij", 1.0, 0.5)
+           for A, B, C in cases]
+    monkeypatch.delenv("TC_AUTOTUNE", raising=False)
+    monkeypatch.delenv("TC_AUTOTUNE_CACHE", raising=False)
+    est = tc.Plan(dev, mode=mode)
+    pl = tc.plan_describe(dev[0][0], "ip", dev[0][2], "pj", dev[0][4], "ij")
+    mcode = {"f64": 0, "bf16x3": 1}[mode]
+    if mode == "f64":
+        tiles = {0: (64, 64), 1: (32, 64), 2: (64, 32)}  # the FP64 tile classes
+        pad = lambda t: -(-200 // t[0]) * t[0] * (-(-100 // t[1]) * t[1])  # noqa: E731
+        got = (est.config(0)["bm"], est.config(0)["bn"])
+        assert got == min(tiles.values(), key=pad)  # the least-padding estimate
+        forced = next(c for c, t in tiles.items() if t != got)
+        want = tiles[forced]
+    else:
+        assert est.config(0)["bn"] == 112
+        forced, want = 64, (128, 64)
+    est.close()
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"tile {_tile_key(mcode, pl)} {forced}\n")
+    monkeypatch.setenv("TC_AUTOTUNE_CACHE", str(cache))
+    plan = tc.Plan(dev, mode=mode)
+    for i in range(3):
+        c = plan.config(i)
+        assert (c["bm"], c["bn"]) == want
+    plan.execute()
+    torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    for (A, B, C0), d in zip(cases, dev):
+        ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.5, C0, "ij")
+        assert norm_err(d[4].cpu().double().numpy(), ref, mag) <= TOLS[mode]
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", ["f64", "bf16x3"])
+def test_balance_divisor_is_tuned_and_cached(monkeypatch, tmp_path, mode):
+    # forty problems and two with a long contracted range: the tuner
+    # times the batch with D = 2, 4, 8, 16 and records its choice; a cached
+    # D then decides how finely the long problems are split
+    dt = torch.float64 if mode == "f64" else torch.float32
+    g = torch.Generator().manual_seed(6)
+    r = lambda *s: (torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1).to(dt).double()  # noqa: E731
+    cases = [(r(128, 2048), r(2048, 256), torch.zeros(128, 256, dtype=torch.float64)) for _ in range(40)]
+    cases += [(r(96, 20000), r(20000, 80), torch.zeros(96, 80, dtype=torch.float64)) for _ in range(2)]
+    dev = [(to_device(A, dt), "ip", to_device(B, dt), "pj", to_device(C, dt), "ij", 1.0, 0.0)
+           for A, B, C in cases]
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TC_AUTOTUNE_CACHE", str(cache))
+    tuned = tc.Plan(dev, mode=mode)
+    bal = [l for l in cache.read_text().splitlines() if l.startswith("balance ")]
+    assert len(bal) == 1
+    sig, d = bal[0].split()[1:]
+    assert int(d) in (2, 4, 8, 16) and tuned.config(0)["balance"] == int(d)
+    tuned.close()
+    splits = {}
+    for D in (2, 16):
+        f = tmp_path / f"tune{D}.txt"
+        f.write_text(f"balance {sig} {D}\n")
+        monkeypatch.setenv("TC_AUTOTUNE_CACHE", str(f))
+        plan = tc.Plan(dev, mode=mode)
+        c = plan.config(len(cases) - 1)
+        assert c["balance"] == D
+        splits[D] = c["splits"]
+        for d_ in dev:
+            d_[4].zero_()
+        plan.execute()
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
+        for (A, B, C0), d_ in zip(cases, dev):
+            ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
+            assert norm_err(d_[4].cpu().double().numpy(), ref, mag) <= TOLS[mode]
+        plan.close()
+    assert splits[16] > splits[2] >= 1
 
 
 @pytest.mark.parametrize("mode", ["f64", "bf16x3"])
