@@ -53,6 +53,9 @@ def parse():
                     help="after the timed region, run one more step between cudaProfilerStart "
                          "and cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="batch512: the autotuner's cache file (default: a file in the system's "
+                         "temporary directory; the plans are tuned when it holds no record)")
     ap.add_argument("--no-ttgt", action="store_true", help="skip the TTGT comparison leg")
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload only: skip the secondary configurations (precision "
@@ -432,9 +435,19 @@ def run_batch(args, ws, rank, local):
             p.labC, 1.0, 0.0) for p, h in zip(probs, host)]
     flops = sum(p.flops() for p in probs)
     lib = L.lib()
-    if mode != "f64":
-        os.environ.setdefault("TC_AUTOTUNE", "1")
+    # tuned plans: tile per shape class and the k-split balance of the batch
+    import tempfile
+    cache = args.autotune_cache or os.environ.get("TC_AUTOTUNE_CACHE") or \
+        os.path.join(tempfile.gettempdir(), "tc_autotune_cache.txt")
+    os.environ["TC_AUTOTUNE_CACHE"] = cache
+    t_plan = time.perf_counter()
     plan = tc.Plan(dev, mode=mode)
+    t_plan = time.perf_counter() - t_plan
+    cfgs = [plan.config(i) for i in range(len(dev))]
+    tuned = {"cache": cache, "plan_create_s": round(t_plan, 2), "balance_divisor": cfgs[0]["balance"],
+             "split_problems": sum(c["splits"] > 1 for c in cfgs),
+             "tiles": {f"{a}x{b}": n for (a, b), n in
+                       __import__("collections").Counter((c["bm"], c["bn"]) for c in cfgs).items()}}
     plan.execute()
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
@@ -497,7 +510,7 @@ def run_batch(args, ws, rank, local):
         plan.close()
         line = {"ms_per_step": round(ms, 4), "value": round(ws * flops / (ms * 1e-3) / 1e12, 5),
                 "unit": "TFLOP/s", "steps": K, "warmup": warm, "total_flops": flops,
-                "gpu_launches_per_step": int(per_step), "device_error": err_code}
+                "gpu_launches_per_step": int(per_step), "device_error": err_code, "autotune": tuned}
         if mode == "f64":
             peak, src, prods = fp64_peak_tflops(), "cuBLAS DGEMM 4096^3 measured in this run", 1
         else:
@@ -555,7 +568,7 @@ def run_batch(args, ws, rank, local):
         "data": "synthetic (seeded uniform[-1,1]; random labels, ranks, extents 8..64, permuted dense layouts)",
         "config": {"workload": f"batch512: 512 independent contractions, d_P 1-3, ranks 2-6, extents 8..64, "
                                f"one CUDA-graph replay of a planned batch, mode={mode}",
-                   "total_flops": flops,
+                   "total_flops": flops, "autotune": tuned,
                    "l2": "inputs larger than L2 (%.2f GB)" % (bi / 1e9), "parallelism": f"replicas x{ws}"},
         "clocks": clk,
         "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
