@@ -47,10 +47,12 @@ struct ProbCfg {
 //      flags -- the output tile: on the tensor cores the tile width (the one
 //      covering n up to 128, and half of it); on the FP64 path the tile class
 //      (64 x 64, 32 x 64, 64 x 32).  Each candidate runs the class's first
-//      problem of the batch on one SM's worth of CTAs (one persistent CTA;
-//      on the FP64 path the class's CTAs per SM) into a scratch copy of its
-//      output; the least time wins: in a batch the other problems keep the
-//      other SMs busy, so the SM-time a problem costs is what to minimise.
+//      problem of the batch into a scratch copy of its output; the least
+//      time wins.  In a batch the other problems keep the other SMs busy, so
+//      what one problem costs in SM-time is what to minimise: the tensor-core
+//      candidates run on one persistent CTA (one SM), the FP64 ones as many
+//      copies of the problem's tiles as fill four waves of the whole GPU's
+//      CTAs of that tile class (time per copy).
 //  (2) Per batch -- a signature of its problems' shapes and layout classes --
 //      the split of long contracted ranges: a problem is split along k until
 //      no work item exceeds 1/D of a CTA's (FP64: a warp's) fair share of the
@@ -61,8 +63,8 @@ struct ProbCfg {
 // read from it and written back (one record per line).  Tuning is on when
 // TC_AUTOTUNE=1, or when TC_AUTOTUNE_CACHE is set and TC_AUTOTUNE is not 0;
 // otherwise the plan uses the estimates (least padding, D = 4).  Tile timing
-// of one plan stops after about two seconds (the remaining classes keep the
-// estimate and are tuned by a later plan).
+// within one tc_plan_create stops after about two seconds (the remaining
+// classes keep the estimate and are tuned by a later plan).
 struct TuneKey {
   int mode, lm, ln, lk, akc, bkc;
   bool operator<(const TuneKey& o) const {
@@ -75,6 +77,7 @@ std::map<TuneKey, int> g_tile;          // tensor cores: tile width; FP64: tile 
 std::map<uint64_t, int> g_balance;      // batch signature -> D
 bool g_tune_loaded = false;
 std::string g_tune_path;  // the cache file the tables were read from ("" for none)
+thread_local double t_tile_budget_ms = 0.0;  // tile timing left to this tc_plan_create
 constexpr double kTileTuneBudgetMs = 2000.0;
 constexpr int kBalanceCandidates[] = {2, 4, 8, 16};
 constexpr int kBalanceDefault = 4;
@@ -305,8 +308,14 @@ float time_f64_class(const Planned& p, tc_dtype dt, double alpha, double beta, i
   d.tiles_n = (int32_t)((p.L.n + bn - 1) / bn);
   d.splits = 1;
   d.kps = std::max<int64_t>(1, (p.L.k + f64_tile_k() - 1) / f64_tile_k()) * f64_tile_k();
-  std::vector<WorkItem> items((size_t)tiles);
-  for (int64_t i = 0; i < tiles; ++i) items[(size_t)i] = WorkItem{0, (int32_t)i, 0, 0};
+  // the problem's tiles repeated until the whole GPU's CTAs of this class run
+  // at least four waves of them: time / repetitions is then what one copy of
+  // the problem costs at full occupancy, as in a batch (repeated tiles
+  // rewrite the same scratch output)
+  const int64_t sms = sm_count();
+  const int64_t reps = std::max<int64_t>(1, (4 * sms * f64_batch_ctas_per_sm(cls) + tiles - 1) / tiles);
+  std::vector<WorkItem> items((size_t)(tiles * reps));
+  for (int64_t i = 0; i < tiles * reps; ++i) items[(size_t)i] = WorkItem{0, (int32_t)(i % tiles), 0, 0};
   char* base = static_cast<char*>(t.dev);
   DevProblem* dprob = reinterpret_cast<DevProblem*>(base);
   WorkItem* ditems = reinterpret_cast<WorkItem*>(base + align_up(sizeof(DevProblem), 256));
@@ -320,16 +329,16 @@ float time_f64_class(const Planned& p, tc_dtype dt, double alpha, double beta, i
   q.dtype = dt;
   q.probs = dprob;
   q.items = ditems;
-  q.nitems = tiles;
-  for (int c = 0; c <= kF64BatchClasses; ++c) q.class_off[c] = c <= cls ? 0 : tiles;
-  q.sms = 1;
+  q.nitems = tiles * reps;
+  for (int c = 0; c <= kF64BatchClasses; ++c) q.class_off[c] = c <= cls ? 0 : tiles * reps;
+  q.sms = sms;
   q.split_probs = nullptr;
   q.split_col_prefix = nullptr;
   q.split_cols = 0;
   q.n_split_probs = 0;
   q.max_m_split = q.max_n_split = 0;
   q.counter = ctr;
-  return time_best(t.st, [&] { return launch_f64_batched(q, t.st) == cudaSuccess; });
+  return time_best(t.st, [&] { return launch_f64_batched(q, t.st) == cudaSuccess; }) / (float)reps;
 }
 
 size_t f64_tune_dev_bytes(const Planned& p) {
@@ -337,7 +346,9 @@ size_t f64_tune_dev_bytes(const Planned& p) {
   for (int c = 0; c < kF64BatchClasses; ++c) {
     int bm, bn;
     f64_batch_tile(c, &bm, &bn);
-    most = std::max<int64_t>(most, ((p.L.m + bm - 1) / bm) * ((p.L.n + bn - 1) / bn));
+    const int64_t tiles = ((p.L.m + bm - 1) / bm) * ((p.L.n + bn - 1) / bn);
+    const int64_t reps = std::max<int64_t>(1, (4 * sm_count() * f64_batch_ctas_per_sm(c) + tiles - 1) / tiles);
+    most = std::max<int64_t>(most, tiles * reps);
   }
   return align_up(sizeof(DevProblem), 256) + align_up(sizeof(WorkItem) * (size_t)most, 256) +
          align_up(sizeof(unsigned long long) * kF64BatchClasses, 256);
@@ -446,7 +457,6 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   }
   // the autotuner's tile records (see K7), timed here for classes without one
   const bool tune = autotune_enabled();
-  double tune_ms = 0.0;
   auto tuned_tile = [&](int i) -> int {
     if (!tune || pl->planned[i].L.k == 0) return -1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -454,14 +464,14 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     const TuneKey key = tune_key(pl->mode, pl->planned[i]);
     auto it = g_tile.find(key);
     if (it != g_tile.end()) return it->second;
-    if (tune_ms > kTileTuneBudgetMs) return -1;
+    if (t_tile_budget_ms <= 0.0) return -1;
     const Layout& L = pl->planned[i].L;
     // one SM runs the whole problem: skip those too large to time that way
     const double flops = 2.0 * (double)L.m * (double)L.n * (double)L.k;
     if (flops > (f64 ? 0x1p27 : 0x1p34)) return -1;
     const auto t0 = std::chrono::steady_clock::now();
     const int v = tune_tile(pl->planned[i], pl->dtype, pl->mode, alpha[i], beta[i]);
-    tune_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    t_tile_budget_ms -= std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (v >= 0) {
       g_tile[key] = v;
       tune_save_file();
@@ -764,6 +774,7 @@ int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem
   if (rc != TC_OK) return rc;
   const std::vector<tc_problem> list(probs, probs + count);
   int balance = kBalanceDefault;
+  t_tile_budget_ms = kTileTuneBudgetMs;  // shared by the balance trials and the plan
   if (autotune_enabled()) {
     std::vector<Planned> ps;
     for (const tc_problem& pr : list) {

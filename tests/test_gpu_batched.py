@@ -131,10 +131,10 @@ def _tile_key(mode_code, pl):
 
 @pytest.mark.parametrize("mode", ["f64", "bf16x3"])
 def test_cached_tile_record_changes_the_choice(monkeypatch, tmp_path, mode):
-    # three problems of one shape class (m = 200, n = 100, k = 96): the
-    # estimate takes the least-padding FP64 tile (64 x 32 pads 200 x 100 least)
-    # or the tensor-core tile covering n (112 columns); a cached record of
-    # the class overrides it, and the results still match the oracle
+    # three problems of one shape class (200 x 100 x 96 as given; the planner
+    # swaps A and B for the row-major C): the estimate takes the
+    # least-padding FP64 tile or the tensor-core tile covering n; a cached
+    # record of the class overrides it, and the results still match the oracle
     dt = torch.float64 if mode == "f64" else torch.float32
     g = torch.Generator().manual_seed(5)
     r = lambda *s: (torch.rand(*s, generator=g, dtype=torch.float64) * 2 - 1).to(dt).double()  # noqa: E731
@@ -146,15 +146,16 @@ def test_cached_tile_record_changes_the_choice(monkeypatch, tmp_path, mode):
     est = tc.Plan(dev, mode=mode)
     pl = tc.plan_describe(dev[0][0], "ip", dev[0][2], "pj", dev[0][4], "ij")
     mcode = {"f64": 0, "bf16x3": 1}[mode]
+    m, n = pl["m"], pl["n"]  # the matrix view (C row-major: A and B trade roles)
     if mode == "f64":
         tiles = {0: (64, 64), 1: (32, 64), 2: (64, 32)}  # the FP64 tile classes
-        pad = lambda t: -(-200 // t[0]) * t[0] * (-(-100 // t[1]) * t[1])  # noqa: E731
+        pad = lambda t: -(-m // t[0]) * t[0] * (-(-n // t[1]) * t[1])  # noqa: E731
         got = (est.config(0)["bm"], est.config(0)["bn"])
         assert got == min(tiles.values(), key=pad)  # the least-padding estimate
         forced = next(c for c, t in tiles.items() if t != got)
         want = tiles[forced]
     else:
-        assert est.config(0)["bn"] == 112
+        assert est.config(0)["bn"] == min(128, -(-n // 16) * 16)  # the tile covering n
         forced, want = 64, (128, 64)
     est.close()
     cache = tmp_path / "tune.txt"
