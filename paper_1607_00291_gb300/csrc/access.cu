@@ -163,9 +163,10 @@ bool make_box(const Bundle& R, const int64_t* rs, const Bundle& K, const int64_t
 
 }  // namespace
 
-void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box) {
+void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box, bool pair) {
   std::memset(&d.boxA, 0, sizeof d.boxA);
   std::memset(&d.boxB, 0, sizeof d.boxB);
+  d.pair = 0;
   const int acc = g_access.load();
   d.elem_gather = acc == TC_ACCESS_SCATTER ? 1 : 0;
   if (!allow_box || acc != TC_ACCESS_BOX || L.m <= 0 || L.n <= 0 || L.k <= 0) return;
@@ -174,11 +175,13 @@ void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_b
   // measured slower than gathering both
   const bool a_ok = make_box(L.I, L.I.s0, L.P, L.P.s0, d.a, kTileM, d.a_kc != 0,
                              maps ? &maps[0] : nullptr, &d.boxA);
-  const bool b_ok = make_box(L.J, L.J.s0, L.P, L.P.s1, d.b, d.bn, d.b_kc != 0,
-                             maps ? &maps[1] : nullptr, &d.boxB);
+  const bool b_ok = make_box(L.J, L.J.s0, L.P, L.P.s1, d.b, pair ? d.bn / 2 : d.bn,
+                             d.b_kc != 0, maps ? &maps[1] : nullptr, &d.boxB);
   if (!(a_ok && b_ok)) {
     std::memset(&d.boxA, 0, sizeof d.boxA);
     std::memset(&d.boxB, 0, sizeof d.boxB);
+  } else {
+    d.pair = pair ? 1 : 0;
   }
 }
 

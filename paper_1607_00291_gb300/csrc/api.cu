@@ -69,8 +69,9 @@ int sm_count() {
 //  * tile width bn: the next multiple of 16 above n, at most 128;
 //  * split count S: when the output alone has fewer tiles than SMs, split the
 //    contracted range so the grid covers the SMs, keeping at least 8 k-tiles
-//    of 32 per split (the kernel itself bounds every FP32 accumulation chain
-//    to 1024 terms, so accuracy needs no split).
+//    of 32 per split; and at least as many splits as keep every split within
+//    tc_max_item_ktiles() k-tiles (the kernel bounds every FP32 accumulation
+//    chain to 1024 terms and folds at most 16 such chunks per item).
 TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force, int split_mult) {
   (void)pieces;
   TcChoice c;
@@ -83,11 +84,37 @@ TcChoice choose_tc(const Layout& L, int pieces, int sms, int bn_force, int split
   int64_t s = 1;
   if (tiles < sms) s = std::min<int64_t>(sms / std::max<int64_t>(tiles, 1), std::max<int64_t>(1, kt / 8));
   s = std::max<int64_t>(1, s) * std::max(1, split_mult);
+  s = std::max<int64_t>(s, (kt + tc_max_item_ktiles() - 1) / tc_max_item_ktiles());
   s = std::min<int64_t>(s, std::max<int64_t>(kt, 1));
   const int64_t ktps = (kt + s - 1) / s;
   c.kps = std::max<int64_t>(1, ktps) * 32;
   c.splits = (int)std::max<int64_t>(1, (L.k + c.kps - 1) / c.kps);
   return c;
+}
+
+// The pair form of the tensor-core box kernel (cta_group::2: each CTA pair
+// computes 256-row tiles, each CTA loading its own 128 rows of A and half of
+// the tile's columns of B, which cuts every SM's intake of operand bytes per
+// k-tile by a quarter) is taken when both operands are boxes for it and the
+// problem has at least two waves of pair tiles.  TC_PAIR=0 turns it off,
+// TC_PAIR=1 takes it whenever the boxes allow (tests, experiments).
+int pair_setting() {
+  const char* e = std::getenv("TC_PAIR");
+  if (e && e[0] == '0') return 0;
+  if (e && e[0] == '1') return 2;
+  return 1;
+}
+
+// Access plan of a single tensor-core contraction: the pair form where it
+// applies, else boxes or gathers (plan_access).
+void plan_single_access(const Layout& L, DevProblem& d, CUtensorMap* maps, int sms) {
+  const int ps = pair_setting();
+  const int64_t pair_items = ((L.m + 255) / 256) * d.tiles_n * d.splits;
+  if (ps > 0 && L.m > 128 && (ps == 2 || pair_items >= sms)) {
+    plan_access(L, d, maps, true, true);
+    if (d.pair) return;
+  }
+  plan_access(L, d, maps);
 }
 
 struct WsLayout {
@@ -177,7 +204,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     d.tiles_n = (int32_t)((L.n + d.bn - 1) / d.bn);
     d.splits = w.tcc.splits;
     d.kps = w.tcc.kps;
-    plan_access(L, d, q.tm);
+    plan_single_access(L, d, q.tm, sm_count());
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.reduce_f64 = split_reduction_f64() ? 1 : 0;
     q.ctas = sm_count();
@@ -280,9 +307,12 @@ int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_ten
   d.b = p.b;
   d.a_kc = p.info.a_k_contig;
   d.b_kc = p.info.b_k_contig;
-  d.bn = ws_layout(p, mode).tcc.bn;
+  const TcChoice tcc = ws_layout(p, mode).tcc;
+  d.bn = tcc.bn;
+  d.tiles_n = (int32_t)((p.L.n + d.bn - 1) / d.bn);
+  d.splits = tcc.splits;
   CUtensorMap maps[2];
-  plan_access(p.L, d, box_encoder_available() ? maps : nullptr);
+  plan_single_access(p.L, d, box_encoder_available() ? maps : nullptr, sm_count());
   *a_box = d.boxA.rank > 0;
   *b_box = d.boxB.rank > 0;
   return TC_OK;

@@ -108,9 +108,11 @@ struct BoxAccess {
 // operands, access flags and tile width, and encode the tensor maps of the
 // operands that take boxes into maps[0] (A) and maps[1] (B); with maps ==
 // null only the eligibility is decided; allow_box = false keeps every operand
-// gathered.  Defined in access.cu.
+// gathered; pair = true plans B's boxes bn / 2 columns wide (the pair form)
+// and sets d.pair when both operands take boxes.  Defined in access.cu.
 struct DevProblem;
-void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box = true);
+void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box = true,
+                 bool pair = false);
 bool box_encoder_available();  // the driver's tensor-map encoder could be found
 // The process-wide split-reduction setting (tc_set_split_reduction): true for FP64.
 bool split_reduction_f64();
@@ -132,6 +134,9 @@ struct DevProblem {
   int32_t splits;   // pieces of the contracted range
   int32_t elem_gather;  // tensor-core path: gather element by element, ignoring the
                         // block-scatter vectors (the plain scatter-matrix form)
+  int32_t pair;     // tensor-core box form on CTA pairs (cta_group::2): 256-row tiles,
+                    // each CTA of the pair loading its 128 rows of A and half of B's
+                    // columns (boxB then covers bn / 2 columns)
   int64_t kps;      // contracted indices per split (a multiple of the k-tile)
   BoxAccess boxA, boxB;       // tensor-core path: TMA boxes or gathers per operand
   const CUtensorMap* tmaps;   // batch: the two tensor maps in device memory (a single
@@ -194,5 +199,8 @@ cudaError_t launch_build_scatter_batched(const Layout* layouts, const int64_t* o
                                          int32_t count, int64_t total, int32_t b, int64_t* out,
                                          cudaStream_t s);
 int tc_bn_max();  // widest output tile of the tensor-core mainloop (columns)
+// Most k-tiles (of 32) one work item of the tensor-core mainloop may take:
+// its running chunk sum is plain FP32, accurate for that many chunks.
+int tc_max_item_ktiles();
 
 }  // namespace tc

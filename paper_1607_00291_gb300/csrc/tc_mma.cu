@@ -25,17 +25,19 @@
 // the spiky 4096^3 workload: 2.25e-5 with 4096-term chains).  So a tile's
 // contracted range is processed in chunks of at most 1024 terms, each into a
 // fresh accumulator, and the epilogue warps add the finished chunks into a
-// running float-float sum (Knuth's two-sum) that stays in Tensor Memory,
-// releasing the accumulator to the next chunk's MMAs as soon as they have
-// read it.  After the last chunk they apply alpha/beta through
-// rscat(C) + cscat(C), or -- when a tile's range is also split across CTAs for
-// parallelism -- store the FP32 partial that K4 sums the same compensated way.
+// running FP32 sum that stays in Tensor Memory, releasing the accumulator to
+// the next chunk's MMAs as soon as they have read it.  A work item holds at
+// most 16 chunks (the planner splits longer ranges across items), so the
+// folds add at most 16 roundings of 2^-24 of the sum's magnitude (below 1e-6
+// of sum|a||b|).  After the last chunk they apply alpha/beta through
+// rscat(C) + cscat(C), or -- when a tile's range is split across items --
+// store the FP32 partial that K4 sums with compensated (two-sum) arithmetic.
 //
 // Warp roles (672 threads; 704 in the BOX form): warps 0-7 load (cp.async),
 // or in the BOX form convert, warps 8-15 convert, warps 16-19 run the
 // epilogue (one per Tensor Memory lane quarter), warp 20 owns the Tensor
-// Memory allocation (512 columns: the accumulator, the hi and lo words of the
-// running sum, A's piece stages) and its lane 0 issues the MMAs, and in the
+// Memory allocation (512 columns: the accumulator, the running sum, A's piece
+// stages) and its lane 0 issues the MMAs, and in the
 // BOX form lane 0 of warp 21 issues the boxes.  The output stores of one tile
 // overlap the MMAs of the next.  Hand-offs go through mbarriers: raw_full
 // (cp.async completion, or the boxes' transaction count) / raw_empty,
@@ -82,23 +84,30 @@ constexpr int QR = 16, QPUB = 2;
 constexpr int KSLOT = 2 * BK + 2 * (BK / 4);  // cA[32] rB[32] cbsA[8] rbsB[8]
 constexpr int BNMAX = 128;        // widest output tile (columns)
 constexpr int CHUNK_KT = 32;      // k-tiles per accumulation chunk (1024 terms)
-// Tensor Memory columns: accumulator, running hi and lo words, A's piece
-// stages (16 columns per piece and k-tile: 32 bf16 k-values, two per column)
-constexpr uint32_t TM_ACC = 0, TM_HI = BNMAX, TM_LO = 2 * BNMAX, TM_A = 3 * BNMAX, TM_COLS = 512;
+constexpr int MAX_CHUNKS = 16;    // chunks per work item (longer ranges are split)
+// Tensor Memory columns: accumulator, running sum, A's piece stages (16
+// columns per piece and k-tile: 32 bf16 k-values, two per column)
+constexpr uint32_t TM_ACC = 0, TM_SUM = BNMAX, TM_A = 2 * BNMAX, TM_COLS = 512;
 
 // Shared-memory plan.  Raw FP32 stages hide the load latency; bf16 MMA stages
 // (B's pieces in shared memory, A's in Tensor Memory) let the converters run
 // ahead of the tensor core.
-template <int NS, bool BOX>
+// PAIR: B's panels are half as wide (the pair splits the tile's columns), so
+// a raw stage is 24 instead of 32 KB and seven of them fit.
+template <int NS, bool BOX, bool PAIR = false>
 struct Lay {
-  static constexpr int RS = 5;                   // raw FP32 stages
-  static constexpr int MS = NS == 3 ? 2 : 3;     // bf16 MMA stages
-  static constexpr int PB = BNMAX * BK * 2;      // one bf16 piece of B
+  static constexpr int RB = PAIR ? BNMAX / 2 : BNMAX;  // B rows per CTA
+  // bf16 MMA stages, as many as Tensor Memory (A's pieces: NS x 16 of its 256
+  // free columns per stage) and shared memory (B's pieces) allow: the ring of
+  // MMA stages, each returned by a tcgen05.commit, paces the pipeline
+  static constexpr int MS = PAIR ? (NS == 3 ? 5 : 8) : (NS == 3 ? 3 : 5);
+  static constexpr int RS = PAIR ? 6 : 4;        // raw FP32 stages
+  static constexpr int PB = RB * BK * 2;         // one bf16 piece of B
   static constexpr int MMA_STAGE = NS * PB;
   static constexpr uint32_t TA_STAGE = NS * 16;  // Tensor Memory columns of A's pieces
   static_assert(TM_A + MS * TA_STAGE <= TM_COLS, "Tensor Memory plan");
   static constexpr int RAW_A = BM * BK * 4;
-  static constexpr int RAW_STAGE = RAW_A + BNMAX * BK * 4;
+  static constexpr int RAW_STAGE = RAW_A + RB * BK * 4;
   static constexpr int MMA0 = 0;
   static constexpr int RAW0 = MMA0 + MS * MMA_STAGE;
   static constexpr int SCAT = RAW0 + RS * RAW_STAGE;  // int64 rA[BM] cB[BNMAX] rC[BM] cC[BNMAX]
@@ -171,7 +180,11 @@ struct Item {
   int nchunks;
 };
 
-__device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w) {
+// PAIR: the CTA pair's tile has 256 rows; CTA `crank` of the pair takes rows
+// 128 crank .. 128 crank + 127 of it (all of its columns).
+template <bool PAIR = false>
+__device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w,
+                                         uint32_t crank = 0) {
   Item it;
   int64_t tile;
   if (a.probs) {
@@ -185,7 +198,7 @@ __device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single
     it.split = (int)(w / a.tiles_single);
   }
   const DevProblem* d = it.d;
-  it.m0 = (tile / d->tiles_n) * BM;
+  it.m0 = (tile / d->tiles_n) * (PAIR ? 2 * BM : BM) + (PAIR ? (int64_t)BM * crank : 0);
   it.n0 = (tile % d->tiles_n) * d->bn;
   it.kbeg = (int64_t)it.split * d->kps;
   it.kend = it.kbeg + d->kps < d->k ? it.kbeg + d->kps : d->k;
@@ -353,10 +366,11 @@ __device__ __forceinline__ void convert_panel(int t, const uint8_t* raw, uint8_t
                                               bool kcontig, int rstride) {
   constexpr int TASKS = R * BK / 8;
   constexpr int PBY = R * BK * 2;
-  static_assert(TASKS % NTH == 0, "converter tasks per thread");
+  static_assert(TASKS % NTH == 0 || NTH % TASKS == 0, "converter tasks per thread");
   const float* rf = reinterpret_cast<const float*>(raw);
+  if (TASKS < NTH && t >= TASKS) return;  // fewer tasks than threads: one each
 #pragma unroll
-  for (int i = 0; i < TASKS / NTH; ++i) {
+  for (int i = 0; i < (TASKS + NTH - 1) / NTH; ++i) {
     const int c = t + i * NTH;
     const int r = c % R, q = c / R;
     float v[8];
@@ -421,10 +435,15 @@ __device__ __forceinline__ void convert_a_tmem(int cw, int lane, const uint8_t* 
 // vectors (no box code at all).  BOX = true: both operands of every work item
 // are TMA boxes, issued by the box warp; there are no loaders, and their eight
 // warps convert alongside the converters.
-template <int NS, bool BOX>
+template <int NS, bool BOX, bool PAIR>
 __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__ Args a) {
+  static_assert(BOX || !PAIR, "the pair form loads both operands as boxes");
   constexpr int NCV = BOX ? NLOAD + NCONV : NCONV;  // converter threads
-  using Ly = Lay<NS, BOX>;
+  // B rows per CTA: the pair splits the tile's columns between its two CTAs
+  // (its bf16 pieces then lie RB * BK * 2 bytes apart in a stage)
+  constexpr int RB = PAIR ? BNMAX / 2 : BNMAX;
+  using Ly = Lay<NS, BOX, PAIR>;
+  static_assert(RB == Ly::RB, "B rows per CTA");
   constexpr int RS = Ly::RS, MS = Ly::MS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align to 1 KB by offsetting the shared-memory pointer itself, so that the
@@ -458,13 +477,15 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       mbar_init(&raw_full[s], BOX ? 1 : NLOAD);
       mbar_init(&raw_empty[s], NCV / 32);  // one arrival per converter warp
     }
+    // pair form: the even CTA's mma_full and acc_empty also count the odd
+    // CTA's converter warps and epilogue threads (remote arrivals)
     for (int s = 0; s < MS; ++s) {
-      mbar_init(&mma_full[s], NCV / 32);
+      mbar_init(&mma_full[s], (PAIR ? 2 : 1) * NCV / 32);
       mbar_init(&mma_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], NEPI);
+      mbar_init(&acc_empty[b], (PAIR ? 2 : 1) * NEPI);
     }
     mbar_init(drain, 1);
     for (int q = 0; q < QR; ++q) {
@@ -477,16 +498,26 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     *sProb = a.single;
     fence_mbar_init();
   }
+  // the pair's two CTAs allocate together: the same columns in both
   if (warp == MMA_WARP) {
-    tmem_alloc(tmem_slot, TM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc2(tmem_slot, TM_COLS);
+      tmem_relinquish2();
+    } else {
+      tmem_alloc(tmem_slot, TM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  // both CTAs' barriers are initialised before any arrival from the other
+  if constexpr (PAIR) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int64_t nitems = a.nitems;
-  const int64_t w0 = blockIdx.x, dw = gridDim.x;
+  // pair form: the pair (cluster) takes work items, both CTAs the same ones
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+  const int64_t w0 = PAIR ? blockIdx.x / 2 : blockIdx.x, dw = PAIR ? gridDim.x / 2 : gridDim.x;
   // dynamic items (batches, gather form): the j-th item of this CTA is entry
   // j of the work queue; otherwise items w0, w0 + dw, ...
   const bool dyn = !BOX && a.counter != nullptr;
@@ -548,12 +579,12 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     };
     if (dyn && t == 0) publish_upto(QPUB - 1);
     int64_t w = item_of(0);
-    if (w < nitems) fetch_rows(get_item(a, sProb, w));
+    if (w < nitems) fetch_rows(get_item<PAIR>(a, sProb, w, crank));
     for (int64_t j = 0;; ++j) {
       // uniform exit; previous rows consumed
       if (bar_or(BAR_LOAD, NLOAD, *abort || w >= nitems)) break;
       if (dyn && t == 0) publish_upto(j + QPUB);
-      const Item it = get_item(a, sProb, w);
+      const Item it = get_item<PAIR>(a, sProb, w, crank);
       const DevProblem* d = it.d;
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
@@ -562,7 +593,7 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       }
       w = item_of(j + 1);
       release_item(j);
-      if (w < nitems) fetch_rows(get_item(a, sProb, w));
+      if (w < nitems) fetch_rows(get_item<PAIR>(a, sProb, w, crank));
       const float* A = static_cast<const float*>(d->a);
       const float* B = static_cast<const float*>(d->b);
       const bool akc = d->a_kc, bkc = d->b_kc;
@@ -616,16 +647,17 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     int64_t w = item_of(0);
     for (int64_t j = 0;; ++j) {
       if (bar_or(BAR_CONV, NCV, *abort || w >= nitems)) break;  // uniform exit
-      const Item it = get_item(a, sProb, w);
+      const Item it = get_item<PAIR>(a, sProb, w, crank);
       w = item_of(j + 1);
       release_item(j);
       const bool akc = it.d->a_kc, bkc = it.d->b_kc;
-      // a row-contiguous B box holds k-rows of bn floats; the gather's k-rows hold BNMAX
-      const int rsB = BOX && !it.d->b_kc ? it.d->bn : BNMAX;
+      // a row-contiguous B box holds k-rows of bn floats (pair form: bn / 2);
+      // the gather's k-rows hold BNMAX
+      const int rsB = BOX && !it.d->b_kc ? (PAIR ? it.d->bn / 2 : it.d->bn) : BNMAX;
       for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
         const int rs = (int)(g % RS), ms = (int)(g % MS);
         const bool ok = mbar_wait(&raw_full[rs], (uint32_t)((g / RS) & 1), abort) &&
-                        mbar_wait(&mma_empty[ms], (uint32_t)(((g / MS) & 1) ^ 1), abort);
+                        mbar_wait<PAIR>(&mma_empty[ms], (uint32_t)(((g / MS) & 1) ^ 1), abort);
         if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together (it arrives as one)
           record_timeout(abort, a.err);
           break;
@@ -635,10 +667,10 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         uint8_t* st = smem + Ly::MMA0 + ms * Ly::MMA_STAGE;
         convert_a_tmem<NS, NCV / 32>(t >> 5, lane, raw, tmem, TM_A + (uint32_t)ms * Ly::TA_STAGE,
                                      akc);
-        if (!BOX || rsB == BNMAX)  // the common k-row pitch as a constant: immediate offsets
-          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, BNMAX);
+        if (!BOX || rsB == RB)  // the common k-row pitch as a constant: immediate offsets
+          convert_panel<RB, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, RB);
         else
-          convert_panel<BNMAX, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, rsB);
+          convert_panel<RB, NS, NCV>(t, raw + Ly::RAW_A, st, bkc, rsB);
         // every lane's pieces in Tensor Memory and visible to the tensor
         // core's proxy in shared memory, every lane's raw reads done, then one
         // arrival per warp on each barrier
@@ -647,7 +679,8 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&mma_full[ms]);
+          if constexpr (PAIR) mbar_arrive_cluster(&mma_full[ms], 0);  // the even CTA issues
+          else mbar_arrive(&mma_full[ms]);
           mbar_arrive(&raw_empty[rs]);
         }
       }
@@ -669,19 +702,19 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       }
     };
     int64_t w = item_of(0);
-    if (w < nitems) fetch_rows(get_item(a, sProb, w));
+    if (w < nitems) fetch_rows(get_item<PAIR>(a, sProb, w, crank));
     int64_t gc = 0;  // chunks finished by this CTA
     for (int64_t j = 0;; ++j) {
       // uniform exit; previous rows consumed
       if (bar_or(BAR_EPI, NEPI, *abort || w >= nitems)) break;
-      const Item it = get_item(a, sProb, w);
+      const Item it = get_item<PAIR>(a, sProb, w, crank);
       const DevProblem* d = it.d;
       sRC[t] = pre_r;
 #pragma unroll
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
       w = item_of(j + 1);
       release_item(j);
-      if (w < nitems) fetch_rows(get_item(a, sProb, w));
+      if (w < nitems) fetch_rows(get_item<PAIR>(a, sProb, w, crank));
       bar_sync(BAR_EPI, NEPI);
       const bool have = it.KT > 0;
       // descriptor fields in registers: the stores below could alias them as
@@ -724,15 +757,15 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
         if (have && !*abort) {
-          if (!mbar_wait(&acc_full[0], (uint32_t)(gc & 1), abort)) record_timeout(abort, a.err);
+          if (!mbar_wait<PAIR>(&acc_full[0], (uint32_t)(gc & 1), abort)) record_timeout(abort, a.err);
         }
         tc_fence_after();
         ok = __all_sync(0xffffffffu, !*abort);
         // A short tile (one chunk of at most four k-tiles) is written straight
-        // from the accumulator -- the running sum would be (v, 0), the same
-        // values -- which saves the round trip through the hi and lo words but
-        // holds the accumulator until the stores are issued; for longer tiles
-        // the next tile's MMAs gain more from having it released first.
+        // from the accumulator -- the running sum would hold the same values
+        // -- which saves the round trip through the sum but holds the
+        // accumulator until the stores are issued; for longer tiles the next
+        // tile's MMAs gain more from having it released first.
         const bool direct_out = first && last && it.KT <= 4;
         if (ok && direct_out) {
           for (int cb = 0; cb < bn; cb += 8) {
@@ -743,9 +776,9 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
             out8(cb, v, z);
           }
         } else if (ok) {
-          // fold the chunk into the running sum (hi, lo)
+          // fold the chunk into the running sum
           for (int cb = 0; cb < bn; cb += 8) {
-            float v[8], hi[8], lo[8];
+            float v[8], sum[8];
             if (have) {
               tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
             } else {
@@ -754,36 +787,29 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
             }
             if (first) {
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                hi[q] = v[q];
-                lo[q] = 0.f;
-              }
+              for (int q = 0; q < 8; ++q) sum[q] = v[q];
             } else {
-              tmem_ld8(lane_base + TM_HI + (uint32_t)cb, hi);
-              tmem_ld8(lane_base + TM_LO + (uint32_t)cb, lo);
+              tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                float e;
-                two_sum(hi[q], v[q], hi[q], e);
-                lo[q] = __fadd_rn(lo[q], e);
-              }
+              for (int q = 0; q < 8; ++q) sum[q] = __fadd_rn(sum[q], v[q]);
             }
-            tmem_st8(lane_base + TM_HI + (uint32_t)cb, hi);
-            tmem_st8(lane_base + TM_LO + (uint32_t)cb, lo);
+            tmem_st8(lane_base + TM_SUM + (uint32_t)cb, sum);
           }
           tmem_st_wait();
         }
         // the accumulator is free for the next chunk's MMAs
         tc_fence_before();
-        mbar_arrive(&acc_empty[0]);
+        if constexpr (PAIR) mbar_arrive_cluster(&acc_empty[0], 0);
+        else mbar_arrive(&acc_empty[0]);
         if (!ok) break;
         if (!last || direct_out) continue;  // (a short tile is written above)
         // the tile's output from the running sum
         for (int cb = 0; cb < bn; cb += 8) {
-          float hi[8], lo[8];
-          tmem_ld8(lane_base + TM_HI + (uint32_t)cb, hi);
-          tmem_ld8(lane_base + TM_LO + (uint32_t)cb, lo);
-          out8(cb, hi, lo);
+          float sum[8], z[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[q] = 0.f;
+          tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
+          out8(cb, sum, z);
         }
       }
     }
@@ -796,7 +822,7 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
     if (BOX && lane == 0) {
       int64_t g = 0, g_iss = -1;  // the last k-tile whose boxes were issued
       for (int64_t w = w0; w < nitems && !*abort; w += dw) {
-        const Item it = get_item(a, sProb, w);
+        const Item it = get_item<PAIR>(a, sProb, w, crank);
         const DevProblem* d = it.d;
         const BoxAccess bxA = d->boxA, bxB = d->boxB;
         const CUtensorMap* maps = a.probs ? d->tmaps : a.tm;
@@ -807,7 +833,8 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         const uint32_t bytes = (uint32_t)bxA.bytes + (uint32_t)bxB.bytes;
         int32_t cA[5], cB[5];
         box_coords(bxA, (uint32_t)it.m0, (uint32_t)it.kbeg, cA);
-        box_coords(bxB, (uint32_t)it.n0, (uint32_t)it.kbeg, cB);
+        box_coords(bxB, (uint32_t)(it.n0 + (PAIR ? crank * (uint32_t)(d->bn / 2) : 0u)),
+                   (uint32_t)it.kbeg, cB);
         bool failed = false;
         for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
           const int s = (int)(g % RS);
@@ -842,11 +869,13 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       }
     }
   } else if (lane == 0) {
-    // ---- MMA issue ----
+    // ---- MMA issue (pair form: the even CTA issues for both; the odd one
+    // only waits, before releasing Tensor Memory, for the MMAs writing it) ----
     const uint32_t base = smem_u32(smem + Ly::MMA0);
     int64_t g = 0, gc = 0;
     bool failed = false;
-    if (a.fault == 1) {
+    const bool issuer = !PAIR || crank == 0;
+    if (issuer && a.fault == 1) {
       // injected failure: a bounded wait (about 10 ms) on a barrier nothing
       // arrives on yet; it expires, and the CTA unwinds through the abort path
       if (!mbar_wait(drain, 0, abort, 20000000LL)) {
@@ -854,15 +883,15 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         failed = true;
       }
     }
-    int64_t w = failed ? nitems : item_of(0);
+    int64_t w = (failed || !issuer) ? nitems : item_of(0);
     for (int64_t j = 0; w < nitems && !*abort && !failed; ++j) {
-      const Item it = get_item(a, sProb, w);
+      const Item it = get_item<PAIR>(a, sProb, w, crank);
       w = item_of(j + 1);
       if (dyn) mbar_arrive(&wq_empty[j % QR]);  // (this thread alone reads the queue here)
-      const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)it.d->bn);
+      const uint32_t idesc = idesc_bf16_f32(PAIR ? 2 * BM : BM, (uint32_t)it.d->bn);
       for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
         // the epilogue has folded the accumulator's previous chunk
-        if (gc > 0 && !mbar_wait(&acc_empty[0], (uint32_t)((gc - 1) & 1), abort)) {
+        if (gc > 0 && !mbar_wait<PAIR>(&acc_empty[0], (uint32_t)((gc - 1) & 1), abort)) {
           record_timeout(abort, a.err);
           failed = true;
           break;
@@ -873,7 +902,7 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
           const int ms = (int)(g % MS);
-          if (!mbar_wait(&mma_full[ms], (uint32_t)((g / MS) & 1), abort)) {
+          if (!mbar_wait<PAIR>(&mma_full[ms], (uint32_t)((g / MS) & 1), abort)) {
             record_timeout(abort, a.err);
             failed = true;
             break;
@@ -883,29 +912,45 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
           const uint32_t ta = tmem + TM_A + (uint32_t)ms * Ly::TA_STAGE;
 #pragma unroll
           for (int ksl = 0; ksl < BK / 16; ++ksl) {
-            const uint32_t bo = ksl * 2 * (BNMAX / 8) * 128;
+            const uint32_t bo = ksl * 2 * (RB / 8) * 128;
             uint32_t tA[NS];
             uint64_t dB[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
               tA[i] = ta + (uint32_t)(i * 16 + ksl * 8);
-              dB[i] = smem_desc(st + i * Ly::PB + bo, (BNMAX / 8) * 128, 128);
+              dB[i] = smem_desc(st + i * Ly::PB + bo, (RB / 8) * 128, 128);
             }
-            mma_bf16_ts(acc, tA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
+            auto mma = [&](uint32_t ta_, uint64_t db_, uint32_t accum) {
+              if constexpr (PAIR) mma_bf16_ts2(acc, ta_, db_, idesc, accum);
+              else mma_bf16_ts(acc, ta_, db_, idesc, accum);
+            };
+            mma(tA[0], dB[0], (kt > kt0 || ksl > 0) ? 1u : 0u);
 #pragma unroll
             for (int ts = 1; ts < NS; ++ts)
 #pragma unroll
-              for (int i = 0; i <= ts; ++i) mma_bf16_ts(acc, tA[i], dB[ts - i], idesc, 1u);
+              for (int i = 0; i <= ts; ++i) mma(tA[i], dB[ts - i], 1u);
           }
-          mma_commit(&mma_empty[ms]);
+          if constexpr (PAIR) mma_commit2(&mma_empty[ms], 0x3);  // both CTAs' stages
+          else mma_commit(&mma_empty[ms]);
         }
         if (failed) break;
-        if (kt1 > kt0) mma_commit(&acc_full[0]);
-        else mbar_arrive(&acc_full[0]);  // nothing to accumulate: hand over at once
+        if (kt1 > kt0) {
+          if constexpr (PAIR) mma_commit2(&acc_full[0], 0x3);
+          else mma_commit(&acc_full[0]);
+        } else if constexpr (PAIR) {  // nothing to accumulate: hand over at once
+          mbar_arrive_cluster(&acc_full[0], 0);
+          mbar_arrive_cluster(&acc_full[0], 1);
+        } else {
+          mbar_arrive(&acc_full[0]);
+        }
       }
     }
-    // every MMA this thread issued has completed once this commit arrives
-    mma_commit(drain);
+    // every MMA this thread issued has completed once this commit arrives (in
+    // the pair form on both CTAs' drain barriers)
+    if (issuer) {
+      if constexpr (PAIR) mma_commit2(drain, 0x3);
+      else mma_commit(drain);
+    }
     if (!mbar_wait(drain, 0, abort)) {
       // even on abort, wait for the drain itself (bounded) before releasing TMEM
       const long long t0 = clock64();
@@ -916,9 +961,11 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
 
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs are done with both Tensor Memories
   if (warp == MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc(tmem, TM_COLS);
+    if constexpr (PAIR) tmem_dealloc2(tmem, TM_COLS);
+    else tmem_dealloc(tmem, TM_COLS);
   }
 }
 
@@ -999,14 +1046,15 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
   }
 }
 
-template <int NS, bool BOX>
+template <int NS, bool BOX, bool PAIR>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Lay<NS, BOX>::ALLOC);
+    cudaError_t e = cudaFuncSetAttribute(k_tc<NS, BOX, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Lay<NS, BOX, PAIR>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -1024,16 +1072,36 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
     a.nitems = q.nitems;
     a.tiles_single = 1;
   } else {
-    a.tiles_single = ((q.single.m + BM - 1) / BM) * q.single.tiles_n;
+    const int64_t rows = PAIR ? 2 * BM : BM;  // the pair form's tiles have 256 rows
+    a.tiles_single = ((q.single.m + rows - 1) / rows) * q.single.tiles_n;
     a.nitems = a.tiles_single * q.single.splits;
   }
   if (a.nitems == 0) return cudaSuccess;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
   // dynamic items count from zero in every launch (a memset node under capture)
   if (a.counter && cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
     return cudaGetLastError();
   mainloop_event_before(s);
-  k_tc<NS, BOX><<<(unsigned)grid, nthreads(BOX), Lay<NS, BOX>::ALLOC, s>>>(a);
+  if constexpr (PAIR) {
+    // clusters of two CTAs, one pair per work item at a time
+    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(q.ctas / 2, a.nitems));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+    cfg.blockDim = dim3(nthreads(BOX), 1, 1);
+    cfg.dynamicSmemBytes = Lay<NS, BOX, PAIR>::ALLOC;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc<NS, BOX, PAIR>, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
+    k_tc<NS, BOX, PAIR><<<(unsigned)grid, nthreads(BOX), Lay<NS, BOX, PAIR>::ALLOC, s>>>(a);
+  }
   note_launch();
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
@@ -1061,13 +1129,19 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
 }  // namespace
 
 int tc_bn_max() { return BNMAX; }
+int tc_max_item_ktiles() { return MAX_CHUNKS * CHUNK_KT; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
   // boxes only when every work item has both operands as boxes (the planner
-  // sets both or neither; batch plans set neither)
+  // sets both or neither; batch plans set neither); the pair form only with
+  // boxes planned for it (B boxes half the tile wide)
   const bool box = !q.probs && q.single.boxA.rank > 0 && q.single.boxB.rank > 0;
-  if (q.pieces == 3) return box ? launch_cfg<3, true>(q, s) : launch_cfg<3, false>(q, s);
-  return box ? launch_cfg<2, true>(q, s) : launch_cfg<2, false>(q, s);
+  const bool pair = box && q.single.pair;
+  if (q.pieces == 3)
+    return pair ? launch_cfg<3, true, true>(q, s)
+                : box ? launch_cfg<3, true, false>(q, s) : launch_cfg<3, false, false>(q, s);
+  return pair ? launch_cfg<2, true, true>(q, s)
+              : box ? launch_cfg<2, true, false>(q, s) : launch_cfg<2, false, false>(q, s);
 }
 
 }  // namespace tc

@@ -219,3 +219,26 @@ def test_long_contracted_range_chunked_accumulation(mode):
     got = run(1.0, A, "ip", B, "pj", 0.0, C0, "ij", mode)
     ref, mag = oracle_ref(1.0, A, "ip", B, "pj", 0.0, C0, "ij")
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_long_range_items_are_split(mode):
+    # k = 20000 over 256 output tiles: no split for parallelism, but a work
+    # item folds at most 16 chunks of 1024 terms in its FP32 running sum, so
+    # the range is split in two and the partials are summed compensated
+    g = torch.Generator().manual_seed(23)
+    A = f32(torch.rand(2048, 20000, generator=g, dtype=torch.float64) * 2 - 1)
+    B = f32(torch.rand(20000, 2048, generator=g, dtype=torch.float64) * 2 - 1)
+    dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
+    dC = torch.zeros(2048, 2048, dtype=torch.float32, device="cuda")
+    tc.contract(dA, "ip", dB, "pj", dC, "ij", mode=mode)
+    torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    got = dC.cpu().double().numpy()
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([[0, 2047], rng.integers(0, 2048, 30)])
+    a, b = A.numpy(), B.numpy()
+    for r in rows:
+        c = np.zeros((1, 2048))
+        mag = oracle.contract_(1.0, a[r:r + 1], "ip", b, "pj", 0.0, c, "ij")
+        assert norm_err(got[r:r + 1], c, mag) <= TOLS[mode], r
