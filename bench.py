@@ -1160,10 +1160,15 @@ def secondary_configs(args, ws, rank, local):
             ("spiky_f32_f64", "spiky_f32", "f64"), ("grad_f32_bf16x3", "grad_f32", "bf16x3"),
             ("batch512_bf16x3", "batch512", "bf16x3"), ("batch512_f64", "batch512", "f64"),
             ("tccg_bf16x3", "tccg", "bf16x3"), ("tccg_f64", "tccg", "f64")]
+    # steps per entry: a timed region of about 0.1-0.5 s each (a few milliseconds would
+    # measure the host's start-up of the clock sampler rather than the step)
+    steps = {"spiky_f32_bf16x3": 200, "spiky_f32_bf16x6": 200, "spiky_f32_f64": 3,
+             "grad_f32_bf16x3": 200, "batch512_bf16x3": 50, "batch512_f64": 3,
+             "tccg_bf16x3": 10, "tccg_f64": 3}
     for key, wl, mode in runs:
         a = copy.copy(args)
         a.workload, a.mode, a.lean = wl, mode, True
-        a.steps = min(args.steps, 3 if mode == "f64" else 10)
+        a.steps = steps[key]
         a.warmup = 3
         a.no_ttgt = a.no_cpu_baseline = True
         a.profile = False
