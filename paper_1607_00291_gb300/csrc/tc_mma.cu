@@ -165,6 +165,7 @@ struct Args {
   int fault;  // 1: injected timeout (see TcLaunch::fault)
   unsigned long long* counter;  // batch: the shared work counter (dynamic items), or null
   const int32_t* gate;  // checked launch: no work if *gate == kDevBounds (or null)
+  int dbuf;  // every work item is one chunk: alternate two accumulators (see the epilogue)
 };
 
 __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err) {
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
   uint64_t* raw_empty = raw_full + RS;
   uint64_t* mma_full = raw_empty + RS;
   uint64_t* mma_empty = mma_full + MS;
-  uint64_t* acc_full = mma_empty + MS;  // [1] used (two reserved)
+  uint64_t* acc_full = mma_empty + MS;  // [0], and [1] with two accumulators
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
@@ -756,24 +757,43 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       };
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
+        // two accumulators (every item one chunk): the running-sum columns
+        // serve as the second, and items alternate between them
+        const int buf = a.dbuf ? (int)(gc & 1) : 0;
+        const uint32_t use = (uint32_t)(a.dbuf ? gc >> 1 : gc);  // earlier uses of buf
         if (have && !*abort) {
-          if (!mbar_wait<PAIR>(&acc_full[0], (uint32_t)(gc & 1), abort)) record_timeout(abort, a.err);
+          if (!mbar_wait<PAIR>(&acc_full[buf], use & 1u, abort)) record_timeout(abort, a.err);
         }
         tc_fence_after();
         ok = __all_sync(0xffffffffu, !*abort);
-        // A short tile (one chunk of at most four k-tiles) is written straight
-        // from the accumulator -- the running sum would hold the same values
-        // -- which saves the round trip through the sum but holds the
-        // accumulator until the stores are issued; for longer tiles the next
+        // A short tile (one chunk of at most four k-tiles), or any tile when
+        // there are two accumulators, is written straight from its
+        // accumulator -- the running sum would hold the same values -- which
+        // saves the round trip through the sum; with one accumulator that
+        // holds it until the stores are issued, and for longer tiles the next
         // tile's MMAs gain more from having it released first.
-        const bool direct_out = first && last && it.KT <= 4;
+        const bool direct_out = a.dbuf || (first && last && it.KT <= 4);
         if (ok && direct_out) {
-          for (int cb = 0; cb < bn; cb += 8) {
-            float v[8], z[8];
+          // 16 columns per Tensor Memory load and wait (bn is a multiple of 16)
+          const uint32_t accc = buf ? TM_SUM : TM_ACC;
+          float z[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = z[q] = 0.f;
-            if (have) tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
-            out8(cb, v, z);
+          for (int q = 0; q < 8; ++q) z[q] = 0.f;
+          for (int cb = 0; cb < bn; cb += 16) {
+            float v[16];
+            if (have) {
+              tmem_ld16(lane_base + accc + (uint32_t)cb, v);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+#pragma unroll
+            for (int p8 = 0; p8 < 2; ++p8) {
+              float v8[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v8[q] = v[8 * p8 + q];
+              out8(cb + 8 * p8, v8, z);
+            }
           }
         } else if (ok) {
           // fold the chunk into the running sum
@@ -799,8 +819,8 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         }
         // the accumulator is free for the next chunk's MMAs
         tc_fence_before();
-        if constexpr (PAIR) mbar_arrive_cluster(&acc_empty[0], 0);
-        else mbar_arrive(&acc_empty[0]);
+        if constexpr (PAIR) mbar_arrive_cluster(&acc_empty[buf], 0);
+        else mbar_arrive(&acc_empty[buf]);
         if (!ok) break;
         if (!last || direct_out) continue;  // (a short tile is written above)
         // the tile's output from the running sum
@@ -890,14 +910,16 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
       if (dyn) mbar_arrive(&wq_empty[j % QR]);  // (this thread alone reads the queue here)
       const uint32_t idesc = idesc_bf16_f32(PAIR ? 2 * BM : BM, (uint32_t)it.d->bn);
       for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
-        // the epilogue has folded the accumulator's previous chunk
-        if (gc > 0 && !mbar_wait<PAIR>(&acc_empty[0], (uint32_t)((gc - 1) & 1), abort)) {
+        const int buf = a.dbuf ? (int)(gc & 1) : 0;
+        const int64_t use = a.dbuf ? gc >> 1 : gc;  // earlier uses of this accumulator
+        // the epilogue has read (or folded) this accumulator's previous chunk
+        if (use > 0 && !mbar_wait<PAIR>(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
           record_timeout(abort, a.err);
           failed = true;
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + TM_ACC;
+        const uint32_t acc = tmem + (buf ? TM_SUM : TM_ACC);
         const int64_t kt0 = (int64_t)ch * CHUNK_KT;
         const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
         for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
@@ -935,13 +957,13 @@ __global__ void __launch_bounds__(nthreads(BOX), 1) k_tc(const __grid_constant__
         }
         if (failed) break;
         if (kt1 > kt0) {
-          if constexpr (PAIR) mma_commit2(&acc_full[0], 0x3);
-          else mma_commit(&acc_full[0]);
+          if constexpr (PAIR) mma_commit2(&acc_full[buf], 0x3);
+          else mma_commit(&acc_full[buf]);
         } else if constexpr (PAIR) {  // nothing to accumulate: hand over at once
-          mbar_arrive_cluster(&acc_full[0], 0);
-          mbar_arrive_cluster(&acc_full[0], 1);
+          mbar_arrive_cluster(&acc_full[buf], 0);
+          mbar_arrive_cluster(&acc_full[buf], 1);
         } else {
-          mbar_arrive(&acc_full[0]);
+          mbar_arrive(&acc_full[buf]);
         }
       }
     }
@@ -1068,6 +1090,8 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   a.fault = q.fault;
   a.counter = q.probs && !BOX ? q.counter : nullptr;
   a.gate = q.gate;
+  // a single problem whose every work item is one accumulation chunk
+  a.dbuf = !q.probs && q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0;
   if (q.probs) {
     a.nitems = q.nitems;
     a.tiles_single = 1;
