@@ -1,6 +1,7 @@
 // libtc C ABI: argument checks, planning, workspace carving and launches.
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -47,6 +48,11 @@ int32_t* err_word() {
 }
 
 size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : 4; }
+
+bool log_enabled() {
+  const char* e = std::getenv("TC_LOG");
+  return e && e[0] == '1';
+}
 
 int check_modes(tc_dtype dt, tc_mode mode) {
   if (dt != TC_F64 && dt != TC_F32) return TC_ERR_ARG;
@@ -210,6 +216,15 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     q.ctas = sm_count();
     q.err = err_word();
     q.gate = gate;
+    if (log_enabled())
+      std::fprintf(stderr,
+                   "[libtc] contract: %s data, %s, m=%lld n=%lld k=%lld, tile %dx%d, %d k-split(s), "
+                   "access %s%s%s\n",
+                   dt == TC_F64 ? "f64" : "f32", mode == TC_MODE_BF16X6 ? "bf16x6" : "bf16x3",
+                   (long long)L.m, (long long)L.n, (long long)L.k, d.pair ? 256 : 128, d.bn,
+                   d.splits, d.boxA.rank > 0 ? "TMA boxes" : d.elem_gather ? "element gathers"
+                                                                           : "block gathers",
+                   d.pair ? " on CTA pairs" : "", gate ? ", checked" : "");
     // TC_FAULT=timeout: test hook that makes the kernel's first wait expire
     if (const char* f = std::getenv("TC_FAULT")) q.fault = std::strcmp(f, "timeout") == 0 ? 1 : 0;
     return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
@@ -232,6 +247,14 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   f.max_ctas = sm_count();
   f.err = err_word();
   f.gate = gate;
+  if (log_enabled())
+    std::fprintf(stderr, "[libtc] contract: %s data, f64, m=%lld n=%lld k=%lld, %s%s\n",
+                 dt == TC_F64 ? "f64" : "f32", (long long)L.m, (long long)L.n, (long long)L.k,
+                 f64_grid(L.m, L.n, L.k, f.max_ctas, f.partial != nullptr) ==
+                         f64_grid(L.m, L.n, L.k, 0, false)
+                     ? "plain tiling"
+                     : "stream-K over one CTA per SM",
+                 gate ? ", checked" : "");
   return launch_f64(f, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
@@ -285,6 +308,7 @@ int tc_workspace_size(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc
 int tc_contract(tc_dtype dtype, tc_mode mode, double alpha, const tc_tensor* A,
                 const tc_tensor* B, double beta, const tc_tensor* C, void* workspace,
                 size_t ws_bytes, void* stream) {
+  NvtxRange range("tc_contract");
   int rc = check_modes(dtype, mode);
   if (rc != TC_OK) return rc;
   Planned p;

@@ -604,19 +604,17 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   }
   pl->nitems = (int64_t)items.size();
   pl->n_split = (int32_t)splitp.size();
-  if (const char* lg = std::getenv("TC_LOG")) {
-    if (lg[0] == '1') {
-      std::map<std::pair<int, int>, int> tiles;
-      double ksteps = 0;
-      for (const WorkItem& w : items) ksteps += item_cost(w);
-      for (int i = 0; i < np; ++i) tiles[{pl->cfg[i].bm, pl->cfg[i].bn}]++;
-      std::fprintf(stderr, "[libtc] batch plan: %d problems, %lld work items, %d split, "
-                   "%.3g k-index-units of work; tiles (m x n: problems):", np,
-                   (long long)pl->nitems, pl->n_split, ksteps);
-      for (const auto& kv : tiles)
-        std::fprintf(stderr, " %dx%d: %d", kv.first.first, kv.first.second, kv.second);
-      std::fprintf(stderr, "\n");
-    }
+  if (log_enabled()) {
+    std::map<std::pair<int, int>, int> tiles;
+    double ksteps = 0;
+    for (const WorkItem& w : items) ksteps += item_cost(w);
+    for (int i = 0; i < np; ++i) tiles[{pl->cfg[i].bm, pl->cfg[i].bn}]++;
+    std::fprintf(stderr, "[libtc] batch plan: %d problems, %lld work items, %d split, "
+                 "%.3g k-index-units of work; tiles (m x n: problems):", np,
+                 (long long)pl->nitems, pl->n_split, ksteps);
+    for (const auto& kv : tiles)
+      std::fprintf(stderr, " %dx%d: %d", kv.first.first, kv.first.second, kv.second);
+    std::fprintf(stderr, "\n");
   }
 
   const size_t es = f64 ? sizeof(double) : sizeof(float);
@@ -769,6 +767,7 @@ extern "C" {
 
 int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
                    tc_plan** out) {
+  NvtxRange range("tc_plan_create");
   if (!out || count < 0 || (count > 0 && !probs)) return TC_ERR_ARG;
   int rc = check_modes(dtype, mode);
   if (rc != TC_OK) return rc;
@@ -833,6 +832,7 @@ int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes) {
 }
 
 int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+  NvtxRange range("tc_plan_execute");
   (void)workspace;
   (void)ws_bytes;
   if (!plan) return TC_ERR_ARG;

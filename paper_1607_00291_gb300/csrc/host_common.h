@@ -3,10 +3,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only: the ranges cost nothing without a profiler
 
 #include "tc_internal.h"
 
 namespace tc {
+
+// A named NVTX range around an entry point's host work and launches (visible
+// in timeline profilers; inert otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// TC_LOG=1: one line per contraction or plan on stderr describing its plan.
+bool log_enabled();
 
 // Device error word of the current device (looked up once per device).
 int32_t* err_word();

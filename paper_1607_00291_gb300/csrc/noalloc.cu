@@ -56,6 +56,7 @@ int scratch_on_current_device(int64_t** out) {
 extern "C" int tc_contract_noalloc(tc_dtype dtype, double alpha, const tc_tensor* A,
                                    const tc_tensor* B, double beta, const tc_tensor* C,
                                    void* stream) {
+  NvtxRange range("tc_contract_noalloc");
   if (dtype != TC_F64 && dtype != TC_F32) return TC_ERR_ARG;
   Planned p;
   int rc = plan_problem(A, B, C, &p);
