@@ -220,12 +220,20 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
   // run.  For J and B this costs little: after step 4 C's unit stride lies
   // in I, and the epilogue's threads run along I (each store instruction
   // still covers whole lines; only the distance between a tile's columns
-  // grows), and ordering J by C instead can cost B its box form.  For I and A it moves C's
-  // unit-stride dim away from the epilogue's threads; A is read once per
-  // output tile across from it, about k / 128 times C's traffic, so I is
-  // re-sorted only for k >= 512.
-  int64_t kprod = 1;
+  // grows), and ordering J by C instead can cost B its box form.  For I and A
+  // it moves C's unit-stride dim away from the epilogue's threads: every
+  // store of C then lands in its own sector, where otherwise every load of A
+  // does.  A is read once per output tile across from it (about k x
+  // ceil(n / 128) loads per row against n stores), and a scattered store
+  // costs about two and a half scattered loads (measured), so I is sorted by
+  // A's strides only when k ceil(n / 128) >= 2.5 n.  Otherwise A's
+  // smallest-stride dim moves up to second place, right after C's: a tile's
+  // rows then span C's first dim and a few steps of A's, so the tiles that
+  // run side by side read every sector of A whole between them (from L2)
+  // instead of one element of it each.
+  int64_t kprod = 1, nprod = 1;
   for (int i = 0; i < nP; ++i) kprod *= P[i].len;
+  for (int i = 0; i < nJ; ++i) nprod *= J[i].len;
   {
     int64_t minAP = INT64_MAX, minAI = INT64_MAX, minBP = INT64_MAX, minBJ = INT64_MAX;
     for (int i = 0; i < nP; ++i) {
@@ -234,8 +242,21 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
     }
     for (int i = 0; i < nI; ++i) minAI = std::min<int64_t>(minAI, std::llabs(I[i].s0));
     for (int i = 0; i < nJ; ++i) minBJ = std::min<int64_t>(minBJ, std::llabs(J[i].s0));
-    if (kprod >= 512 && nI > 0 && minAI <= minAP)
-      stable_sort(I, nI, [](const LDim& x) { return std::llabs(x.s0); });
+    if (nI > 0 && minAI <= minAP) {
+      const double loads = (double)kprod * (double)((nprod + 127) / 128);
+      if (2.0 * loads >= 5.0 * (double)nprod) {
+        stable_sort(I, nI, [](const LDim& x) { return std::llabs(x.s0); });
+      } else {
+        int u = 0;
+        for (int i = 1; i < nI; ++i)
+          if (std::llabs(I[i].s0) < std::llabs(I[u].s0)) u = i;
+        if (u > 1) {
+          const LDim t = I[u];
+          for (int i = u; i > 1; --i) I[i] = I[i - 1];
+          I[1] = t;
+        }
+      }
+    }
     if (nJ > 0 && minBJ <= minBP) stable_sort(J, nJ, [](const LDim& x) { return std::llabs(x.s0); });
   }
 
