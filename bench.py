@@ -45,10 +45,13 @@ def parse():
                     choices=sorted(W.SPECS) + ["batch512", "tccg"] + sorted(W.PAPER_SHAPES))
     ap.add_argument("--mode", choices=["f64", "bf16x3", "bf16x6"], default=None,
                     help="override the workload's arithmetic")
-    ap.add_argument("--access", choices=["box", "block", "scatter"], default="box",
-                    help="tensor-core operand access: TMA boxes where tiles are boxes and "
+    ap.add_argument("--access", choices=["auto", "box", "block", "scatter", "packed"],
+                    default="auto",
+                    help="tensor-core operand access: the library's choice (auto), TMA boxes "
+                         "where tiles are boxes and "
                          "block-scatter gathers elsewhere (box), block-scatter gathers only "
-                         "(block), or element gathers only (scatter)")
+                         "(block), element gathers only (scatter), or both operands packed "
+                         "once before the mainloop (packed)")
     ap.add_argument("--profile", action="store_true",
                     help="after the timed region, run one more step between cudaProfilerStart "
                          "and cudaProfilerStop (for ncu --profile-from-start off)")
@@ -177,6 +180,23 @@ def profiled_step(args, fn):
     fn()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
+
+
+KERNELS = {"packed": "k_pack+k_tcp", "gather": "k_tc", "box": "k_tc", "pair": "k_tc"}
+
+
+def tc_forms(calls, mode):
+    """The tensor-core mainloop form of each call (A, labA, B, labB, C, labC,
+    ...) under the current settings, or None in the FP64 mode."""
+    if mode == "f64":
+        return None
+    return [tc.operand_form(c[0], c[1], c[2], c[3], c[4], c[5], mode) for c in calls]
+
+
+def kernel_name(mode, forms):
+    if mode == "f64":
+        return "k_f64"
+    return "+".join(sorted({KERNELS[f] for f in forms}))
 
 
 def traffic_for(kernel: str, workload: str):
@@ -709,7 +729,10 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
                                 "peak": round(peak_v, 5), "frac": round(ach / peak_v, 4), "peak_source": src,
                                 "algorithmic": f"{flops:.4g} flops per step"
                                                + (f" (x{prods} bf16 products)" if mode != "f64" else "")}
-        kname = "k_f64" if mode == "f64" else "k_tc"
+        forms = tc_forms(calls, mode)
+        kname = kernel_name(mode, forms)
+        if forms:
+            line["forms"] = forms
         line["roofline"].update({"kernel": kname, "kernel_ms": round(kms, 4), "kernel_ms_per_call": per_call,
                                  "traffic": traffic_for(kname, getattr(args, "traffic_key", ""))})
         line["call_ms"] = call_ms
@@ -747,7 +770,8 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / ek, ws)
 
     prods = 1 if mode == "f64" else (3 if mode == "bf16x3" else 6)
-    kname = "k_f64" if mode == "f64" else "k_tc"
+    forms = tc_forms(calls, mode)
+    kname = kernel_name(mode, forms)
     if hbm_bytes is not None:
         mp = measured_peaks()
         peak_v = mp.get("hbm_gbs", 6800.0)
@@ -889,17 +913,39 @@ def run_tccg(args, ws, rank, local):
                      flops=flops, mode=mode, desc=desc, cfg_extra=extra,
                      cpu=None if lean else (spec0, host(0), 0), checks=checks)
     call_ms = line.get("call_ms") or line["roofline"].get("call_ms")
+    kms = line["roofline"].get("kernel_ms_per_call") or call_ms
     tt = (line.get("ttgt") or {}).get("ms_per_problem")
-    rows = []
+    # each string's floor: its algorithmic bytes (A and B read once, C written
+    # once) at the measured copy bandwidth, or its products at the pipe's peak
+    mp = measured_peaks()
+    hbm_peak = mp.get("hbm_gbs", 6800.0)
+    es = 8 if mode == "f64" else 4
+    if mode == "f64":
+        pipe_peak, prods = fp64_peak_tflops(), 1
+    else:
+        pipe_peak, prods = mp.get("bf16_tflops", 1900.0), (3 if mode == "bf16x3" else 6)
+    rows, floor_sum = [], 0.0
     for i, (s_, p) in enumerate(zip(W.TCCG_STRINGS, probs)):
-        r = {"string": s_, "extent": p.ext[p.labC[0]], "ms": call_ms[i],
+        nbytes = es * sum(int(np.prod([p.ext[x] for x in lab])) for lab in (p.labA, p.labB, p.labC))
+        t_hbm = nbytes / (hbm_peak * 1e9) * 1e3
+        t_pipe = prods * p.flops() / (pipe_peak * 1e12) * 1e3
+        floor = max(t_hbm, t_pipe)
+        floor_sum += floor
+        r = {"string": s_, "extent": p.ext[p.labC[0]], "ms": call_ms[i], "kernel_ms": kms[i],
              "tflops": round(p.flops() / (call_ms[i] * 1e-3) / 1e12, 4),
+             "bound": "hbm" if t_hbm >= t_pipe else "tensor", "floor_ms": round(floor, 4),
+             "floor_over_kernel": round(floor / kms[i], 4),
              "paper_bsmtc_1core_gflops": PAPER_BSMTC_1CORE_GFLOPS[i]}
         if tt:
             r["ttgt_ms"] = tt[i]
             r["ttgt_time_over_ours"] = round(tt[i] / call_ms[i], 3)
         rows.append(r)
     line["per_string"] = rows
+    line["floors"] = {"sum_floor_ms": round(floor_sum, 4), "sum_kernel_ms": round(sum(kms), 4),
+                      "frac": round(floor_sum / sum(kms), 4),
+                      "note": "per string the larger of its HBM floor (MEASURED_PEAKS.json hbm_gbs) "
+                              "and its pipe floor; most strings are HBM-bound, so the line's "
+                              "tensor-pipe fraction understates them"}
     return line
 
 
@@ -1007,7 +1053,9 @@ def run_ours(args, ws, rank, local):
     err_code = tc.device_error()
     if lean:
         prods = 1 if spec.mode == "f64" else (3 if spec.mode == "bf16x3" else 6)
-        kname = "k_f64" if spec.mode == "f64" else "k_tc"
+        form = None if spec.mode == "f64" else tc.operand_form(dA, spec.labA, dB, spec.labB, dC,
+                                                               spec.labC, spec.mode)
+        kname = "k_f64" if spec.mode == "f64" else KERNELS[form]
         if spec.mode == "f64":
             peak_v, src = fp64_peak_tflops(), "cuBLAS DGEMM 4096^3 measured in this run"
         else:
@@ -1025,8 +1073,7 @@ def run_ours(args, ws, rank, local):
                              "algorithmic": f"{flops:.4g} flops per launch"
                                             + (f" (x{prods} bf16 products)" if spec.mode != "f64" else "")}}
         if spec.mode != "f64":
-            fa, fb = tc.box_access(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.mode)
-            line["operand_access"] = f"A {'TMA box' if fa else 'gather'}, B {'TMA box' if fb else 'gather'}"
+            line["operand_access"] = form
         if rank == 0:
             dC.copy_(C0)
             step()
@@ -1081,15 +1128,16 @@ def run_ours(args, ws, rank, local):
         peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if mp else "fallback 1.9 PFLOP/s bf16"
         prods = 3 if spec.mode == "bf16x3" else 6
         bound, unit, ach = "tensor", "TFLOP/s", prods * flops / (kms_max * 1e-3) / 1e12
-        kname = "k_tc"
+        kname = KERNELS[tc.operand_form(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.mode)]
     value = ws * flops / (ms_max * 1e-3) / 1e12
     extra = {"l2": f"inputs larger than L2 (A = {host_bytes(spec)[0] / 1e6:.1f} MB > {L2_BYTES / 1e6:.0f} MB)",
              "parallelism": f"replicas x{ws}"}
     if spec.mode != "f64":
-        fa, fb = tc.box_access(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.mode)
-        how = {"block": "block-scatter gather", "scatter": "element gather", "box": "block-scatter gather"}
-        extra["operand_access"] = (f"{args.access}: A {'TMA box' if fa else how[args.access]}, "
-                                   f"B {'TMA box' if fb else how[args.access]}")
+        form = tc.operand_form(dA, spec.labA, dB, spec.labB, dC, spec.labC, spec.mode)
+        how = {"gather": "A and B gathered through their scatter vectors",
+               "box": "A and B TMA boxes", "pair": "A and B TMA boxes on CTA pairs",
+               "packed": "A and B packed once (k_pack), then streamed by bulk copies (k_tcp)"}
+        extra["operand_access"] = f"{args.access}: {how[form]}"
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": ws, "steps": K,
         "warmup": warm, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
@@ -1236,7 +1284,7 @@ def main():
         tc.set_access(args.access)
         line = run_ours(args, ws, rank, local)
         if args.workload == "cc4x4_f64" and not args.no_configs and args.mode is None \
-                and args.access == "box":
+                and args.access == "auto":
             line["configs"] = secondary_configs(args, ws, rank, local)
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -196,7 +196,13 @@ TC_API void tc_plan_destroy(tc_plan* plan);
 /* How the tensor-core mainloop (BF16X3 / BF16X6 modes) reads A and B into
  * shared memory.  Results are identical, bit for bit, in every setting; only
  * the speed differs.
- * TC_ACCESS_BOX (default): when, for both A and B, the tile rows and a k-tile
+ * TC_ACCESS_AUTO (default): the packed form (below) for single contractions
+ * of at least 2^26 multiply-adds (m n k) unless both operands are boxes and
+ * one of them is read by a single row or column of output tiles (packing
+ * would add a write and a read of it and save nothing: a box reads it at
+ * full speed); otherwise as TC_ACCESS_BOX.  tc_operand_form reports the
+ * choice.
+ * TC_ACCESS_BOX: when, for both A and B, the tile rows and a k-tile
  * form one box in the operand's own dims -- its unit-stride dim leads the row
  * or the k bundle, the bundle dims before the one a tile ends in are covered
  * whole, and that dim's tile extent divides its length (the last dim of a
@@ -212,13 +218,26 @@ TC_API void tc_plan_destroy(tc_plan* plan);
  * TC_ACCESS_SCATTER: the same gathers one element at a time, ignoring the
  * block-scatter vectors: the paper's plain scatter-matrix form, kept for
  * comparison.
+ * TC_ACCESS_PACKED: single contractions first pack A and B, once each,
+ * through their scatter vectors into bf16 pieces laid out as the tensor core
+ * reads them (the packing of BLIS that Sections 5-6 build on: every element
+ * gathered once instead of once per output tile across from it); the
+ * mainloop then streams the packed units with bulk copies.  The workspace
+ * grows by about the bytes of A and B (tc_workspace_size reports it).
+ * Batches gather as in TC_ACCESS_BLOCK.
  * The FP64 mode always uses the BLOCK form.  The setting is process-wide and
  * read when a contraction is issued or a plan is created; it is not tied to
  * any thread or stream, so a host thread that changes it while another issues
  * contractions races with that thread (either setting may apply to a call
  * issued meanwhile): set it once at start-up, or serialise.  Returns the
  * previous setting, or TC_ERR_ARG for an unknown value. */
-typedef enum { TC_ACCESS_BOX = 0, TC_ACCESS_BLOCK = 1, TC_ACCESS_SCATTER = 2 } tc_access;
+typedef enum {
+  TC_ACCESS_BOX = 0,
+  TC_ACCESS_BLOCK = 1,
+  TC_ACCESS_SCATTER = 2,
+  TC_ACCESS_PACKED = 3,
+  TC_ACCESS_AUTO = 4
+} tc_access;
 TC_API int tc_set_access(int access);
 
 /* How the tensor-core path sums the FP32 partial results of a contracted
@@ -244,6 +263,16 @@ TC_API int tc_set_split_reduction(int reduce);
  * are then gathered).  TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
 TC_API int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
                          const tc_tensor* C, int32_t* a_box, int32_t* b_box);
+
+/* The form the tensor-core mainloop will take for this contraction under the
+ * current settings (tc_set_access, TC_PAIR): *form = TC_FORM_GATHER (both
+ * operands gathered through their scatter vectors), TC_FORM_BOX (both TMA
+ * boxes, one CTA per tile), TC_FORM_PAIR (boxes on CTA pairs) or
+ * TC_FORM_PACKED (both packed before the mainloop).  Host only.
+ * TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
+typedef enum { TC_FORM_GATHER = 0, TC_FORM_BOX = 1, TC_FORM_PAIR = 2, TC_FORM_PACKED = 3 } tc_form;
+TC_API int tc_operand_form(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                           const tc_tensor* C, int32_t* form);
 
 /* ---- scatter vectors (K1 on its own; used by the tests) ------------------------ */
 

@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import TcError  # noqa: F401
 
 __all__ = ["contract", "workspace_size", "plan_describe", "build_scatter", "device_error",
-           "set_access", "access", "box_access", "set_split_reduction", "set_checks", "checks", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
+           "set_access", "access", "box_access", "operand_form", "set_split_reduction", "set_checks", "checks", "TcError", "TcContract", "contract_autograd", "Plan", "contract_batched"]
 
 _MODES = {"f64": L.TC_MODE_F64, "bf16x3": L.TC_MODE_BF16X3, "bf16x6": L.TC_MODE_BF16X6}
 
@@ -109,16 +109,23 @@ def plan_describe(A, labA, B, labB, C, labC) -> dict:
                 c_m_contig=bool(info.c_m_contig))
 
 
-_ACCESS = {"block": L.TC_ACCESS_BLOCK, "scatter": L.TC_ACCESS_SCATTER, "box": L.TC_ACCESS_BOX}
+_ACCESS = {"block": L.TC_ACCESS_BLOCK, "scatter": L.TC_ACCESS_SCATTER, "box": L.TC_ACCESS_BOX,
+           "packed": L.TC_ACCESS_PACKED, "auto": L.TC_ACCESS_AUTO}
 
 
 def set_access(access: str) -> str:
     """Operand access of the tensor-core mainloop, process-wide (results are
-    identical in every setting): "box" (default) loads every operand whose
-    tiles are boxes in its own dims with TMA and block-gathers the rest;
+    identical in every setting): "auto" (default) takes the packed form
+    for large single contractions unless a box operand read by one row or
+    column of tiles makes packing useless, else as "box"; "box" loads every
+    operand whose tiles are boxes in its own dims with TMA and block-gathers
+    the rest;
     "block" gathers every operand through the scatter vectors, 16 bytes at a
     time where the block-scatter vectors allow; "scatter" gathers element by
-    element (the plain scatter-matrix form).  Returns the previous setting."""
+    element (the plain scatter-matrix form); "packed" packs A and B once
+    each into bf16 pieces in the tensor core's layout before the mainloop
+    (single contractions; batches gather as with "block").  Returns the
+    previous setting."""
     if access not in _ACCESS:
         raise ValueError(f"access must be one of {sorted(_ACCESS)}")
     prev = L.lib().tc_set_access(_ACCESS[access])
@@ -186,7 +193,7 @@ class checks:
 def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):
     """(a_box, b_box): whether tc_contract in tensor-core `mode` loads the
     matrix-role operands A and B as TMA boxes (True) or gathers them (False)
-    under the current access setting (only "box", the default, takes boxes).  Host only; A, B, C are tensors or
+    under the current access setting (only "box" and "auto" take boxes).  Host only; A, B, C are tensors or
     (shape, strides) pairs (pairs are taken as 16-byte aligned)."""
     keep = []
 
@@ -199,6 +206,26 @@ def box_access(A, labA, B, labB, C, labC, mode: str = "bf16x3"):
     L.check(L.lib().tc_box_access(L.TC_F32, _mode_code(mode), d(A, labA), d(B, labB), d(C, labC),
                                   a, b), "tc_box_access")
     return bool(a.value), bool(b.value)
+
+
+_FORMS = {0: "gather", 1: "box", 2: "pair", 3: "packed"}
+
+
+def operand_form(A, labA, B, labB, C, labC, mode: str = "bf16x3") -> str:
+    """The form tc_contract in tensor-core `mode` takes under the current
+    settings: "gather", "box", "pair" (boxes on CTA pairs) or "packed".
+    Host only; arguments as for box_access."""
+    keep = []
+
+    def d(x, lab):
+        if isinstance(x, torch.Tensor):
+            return L.make_tensor(tuple(x.shape), x.stride(), lab, x.data_ptr(), keep)
+        return L.make_tensor(x[0], x[1], lab, 0, keep)
+
+    f = L.c_i32(0)
+    L.check(L.lib().tc_operand_form(L.TC_F32, _mode_code(mode), d(A, labA), d(B, labB), d(C, labC),
+                                    f), "tc_operand_form")
+    return _FORMS[f.value]
 
 
 def build_scatter(A, labA, B, labB, C, labC, b: int = 4):

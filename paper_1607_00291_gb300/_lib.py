@@ -10,7 +10,7 @@ MAX_RANK = 16
 
 TC_F64, TC_F32 = 0, 1
 TC_MODE_F64, TC_MODE_BF16X3, TC_MODE_BF16X6 = 0, 1, 2
-TC_ACCESS_BOX, TC_ACCESS_BLOCK, TC_ACCESS_SCATTER = 0, 1, 2
+TC_ACCESS_BOX, TC_ACCESS_BLOCK, TC_ACCESS_SCATTER, TC_ACCESS_PACKED, TC_ACCESS_AUTO = 0, 1, 2, 3, 4
 TC_REDUCE_COMPENSATED, TC_REDUCE_F64 = 0, 1
 TC_OK = 0
 STATUS = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_LABEL", -3: "TC_ERR_EXTENT", -4: "TC_ERR_OVERLAP",
@@ -62,6 +62,8 @@ SIGNATURES = {
     "tc_set_checks": (c_i32, [c_i32]),
     "tc_box_access": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
                       [ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "tc_operand_form": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
+                        [ctypes.POINTER(c_i32)]),
     "tc_set_mainloop_events": (c_i32, [c_vp, c_vp]),
     "tc_launch_count": (ctypes.c_uint64, []),
     "tc_status_string": (ctypes.c_char_p, [c_i32]),

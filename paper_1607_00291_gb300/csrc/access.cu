@@ -33,7 +33,7 @@
 namespace tc {
 namespace {
 
-std::atomic<int> g_access{TC_ACCESS_BOX};
+std::atomic<int> g_access{TC_ACCESS_AUTO};
 
 constexpr int kTileK = 32;  // k-tile of the tensor-core mainloop
 constexpr int kTileM = 128; // rows of an A tile
@@ -169,7 +169,9 @@ void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_b
   d.pair = 0;
   const int acc = g_access.load();
   d.elem_gather = acc == TC_ACCESS_SCATTER ? 1 : 0;
-  if (!allow_box || acc != TC_ACCESS_BOX || L.m <= 0 || L.n <= 0 || L.k <= 0) return;
+  if (!allow_box || (acc != TC_ACCESS_BOX && acc != TC_ACCESS_AUTO) || L.m <= 0 || L.n <= 0 ||
+      L.k <= 0)
+    return;
   // both operands or neither: with one operand boxed and the other gathered
   // the kernel would need loader warps and the box warp on one stage, which
   // measured slower than gathering both
@@ -208,8 +210,13 @@ extern "C" int tc_set_split_reduction(int reduce) {
   return tc::g_reduce.exchange(reduce);
 }
 
+namespace tc {
+int access_setting() { return g_access.load(); }
+}  // namespace tc
+
 extern "C" int tc_set_access(int access) {
-  if (access != TC_ACCESS_BLOCK && access != TC_ACCESS_SCATTER && access != TC_ACCESS_BOX)
+  if (access != TC_ACCESS_BLOCK && access != TC_ACCESS_SCATTER && access != TC_ACCESS_BOX &&
+      access != TC_ACCESS_PACKED && access != TC_ACCESS_AUTO)
     return TC_ERR_ARG;
   return tc::g_access.exchange(access);
 }

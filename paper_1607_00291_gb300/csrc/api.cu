@@ -126,9 +126,51 @@ void plan_single_access(const Layout& L, DevProblem& d, CUtensorMap* maps, int s
 struct WsLayout {
   size_t scatter_off, scatter_bytes;
   size_t partial_off, partial_bytes;
+  size_t pack_off, pack_bytes;  // packed form: the packed units of A and B
   size_t total;
   TcChoice tcc;
 };
+
+// A problem's descriptor fields that the access plan reads.
+DevProblem access_problem(const Planned& p, const TcChoice& c) {
+  DevProblem d;
+  std::memset(&d, 0, sizeof d);
+  d.a = p.a;
+  d.b = p.b;
+  d.a_kc = p.info.a_k_contig;
+  d.b_kc = p.info.b_k_contig;
+  d.bn = c.bn;
+  d.tiles_n = (int32_t)((p.L.n + c.bn - 1) / c.bn);
+  d.splits = c.splits;
+  return d;
+}
+
+// The packed form of the tensor-core mainloop: always under TC_ACCESS_PACKED;
+// under TC_ACCESS_AUTO for contractions of at least 2^26 multiply-adds, unless
+// both operands are boxes and one of them has a single row (column) of output
+// tiles across from it.  Packing an operand costs one read of it through its
+// scatter vectors and one write and one read of its packed units; it pays
+// wherever the operand is re-read by several tiles or would be gathered (the
+// packing kernel, with many small CTAs per SM, gathers faster than the
+// mainloop's loader warps do), and also spares the mainloop its converters.
+// Measured on GB300: the 4096^3 contraction 0.53 -> 0.46 ms (boxes before),
+// Section 9's square and rank-k random contractions 6.0 -> 1.3 and 7.0 -> 1.8
+// ms (gathers before); the two gradient contractions whose 268 MB operand
+// is a box read by one column of tiles 0.09 -> 0.17 and 0.10 -> 0.35 ms,
+// hence the exception.
+bool packed_form(const Planned& p, const TcChoice& c) {
+  const Layout& L = p.L;
+  if (L.m <= 0 || L.n <= 0 || L.k <= 0) return false;
+  const int acc = access_setting();
+  if (acc == TC_ACCESS_PACKED) return true;
+  if (acc != TC_ACCESS_AUTO) return false;
+  if ((double)L.m * (double)L.n * (double)L.k < 67108864.0) return false;
+  const int64_t tm = (L.m + 127) / 128, tn = (L.n + c.bn - 1) / c.bn;
+  if (tm > 1 && tn > 1) return true;
+  DevProblem d = access_problem(p, c);
+  plan_single_access(L, d, nullptr, sm_count());
+  return !(d.boxA.rank > 0 && d.boxB.rank > 0);
+}
 
 WsLayout ws_layout(const Planned& p, tc_mode mode) {
   WsLayout w;
@@ -137,6 +179,7 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
   w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
   w.partial_off = w.scatter_bytes;
   w.partial_bytes = 0;
+  w.pack_bytes = 0;
   w.tcc = TcChoice{128, 1, 0};
   if (mode != TC_MODE_F64 && p.L.k > 0) {
     // TC_FORCE_BN (16..128, step 16) pins the tile width, for tests and
@@ -149,13 +192,16 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
     w.tcc = choose_tc(p.L, mode == TC_MODE_BF16X6 ? 3 : 2, sm_count(), force);
     if (w.tcc.splits > 1)
       w.partial_bytes = align_up((size_t)w.tcc.splits * p.L.m * p.L.n * sizeof(float), 256);
+    if (packed_form(p, w.tcc))
+      w.pack_bytes = tc_pack_bytes(p.L.m, p.L.n, p.L.k, w.tcc.bn, mode == TC_MODE_BF16X6 ? 3 : 2);
   }
   if (mode == TC_MODE_F64 && p.L.k > 0) {
     const int sms = sm_count();
     if (f64_grid(p.L.m, p.L.n, p.L.k, sms, true) != f64_grid(p.L.m, p.L.n, p.L.k, 0, false))
       w.partial_bytes = align_up(f64_partial_bytes(sms), 256);
   }
-  w.total = w.scatter_bytes + w.partial_bytes;
+  w.pack_off = w.scatter_bytes + w.partial_bytes;
+  w.total = w.pack_off + w.pack_bytes;
   return w;
 }
 
@@ -213,6 +259,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     plan_single_access(L, d, q.tm, sm_count());
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.reduce_f64 = split_reduction_f64() ? 1 : 0;
+    q.pack_ws = w.pack_bytes > 0 ? static_cast<char*>(ws) + w.pack_off : nullptr;
     q.ctas = sm_count();
     q.err = err_word();
     q.gate = gate;
@@ -222,8 +269,8 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
                    "access %s%s%s\n",
                    dt == TC_F64 ? "f64" : "f32", mode == TC_MODE_BF16X6 ? "bf16x6" : "bf16x3",
                    (long long)L.m, (long long)L.n, (long long)L.k, d.pair ? 256 : 128, d.bn,
-                   d.splits, d.boxA.rank > 0 ? "TMA boxes" : d.elem_gather ? "element gathers"
-                                                                           : "block gathers",
+                   d.splits, q.pack_ws ? "packed units" : d.boxA.rank > 0 ? "TMA boxes"
+                                        : d.elem_gather ? "element gathers" : "block gathers",
                    d.pair ? " on CTA pairs" : "", gate ? ", checked" : "");
     // TC_FAULT=timeout: test hook that makes the kernel's first wait expire
     if (const char* f = std::getenv("TC_FAULT")) q.fault = std::strcmp(f, "timeout") == 0 ? 1 : 0;
@@ -325,20 +372,34 @@ int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_ten
   if (mode == TC_MODE_F64) return TC_ERR_UNSUPPORTED;
   Planned p;
   if ((rc = plan_problem(A, B, C, &p)) != TC_OK) return rc;
-  DevProblem d;
-  std::memset(&d, 0, sizeof d);
-  d.a = p.a;
-  d.b = p.b;
-  d.a_kc = p.info.a_k_contig;
-  d.b_kc = p.info.b_k_contig;
-  const TcChoice tcc = ws_layout(p, mode).tcc;
-  d.bn = tcc.bn;
-  d.tiles_n = (int32_t)((p.L.n + d.bn - 1) / d.bn);
-  d.splits = tcc.splits;
+  const WsLayout w = ws_layout(p, mode);
+  DevProblem d = access_problem(p, w.tcc);
   CUtensorMap maps[2];
-  plan_single_access(p.L, d, box_encoder_available() ? maps : nullptr, sm_count());
+  if (w.pack_bytes == 0)  // the packed form reads no boxes
+    plan_single_access(p.L, d, box_encoder_available() ? maps : nullptr, sm_count());
   *a_box = d.boxA.rank > 0;
   *b_box = d.boxB.rank > 0;
+  return TC_OK;
+}
+
+int tc_operand_form(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
+                    const tc_tensor* C, int32_t* form) {
+  if (!form) return TC_ERR_ARG;
+  int rc = check_modes(dtype, mode);
+  if (rc != TC_OK) return rc;
+  if (mode == TC_MODE_F64) return TC_ERR_UNSUPPORTED;
+  Planned p;
+  if ((rc = plan_problem(A, B, C, &p)) != TC_OK) return rc;
+  const WsLayout w = ws_layout(p, mode);
+  if (w.pack_bytes > 0) {
+    *form = TC_FORM_PACKED;
+    return TC_OK;
+  }
+  DevProblem d = access_problem(p, w.tcc);
+  CUtensorMap maps[2];
+  plan_single_access(p.L, d, box_encoder_available() ? maps : nullptr, sm_count());
+  *form = d.boxA.rank > 0 && d.boxB.rank > 0 ? (d.pair ? TC_FORM_PAIR : TC_FORM_BOX)
+                                             : TC_FORM_GATHER;
   return TC_OK;
 }
 

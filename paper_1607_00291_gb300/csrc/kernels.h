@@ -114,6 +114,7 @@ struct DevProblem;
 void plan_access(const Layout& L, DevProblem& d, CUtensorMap* maps, bool allow_box = true,
                  bool pair = false);
 bool box_encoder_available();  // the driver's tensor-map encoder could be found
+int access_setting();           // the process-wide tc_set_access value
 // The process-wide split-reduction setting (tc_set_split_reduction): true for FP64.
 bool split_reduction_f64();
 
@@ -171,8 +172,13 @@ struct TcLaunch {
   int fault;  // fault injection for tests: 1 makes the MMA warp's first wait
               // expire (bounded), exercising the timeout and unwind path
   const int32_t* gate;  // checked launch: skip all work if *gate == kDevBounds (or null)
+  void* pack_ws;  // single problem, packed form: tc_pack_bytes() bytes for the packed
+                  // units of A and B (null: the gather or box form)
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
+// Workspace of the packed form: A's units (128 rows x 32 k, all pieces) then
+// B's (bn rows x 32 k), each part 256-byte aligned.
+size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces);
 
 // K6 on the FP64 path (f64.cu): persistent batched mainloop + FP64 reduction
 // of split problems.

@@ -181,24 +181,15 @@ struct Item {
   int nchunks;
 };
 
+// Output tile `tile` of problem d over k-split `split`.
 // PAIR: the CTA pair's tile has 256 rows; CTA `crank` of the pair takes rows
 // 128 crank .. 128 crank + 127 of it (all of its columns).
 template <bool PAIR = false>
-__device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w,
-                                         uint32_t crank = 0) {
+__device__ __forceinline__ Item item_of_tile(const DevProblem* d, int64_t tile, int split,
+                                             uint32_t crank = 0) {
   Item it;
-  int64_t tile;
-  if (a.probs) {
-    const WorkItem wi = a.items[w];
-    it.d = a.probs + wi.prob;
-    tile = wi.tile;
-    it.split = wi.split;
-  } else {
-    it.d = single;
-    tile = w % a.tiles_single;
-    it.split = (int)(w / a.tiles_single);
-  }
-  const DevProblem* d = it.d;
+  it.d = d;
+  it.split = split;
   it.m0 = (tile / d->tiles_n) * (PAIR ? 2 * BM : BM) + (PAIR ? (int64_t)BM * crank : 0);
   it.n0 = (tile % d->tiles_n) * d->bn;
   it.kbeg = (int64_t)it.split * d->kps;
@@ -208,6 +199,16 @@ __device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single
   it.rows_b = (int)(d->n - it.n0 < d->bn ? d->n - it.n0 : d->bn);
   it.nchunks = it.KT > 0 ? (int)((it.KT + CHUNK_KT - 1) / CHUNK_KT) : 1;
   return it;
+}
+
+template <bool PAIR = false>
+__device__ __forceinline__ Item get_item(const Args& a, const DevProblem* single, int64_t w,
+                                         uint32_t crank = 0) {
+  if (a.probs) {
+    const WorkItem wi = a.items[w];
+    return item_of_tile<PAIR>(a.probs + wi.prob, wi.tile, wi.split, crank);
+  }
+  return item_of_tile<PAIR>(single, w % a.tiles_single, (int)(w / a.tiles_single), crank);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -1068,6 +1069,390 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
   }
 }
 
+// ---- the packed form (BLIS-style packing of Section 5, on the GPU) -------------------
+// BLIS packs each operand's panels into a contiguous buffer once and reuses
+// them across every block of the other operand; the paper (Sections 5-6) has
+// the packing read the tensor through the scatter vectors, so that no tensor
+// is ever transposed.  The packed form does the same in two steps:
+//  * k_pack reads A (B) through its scatter vectors once, splits every value
+//    into bf16 pieces exactly as the converters do, and writes each 128-row
+//    (bn-row) x 32-k unit of the operand, all pieces, contiguously in the
+//    tensor core's K-major canonical layout (units ordered row tile by row
+//    tile, k-tile by k-tile);
+//  * k_tcp streams the units of each work item into shared memory with one
+//    bulk copy per operand and k-tile, and issues the same MMAs in the same
+//    order as k_tc (A from shared memory), with the same chunked accumulation
+//    and the same scattered epilogue.
+// Gathering once instead of once per output tile across from the operand cuts
+// the gathers by the operand's reuse (ceil(n / bn) for A, ceil(m / 128) for
+// B), and the mainloop then has no loaders and no converters; the price is
+// one write and one read of the packed operands (as many bytes as the FP32
+// operands for two pieces).  The results equal k_tc's bit for bit.
+struct PackArgs {
+  const float* x;
+  const int64_t* rs;  // the operand's row scatter vector (rows entries)
+  const int64_t* ks;  // its scatter vector along the contracted range (k entries)
+  int64_t rows, k;
+  int32_t R;          // rows of a unit: 128 for A, the tile width bn for B
+  int64_t KT;         // k-tiles of the contracted range
+  int64_t units;      // row tiles x KT
+  uint8_t* out;
+  const int32_t* gate;
+};
+
+// One CTA per unit; task c = (row r = c % R, k-chunk q = c / R) packs eight
+// values of one row (rows past the operand and k past its range are zeros).
+template <int NS>
+__global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
+  if (p.gate && *p.gate == kDevBounds) return;
+  const int R = p.R;
+  const int unit_bytes = NS * R * BK * 2;
+  for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+  const int64_t tr = u / p.KT, kt = u % p.KT;
+  uint8_t* out = p.out + u * (int64_t)unit_bytes;
+  const int64_t k0 = kt * BK;
+  for (int c = threadIdx.x; c < R * (BK / 8); c += blockDim.x) {
+    const int r = c % R, q = c / R;
+    const int64_t row = tr * R + r;
+    float v[8];
+    if (row < p.rows) {
+      const float* xr = p.x + __ldg(p.rs + row);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t kk = k0 + 8 * q + j;
+        v[j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = 0.f;
+    }
+    split8_store<NS>(v, out, R * BK * 2,
+                     (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16));
+  }
+  }
+}
+
+struct PackedArgs {
+  DevProblem single;
+  const uint8_t* pa;  // packed A units [tiles_m][KT][piece][128 x 32 bf16]
+  const uint8_t* pb;  // packed B units [tiles_n][KT][piece][bn x 32 bf16]
+  int64_t KT;         // k-tiles of the whole contracted range
+  int64_t nitems, tiles_single;
+  int32_t* err;
+  const int32_t* gate;
+  int dbuf;  // every work item is one chunk: alternate two accumulators
+  int fault;  // 1: injected timeout (see TcLaunch::fault)
+};
+
+constexpr int PK_THREADS = 192;  // producer warp, MMA warp, four epilogue warps
+constexpr int PK_EPI_W0 = 2;
+
+template <int NS>
+struct PLay {
+  static constexpr int A_BYTES = NS * BM * BK * 2;
+  static constexpr int B_BYTES = NS * BNMAX * BK * 2;  // room for the widest tile
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int NSTG = NS == 3 ? 4 : 6;
+  static constexpr int SCAT = NSTG * STAGE;  // int64 rC[BM] cC[BNMAX]
+  static constexpr int PROB = SCAT + (BM + BNMAX) * 8;
+  static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
+  static constexpr int NBARS = 2 * NSTG + 5;
+  static constexpr int MISC = BARS + NBARS * 8;
+  static constexpr int END = MISC + 16;
+  static constexpr int ALLOC = END + 1024;
+  static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
+};
+
+template <int NS>
+__global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ PackedArgs a) {
+  using Ly = PLay<NS>;
+  constexpr int NSTG = Ly::NSTG;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  int64_t* sRC = reinterpret_cast<int64_t*>(smem + Ly::SCAT);
+  int64_t* sCC = sRC + BM;
+  DevProblem* sProb = reinterpret_cast<DevProblem*>(smem + Ly::PROB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Ly::BARS);
+  uint64_t* empty = full + NSTG;
+  uint64_t* acc_full = empty + NSTG;  // [2]
+  uint64_t* acc_empty = acc_full + 2;  // [2]
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
+  constexpr uint32_t PK_COLS = 2 * BNMAX;  // accumulator + running sum (or the second accumulator)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NSTG; ++s) {
+      mbar_init(&full[s], 1);   // the producer's arrival, with the transaction count
+      mbar_init(&empty[s], 1);  // tcgen05.commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], NEPI);
+    }
+    mbar_init(drain, 1);
+    *abort = (a.gate && *a.gate == kDevBounds) ? 2 : 0;
+    *sProb = a.single;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, PK_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const DevProblem* d = sProb;
+  const int64_t nitems = a.nitems, w0 = blockIdx.x, dw = gridDim.x;
+  const uint32_t a_bytes = (uint32_t)Ly::A_BYTES;
+  const uint32_t b_bytes = (uint32_t)(NS * d->bn * BK * 2);
+  auto item = [&](int64_t w) {
+    return item_of_tile<false>(d, w % a.tiles_single, (int)(w / a.tiles_single));
+  };
+
+  if (warp == 0) {
+    // ---- producer: one lane streams the units of every work item ----
+    if (lane == 0) {
+      int64_t g = 0, g_iss = -1;
+      bool failed = false;
+      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
+        const Item it = item(w);
+        const uint8_t* ua = a.pa + ((it.m0 / BM) * a.KT + it.kbeg / BK) * (int64_t)a_bytes;
+        const uint8_t* ub = a.pb + ((it.n0 / d->bn) * a.KT + it.kbeg / BK) * (int64_t)b_bytes;
+        for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
+          const int s = (int)(g % NSTG);
+          if (!mbar_wait(&empty[s], (uint32_t)(((g / NSTG) & 1) ^ 1), abort)) {
+            record_timeout(abort, a.err);
+            failed = true;
+            break;
+          }
+          const uint32_t st = smem_u32(smem + s * Ly::STAGE);
+          mbar_expect_tx(&full[s], a_bytes + b_bytes);
+          bulk_load(st, ua + kt * (int64_t)a_bytes, a_bytes, &full[s]);
+          bulk_load(st + Ly::A_BYTES, ub + kt * (int64_t)b_bytes, b_bytes, &full[s]);
+          mbar_arrive(&full[s]);
+          g_iss = g;
+        }
+      }
+      // no copy may outlive the CTA (matters only after an abort): only the
+      // last NSTG stages can be in flight; wait for their phases (bounded)
+      if (g_iss >= 0) {
+        for (int64_t gi = g_iss - NSTG + 1 > 0 ? g_iss - NSTG + 1 : 0; gi <= g_iss; ++gi) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[gi % NSTG], (uint32_t)((gi / NSTG) & 1)) &&
+                 clock64() - t0 < 20000000LL) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issue: the same products, in the same order, as k_tc ----
+    if (lane == 0) {
+      int64_t g = 0, gc = 0;
+      bool failed = false;
+      if (a.fault == 1) {
+        // injected failure: a bounded wait (about 10 ms) on a barrier nothing
+        // arrives on yet; it expires, and the CTA unwinds through the abort path
+        if (!mbar_wait(drain, 0, abort, 20000000LL)) {
+          record_timeout(abort, a.err);
+          failed = true;
+        }
+      }
+      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
+        const Item it = item(w);
+        const int bn = d->bn;
+        const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)bn);
+        for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
+          const int buf = a.dbuf ? (int)(gc & 1) : 0;
+          const int64_t use = a.dbuf ? gc >> 1 : gc;
+          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
+            record_timeout(abort, a.err);
+            failed = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = tmem + (buf ? TM_SUM : TM_ACC);
+          const int64_t kt0 = (int64_t)ch * CHUNK_KT;
+          const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
+          for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
+            const int s = (int)(g % NSTG);
+            if (!mbar_wait(&full[s], (uint32_t)((g / NSTG) & 1), abort)) {
+              record_timeout(abort, a.err);
+              failed = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * Ly::STAGE);
+            const uint32_t sb = sa + Ly::A_BYTES;
+#pragma unroll
+            for (int ksl = 0; ksl < BK / 16; ++ksl) {
+              uint64_t dA[NS], dB[NS];
+#pragma unroll
+              for (int i = 0; i < NS; ++i) {
+                dA[i] = smem_desc(sa + i * BM * BK * 2 + ksl * 2 * (BM / 8) * 128,
+                                  (BM / 8) * 128, 128);
+                dB[i] = smem_desc(sb + i * bn * BK * 2 + ksl * 2 * (bn / 8) * 128,
+                                  (uint32_t)(bn / 8) * 128, 128);
+              }
+              mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
+#pragma unroll
+              for (int ts = 1; ts < NS; ++ts)
+#pragma unroll
+                for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+          }
+          if (failed) break;
+          if (kt1 > kt0) mma_commit(&acc_full[buf]);
+          else mbar_arrive(&acc_full[buf]);
+        }
+      }
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0, abort)) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(drain, 0) && clock64() - t0 < 4000000000LL) {
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: one thread per accumulator row (as in k_tc) ----
+    const int t = tid - PK_EPI_W0 * 32;
+    const int wq = warp & 3;
+    const int row = 32 * wq + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
+    constexpr int NB = BNMAX / NEPI;
+    int64_t pre_r = 0, pre_c[NB];
+    auto fetch_rows = [&](const Item& it) {
+      pre_r = t < it.rows_a ? __ldg(d->sp.rC + it.m0 + t) : 0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const int c = t + i * NEPI;
+        pre_c[i] = c < it.rows_b ? __ldg(d->sp.cC + it.n0 + c) : 0;
+      }
+    };
+    int64_t w = w0;
+    if (w < nitems) fetch_rows(item(w));
+    int64_t gc = 0;
+    for (;;) {
+      if (bar_or(BAR_EPI, NEPI, *abort || w >= nitems)) break;
+      const Item it = item(w);
+      sRC[t] = pre_r;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
+      w += dw;
+      if (w < nitems) fetch_rows(item(w));
+      bar_sync(BAR_EPI, NEPI);
+      const bool have = it.KT > 0;
+      const int bn = d->bn;
+      const bool direct = d->splits == 1;
+      const float al = (float)d->alpha, be = (float)d->beta;
+      float* const crow = static_cast<float*>(d->c) + sRC[row];
+      float* const prow = direct ? nullptr
+                                 : static_cast<float*>(d->partial) +
+                                       ((int64_t)it.split * d->n + it.n0) * d->m + it.m0 + row;
+      const int64_t pm = d->m;
+      const bool mv = row < it.rows_a;
+      const int cols = it.rows_b;
+      bool ok = true;
+      auto out8 = [&](int cb, const float (&hi)[8], const float (&lo)[8]) {
+        if (!mv) return;
+        if (!direct) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols) prow[(int64_t)(cb + q) * pm] = __fadd_rn(hi[q], lo[q]);
+        } else if (be == 0.f) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols) crow[sCC[cb + q]] = __fmaf_rn(al, hi[q], al * lo[q]);
+        } else {
+          float old[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) old[q] = cb + q < cols ? crow[sCC[cb + q]] : 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cb + q < cols)
+              crow[sCC[cb + q]] = __fmaf_rn(be, old[q], __fmaf_rn(al, hi[q], al * lo[q]));
+        }
+      };
+      for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
+        const bool first = ch == 0, last = ch + 1 == it.nchunks;
+        const int buf = a.dbuf ? (int)(gc & 1) : 0;
+        const uint32_t use = (uint32_t)(a.dbuf ? gc >> 1 : gc);
+        if (have && !*abort) {
+          if (!mbar_wait(&acc_full[buf], use & 1u, abort)) record_timeout(abort, a.err);
+        }
+        tc_fence_after();
+        ok = __all_sync(0xffffffffu, !*abort);
+        const bool direct_out = a.dbuf || (first && last && it.KT <= 4);
+        if (ok && direct_out) {
+          const uint32_t accc = buf ? TM_SUM : TM_ACC;
+          float z[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[q] = 0.f;
+          for (int cb = 0; cb < bn; cb += 16) {
+            float v[16];
+            if (have) {
+              tmem_ld16(lane_base + accc + (uint32_t)cb, v);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+#pragma unroll
+            for (int p8 = 0; p8 < 2; ++p8) {
+              float v8[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v8[q] = v[8 * p8 + q];
+              out8(cb + 8 * p8, v8, z);
+            }
+          }
+        } else if (ok) {
+          for (int cb = 0; cb < bn; cb += 8) {
+            float v[8], sum[8];
+            if (have) {
+              tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v[q] = 0.f;
+            }
+            if (first) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) sum[q] = v[q];
+            } else {
+              tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) sum[q] = __fadd_rn(sum[q], v[q]);
+            }
+            tmem_st8(lane_base + TM_SUM + (uint32_t)cb, sum);
+          }
+          tmem_st_wait();
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        if (!ok) break;
+        if (!last || direct_out) continue;
+        for (int cb = 0; cb < bn; cb += 8) {
+          float sum[8], z[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[q] = 0.f;
+          tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
+          out8(cb, sum, z);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, PK_COLS);
+  }
+}
+
+cudaError_t launch_reduce(const TcLaunch& q, cudaStream_t s);
+
 template <int NS, bool BOX, bool PAIR>
 cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
@@ -1127,6 +1512,14 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
     k_tc<NS, BOX, PAIR><<<(unsigned)grid, nthreads(BOX), Lay<NS, BOX, PAIR>::ALLOC, s>>>(a);
   }
   note_launch();
+  const cudaError_t e = launch_reduce(q, s);
+  mainloop_event_after(s);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// K4 after the mainloop: the single problem's k-splits, or every split
+// problem of a batch.
+cudaError_t launch_reduce(const TcLaunch& q, cudaStream_t s) {
   const bool single_split = !q.probs && q.single.splits > 1;
   if (single_split || (q.probs && q.n_split_probs > 0)) {
     const int64_t mm = single_split ? q.single.m : q.max_m_split;
@@ -1146,19 +1539,90 @@ cudaError_t launch_cfg(const TcLaunch& q, cudaStream_t s) {
                                                             q.gate);
     note_launch();
   }
-  mainloop_event_after(s);
   return cudaGetLastError();
+}
+
+size_t pack_a_bytes(int64_t m, int64_t k, int pieces) {
+  return align_up((size_t)((m + BM - 1) / BM) * (size_t)((k + BK - 1) / BK) * pieces * BM * BK * 2,
+                  256);
+}
+
+template <int NS>
+cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_tcp<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PLay<NS>::ALLOC);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const DevProblem& d = q.single;
+  const int64_t KT = (d.k + BK - 1) / BK;
+  const int64_t tm = (d.m + BM - 1) / BM, tn = d.tiles_n;
+  if (KT == 0 || tm == 0 || tn == 0) return cudaSuccess;
+  uint8_t* pa = static_cast<uint8_t*>(q.pack_ws);
+  uint8_t* pb = pa + pack_a_bytes(d.m, d.k, NS);
+  mainloop_event_before(s);
+  const int64_t pack_grid_max = (int64_t)q.ctas * 8;
+  PackArgs pk;
+  pk.x = static_cast<const float*>(d.a);
+  pk.rs = d.sp.rA;
+  pk.ks = d.sp.cA;
+  pk.rows = d.m;
+  pk.k = d.k;
+  pk.R = BM;
+  pk.KT = KT;
+  pk.units = tm * KT;
+  pk.out = pa;
+  pk.gate = q.gate;
+  k_pack<NS><<<(unsigned)std::min(pk.units, pack_grid_max), 256, 0, s>>>(pk);
+  note_launch();
+  pk.x = static_cast<const float*>(d.b);
+  pk.rs = d.sp.cB;
+  pk.ks = d.sp.rB;
+  pk.rows = d.n;
+  pk.R = d.bn;
+  pk.units = tn * KT;
+  pk.out = pb;
+  k_pack<NS><<<(unsigned)std::min(pk.units, pack_grid_max), 256, 0, s>>>(pk);
+  note_launch();
+  PackedArgs a;
+  a.single = d;
+  a.pa = pa;
+  a.pb = pb;
+  a.KT = KT;
+  a.tiles_single = tm * tn;
+  a.nitems = a.tiles_single * d.splits;
+  a.err = q.err;
+  a.gate = q.gate;
+  a.dbuf = d.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0;
+  a.fault = q.fault;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
+  k_tcp<NS><<<(unsigned)grid, PK_THREADS, PLay<NS>::ALLOC, s>>>(a);
+  note_launch();
+  const cudaError_t e = launch_reduce(q, s);
+  mainloop_event_after(s);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
 
 int tc_bn_max() { return BNMAX; }
+size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces) {
+  if (m <= 0 || n <= 0 || k <= 0) return 0;
+  const size_t b = (size_t)((n + bn - 1) / bn) * (size_t)((k + BK - 1) / BK) * pieces * bn * BK * 2;
+  return pack_a_bytes(m, k, pieces) + align_up(b, 256);
+}
 int tc_max_item_ktiles() { return MAX_CHUNKS * CHUNK_KT; }
 
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
   // boxes only when every work item has both operands as boxes (the planner
   // sets both or neither; batch plans set neither); the pair form only with
   // boxes planned for it (B boxes half the tile wide)
+  if (!q.probs && q.pack_ws)
+    return q.pieces == 3 ? launch_packed<3>(q, s) : launch_packed<2>(q, s);
   const bool box = !q.probs && q.single.boxA.rank > 0 && q.single.boxB.rank > 0;
   const bool pair = box && q.single.pair;
   if (q.pieces == 3)

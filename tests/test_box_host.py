@@ -46,12 +46,39 @@ def test_only_the_box_setting_takes_boxes():
     sp = W.SPECS["spiky_f32"]
     sh = lambda lab: cm([sp.ext[c] for c in lab])  # noqa: E731
     args = (sh(sp.labA), sp.labA, sh(sp.labB), sp.labB, sh(sp.labC), sp.labC)
-    assert tc.set_access("box") == "box"  # the default
-    for acc in ("block", "scatter"):
+    assert tc.set_access("box") == "auto"  # the default
+    for acc in ("block", "scatter", "packed"):
         with tc.access(acc):
             assert tc.box_access(*args) == (False, False)
     assert tc.box_access(*args) == (True, True)
-    assert tc.set_access("box") == "box"
+    assert tc.set_access("auto") == "box"
+    # the default packs this 4096^3 contraction: no boxes then
+    assert tc.box_access(*args) == (False, False)
+
+
+def test_operand_form_choices():
+    # the mainloop's form per setting (host only; 152 SMs assumed without a GPU)
+    sp = W.SPECS["spiky_f32"]
+    sh = lambda s, lab: cm([s.ext[c] for c in lab])  # noqa: E731
+    spiky = (sh(sp, sp.labA), sp.labA, sh(sp, sp.labB), sp.labB, sh(sp, sp.labC), sp.labC)
+    assert tc.operand_form(*spiky) == "packed"  # the default (auto): 4096^3, both operands reused
+    with tc.access("box"):
+        assert tc.operand_form(*spiky) == "pair"  # 512 pair tiles
+    with tc.access("block"):
+        assert tc.operand_form(*spiky) == "gather"
+    gr = W.SPECS["grad_f32"]
+    fwd = (sh(gr, gr.labA), gr.labA, sh(gr, gr.labB), gr.labB, sh(gr, gr.labC), gr.labC)
+    # the forward's 268 MB A is a box read by one column of output tiles: not packed
+    assert tc.operand_form(*fwd) == "box"
+    # dA = dC x_J B: both operands reused (128 x 32 tiles): packed
+    assert tc.operand_form(sh(gr, gr.labC), gr.labC, sh(gr, gr.labB), gr.labB,
+                           sh(gr, gr.labA), gr.labA) == "packed"
+    # below 2^26 multiply-adds the default keeps the box form; "packed" forces packing
+    small = (cm([256, 64]), "ip", cm([64, 256]), "pj", cm([256, 256]), "ij")
+    assert tc.operand_form(*small) == "box"
+    with tc.access("packed"):
+        assert tc.operand_form(*small) == "packed"
+        assert tc.box_access(*small) == (False, False)
 
 
 def test_tile_structure_rules():

@@ -18,10 +18,13 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("access,colmajor,boxes", [("block", False, (False, False)),
                                                   ("box", False, (False, False)),
-                                                  ("box", True, (True, True))])
+                                                  ("box", True, (True, True)),
+                                                  ("packed", False, (False, False)),
+                                                  ("packed", True, (False, False))])
 def test_injected_timeout_is_reported_and_context_survives(monkeypatch, access, colmajor, boxes):
     # with boxes (True, True), the box warp waits (bounded) for boxes still in
-    # flight before its CTA exits
+    # flight before its CTA exits; in the packed form the producer waits
+    # (bounded) for its bulk copies in flight
     g = torch.Generator().manual_seed(3)
     A = (torch.rand(200, 96, generator=g, dtype=torch.float64) * 2 - 1).float().double()
     B = (torch.rand(96, 150, generator=g, dtype=torch.float64) * 2 - 1).float().double()

@@ -22,6 +22,14 @@ from test_gpu_box import CASES as BOX_CASES, colmajor_rand
 pytestmark = pytest.mark.gpu
 TOLS = {"bf16x3": 3 * 2.0 ** -16 + 8 * 2.0 ** -24, "bf16x6": 1e-5}
 
+
+@pytest.fixture(autouse=True)
+def _box_setting():
+    # the pair form is a box form: these tests run under the "box" setting
+    # (the default "auto" packs the larger of these contractions instead)
+    with tc.access("box"):
+        yield
+
 CASES = {k: v[:4] for k, v in BOX_CASES.items()}
 CASES.update({
     "m300": ("ip", "pj", "ij", dict(i=300, p=96, j=128)),       # odd half of the 2nd pair tile partial
@@ -77,8 +85,9 @@ def test_pair_with_k_splits(monkeypatch):
 
 
 def test_spiky_workload_pairs_by_default(monkeypatch):
-    # the 4096^3 precision-form workload has 512 pair tiles: the default rule
-    # takes the pair form; results equal the single-CTA form's everywhere
+    # the 4096^3 precision-form workload has 512 pair tiles: under the box
+    # setting the pair form is taken unless TC_PAIR=0; results equal the
+    # single-CTA form's everywhere
     s = W.SPECS["spiky_f32"]
     h = W.make_inputs(s, seed=1002)
     dA, dB = to_device(h["A"], torch.float32), to_device(h["B"], torch.float32)
