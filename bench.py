@@ -462,6 +462,7 @@ def run_batch(args, ws, rank, local):
     os.environ["TC_AUTOTUNE_CACHE"] = cache
     t_plan = time.perf_counter()
     plan = tc.Plan(dev, mode=mode)
+    bkernel = {"f64": "k_f64_batched", "packed": "k_pack+k_tcp", "gather": "k_tc"}[plan.form]
     t_plan = time.perf_counter() - t_plan
     cfgs = [plan.config(i) for i in range(len(dev))]
     tuned = {"cache": cache, "plan_create_s": round(t_plan, 2), "balance_divisor": cfgs[0]["balance"],
@@ -538,10 +539,10 @@ def run_batch(args, ws, rank, local):
             peak, src = mp.get("bf16_tflops", 1900.0), "MEASURED_PEAKS.json bf16_tflops (burst)"
             prods = 3 if mode == "bf16x3" else 6
         ach = prods * flops / (kms * 1e-3) / 1e12
-        line["roofline"] = {"bound": "tensor", "kernel": "k_f64_batched" if mode == "f64" else "k_tc",
+        line["roofline"] = {"bound": "tensor", "kernel": bkernel,
                             "achieved": round(ach, 5), "peak": round(peak, 5), "unit": "TFLOP/s",
                             "frac": round(ach / peak, 4), "peak_source": src, "kernel_ms": round(kms, 4),
-                            "traffic": traffic_for("k_f64_batched" if mode == "f64" else "k_tc",
+                            "traffic": traffic_for(bkernel,
                                                    f"batch512_{mode}"),
                             "algorithmic": f"{flops:.4g} flops per launch (x{prods} products)"}
         if check:
@@ -594,7 +595,7 @@ def run_batch(args, ws, rank, local):
         "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": int(per_step * K),
-        "roofline": {"bound": "tensor", "kernel": "k_f64_batched" if mode == "f64" else "k_tc",
+        "roofline": {"bound": "tensor", "kernel": bkernel,
                      "achieved": round(ach, 5), "peak": round(peak, 5), "unit": "TFLOP/s",
                      "frac": round(ach / peak, 4), "peak_source": src, "kernel_ms": round(kms, 4),
                      "traffic": None, "algorithmic": f"{flops:.4g} flops per launch (x{prods} products)"},

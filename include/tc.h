@@ -188,6 +188,13 @@ TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);
  * fair share).  A problem with an empty output gets zeros in out[0..2].
  * Host only.  TC_ERR_ARG for a null pointer or an index out of range. */
 TC_API int tc_plan_config(const tc_plan* plan, int32_t index, int32_t* out);
+/* Mainloop forms of the tensor-core path (tc_operand_form, tc_plan_form). */
+typedef enum { TC_FORM_GATHER = 0, TC_FORM_BOX = 1, TC_FORM_PAIR = 2, TC_FORM_PACKED = 3 } tc_form;
+/* The mainloop form of a tensor-core plan (tc_form): TC_FORM_PACKED when the
+ * plan packs every problem's A and B before its mainloop (tc_set_access), else
+ * TC_FORM_GATHER (batch plans take no boxes).  Host only.
+ * TC_ERR_UNSUPPORTED for an FP64 plan, TC_ERR_ARG for a null pointer. */
+TC_API int tc_plan_form(const tc_plan* plan, int32_t* form);
 TC_API int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* stream);
 TC_API void tc_plan_destroy(tc_plan* plan);
 
@@ -270,7 +277,6 @@ TC_API int tc_box_access(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const
  * boxes, one CTA per tile), TC_FORM_PAIR (boxes on CTA pairs) or
  * TC_FORM_PACKED (both packed before the mainloop).  Host only.
  * TC_ERR_UNSUPPORTED for the FP64 mode or F64 data. */
-typedef enum { TC_FORM_GATHER = 0, TC_FORM_BOX = 1, TC_FORM_PAIR = 2, TC_FORM_PACKED = 3 } tc_form;
 TC_API int tc_operand_form(tc_dtype dtype, tc_mode mode, const tc_tensor* A, const tc_tensor* B,
                            const tc_tensor* C, int32_t* form);
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "tc_set_checks": (c_i32, [c_i32]),
     "tc_box_access": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
                       [ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "tc_plan_form": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
     "tc_operand_form": (c_i32, [c_i32, c_i32] + [ctypes.POINTER(TcTensor)] * 3 +
                         [ctypes.POINTER(c_i32)]),
     "tc_set_mainloop_events": (c_i32, [c_vp, c_vp]),

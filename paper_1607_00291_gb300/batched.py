@@ -65,6 +65,16 @@ class Plan:
         L.check(L.lib().tc_plan_config(self._plan, int(index), out), "tc_plan_config")
         return {"bm": out[0], "bn": out[1], "splits": out[2], "balance": out[3]}
 
+    @property
+    def form(self) -> str:
+        """The mainloop form of a tensor-core plan: "packed" or "gather"
+        (tc_plan_form); "f64" for an FP64 plan."""
+        if self.mode == L.TC_MODE_F64:
+            return "f64"
+        f = L.c_i32(0)
+        L.check(L.lib().tc_plan_form(self._plan, f), "tc_plan_form")
+        return {0: "gather", 3: "packed"}[f.value]
+
     def close(self):
         if getattr(self, "_plan", None):
             L.lib().tc_plan_destroy(self._plan)

@@ -127,9 +127,21 @@ struct WsLayout {
   size_t scatter_off, scatter_bytes;
   size_t partial_off, partial_bytes;
   size_t pack_off, pack_bytes;  // packed form: the packed units of A and B
+  bool pack_pair;               // packed form on CTA pairs
   size_t total;
   TcChoice tcc;
 };
+
+// The packed form on CTA pairs only under TC_PAIR=1: the pairs cut each SM's
+// operand bytes per k-tile by a quarter, but the packed mainloop is bound by
+// its MMA issue rather than by those bytes, and the relay of the odd CTA's
+// stages to the even CTA's issuer made it slower (4096^3: 0.392 against 0.383
+// ms; Section 9's square random contractions: 1.18 against 1.11 ms).
+bool packed_pair(const Layout& L, const TcChoice& c, int sms) {
+  (void)c;
+  (void)sms;
+  return pair_setting() == 2 && L.m > 128;
+}
 
 // A problem's descriptor fields that the access plan reads.
 DevProblem access_problem(const Planned& p, const TcChoice& c) {
@@ -180,6 +192,7 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
   w.partial_off = w.scatter_bytes;
   w.partial_bytes = 0;
   w.pack_bytes = 0;
+  w.pack_pair = false;
   w.tcc = TcChoice{128, 1, 0};
   if (mode != TC_MODE_F64 && p.L.k > 0) {
     // TC_FORCE_BN (16..128, step 16) pins the tile width, for tests and
@@ -192,8 +205,11 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
     w.tcc = choose_tc(p.L, mode == TC_MODE_BF16X6 ? 3 : 2, sm_count(), force);
     if (w.tcc.splits > 1)
       w.partial_bytes = align_up((size_t)w.tcc.splits * p.L.m * p.L.n * sizeof(float), 256);
-    if (packed_form(p, w.tcc))
-      w.pack_bytes = tc_pack_bytes(p.L.m, p.L.n, p.L.k, w.tcc.bn, mode == TC_MODE_BF16X6 ? 3 : 2);
+    if (packed_form(p, w.tcc)) {
+      w.pack_pair = packed_pair(p.L, w.tcc, sm_count());
+      w.pack_bytes = tc_pack_bytes(p.L.m, p.L.n, p.L.k, w.tcc.bn, mode == TC_MODE_BF16X6 ? 3 : 2,
+                                   w.pack_pair);
+    }
   }
   if (mode == TC_MODE_F64 && p.L.k > 0) {
     const int sms = sm_count();
@@ -260,6 +276,7 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     q.pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
     q.reduce_f64 = split_reduction_f64() ? 1 : 0;
     q.pack_ws = w.pack_bytes > 0 ? static_cast<char*>(ws) + w.pack_off : nullptr;
+    if (q.pack_ws) d.pair = w.pack_pair ? 1 : 0;
     q.ctas = sm_count();
     q.err = err_word();
     q.gate = gate;

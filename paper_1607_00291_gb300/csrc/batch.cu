@@ -428,6 +428,13 @@ struct tc_plan {
   CheckBounds* d_bounds = nullptr;  // checked plans: per-problem scatter-vector ranges
   int64_t ctas = 152;
   int64_t sms = 152;
+  // the packed form (tensor-core plans): every problem's A and B packed by one
+  // launch from a job list, then the packed mainloop over the work list
+  bool packed = false;
+  PackJob* d_jobs = nullptr;
+  int64_t* d_job_prefix = nullptr;
+  int32_t njobs = 0;
+  int64_t pack_groups = 0;
 };
 
 namespace {
@@ -564,6 +571,36 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     }
   }
 
+  // The packed form for tensor-core batches: always under TC_ACCESS_PACKED,
+  // under TC_ACCESS_AUTO when the batch holds at least 2^26 multiply-adds
+  // (as for single contractions).  Every operand of a batch is gathered
+  // otherwise, so packing pays here even for operands read by one tile: the
+  // packing launch, many small CTAs per SM, gathers them faster than the
+  // mainloop's loader warps.
+  if (!f64) {
+    double work = 0;
+    for (int i = 0; i < np; ++i) {
+      const Layout& L = pl->planned[i].L;
+      work += (double)L.m * (double)L.n * (double)L.k;
+    }
+    const int acc = access_setting();
+    pl->packed = acc == TC_ACCESS_PACKED || (acc == TC_ACCESS_AUTO && work >= 67108864.0);
+  }
+  std::vector<size_t> pack_a(np, 0), pack_b(np, 0);
+  size_t pack_total = 0;
+  if (pl->packed) {
+    for (int i = 0; i < np; ++i) {
+      const Layout& L = pl->planned[i].L;
+      const ProbCfg& c = pl->cfg[i];
+      if (L.k == 0) continue;
+      const int64_t KT = (L.k + 31) / 32;
+      pack_a[i] = pack_total;
+      pack_total += align_up((size_t)((L.m + 127) / 128) * KT * pl->pieces * 128 * 32 * 2, 256);
+      pack_b[i] = pack_total;
+      pack_total += align_up((size_t)((L.n + c.bn - 1) / c.bn) * KT * pl->pieces * c.bn * 32 * 2, 256);
+    }
+  }
+
   // device buffer: layouts | offsets | scatter | problems | items | split list | partials
   std::vector<int64_t> offs(np + 1, 0);
   for (int i = 0; i < np; ++i) offs[i + 1] = offs[i] + scatter_offsets(pl->planned[i].L, kBsBlock).total;
@@ -610,8 +647,8 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     for (const WorkItem& w : items) ksteps += item_cost(w);
     for (int i = 0; i < np; ++i) tiles[{pl->cfg[i].bm, pl->cfg[i].bn}]++;
     std::fprintf(stderr, "[libtc] batch plan: %d problems, %lld work items, %d split, "
-                 "%.3g k-index-units of work; tiles (m x n: problems):", np,
-                 (long long)pl->nitems, pl->n_split, ksteps);
+                 "%.3g k-index-units of work%s; tiles (m x n: problems):", np,
+                 (long long)pl->nitems, pl->n_split, ksteps, pl->packed ? ", packed" : "");
     for (const auto& kv : tiles)
       std::fprintf(stderr, " %dx%d: %d", kv.first.first, kv.first.second, kv.second);
     std::fprintf(stderr, "\n");
@@ -635,6 +672,9 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   const size_t o_tmap = take(sizeof(CUtensorMap) * 2 * std::max(np, 1));
   const size_t o_ctr = take(sizeof(unsigned long long) * kF64BatchClasses);
   const size_t o_cb = take(pl->checks ? sizeof(CheckBounds) * std::max(np, 1) : 0);
+  const size_t o_jobs = take(pl->packed ? sizeof(PackJob) * 2 * std::max(np, 1) : 0);
+  const size_t o_jpre = take(pl->packed ? sizeof(int64_t) * (2 * np + 1) : 0);
+  const size_t o_pack = take(pack_total);
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -650,6 +690,13 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   pl->d_split = reinterpret_cast<int32_t*>(base + o_split);
   pl->d_split_cols = reinterpret_cast<int64_t*>(base + o_scols);
   if (pl->checks) pl->d_bounds = reinterpret_cast<CheckBounds*>(base + o_cb);
+  if (pl->packed) {
+    pl->d_jobs = reinterpret_cast<PackJob*>(base + o_jobs);
+    pl->d_job_prefix = reinterpret_cast<int64_t*>(base + o_jpre);
+  }
+  uint8_t* packbuf = reinterpret_cast<uint8_t*>(base + o_pack);
+  std::vector<PackJob> jobs;
+  std::vector<int64_t> jpre(1, 0);
   std::vector<int64_t> scols(pl->n_split + 1, 0);
   for (int i = 0; i < pl->n_split; ++i) scols[i + 1] = scols[i] + pl->planned[splitp[i]].L.n;
   pl->split_cols = scols[pl->n_split];
@@ -687,7 +734,41 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
       plan_access(p.L, d, &maps[2 * (size_t)i], /*allow_box=*/false);
       d.tmaps = d_maps + 2 * (size_t)i;
     }
+    if (pl->packed && p.L.k > 0) {
+      const int64_t KT = (p.L.k + 31) / 32;
+      d.pa = packbuf + pack_a[i];
+      d.pb = packbuf + pack_b[i];
+      PackJob ja;
+      std::memset(&ja, 0, sizeof ja);
+      ja.x = static_cast<const float*>(d.a);
+      ja.rs = d.sp.rA;
+      ja.ks = d.sp.cA;
+      ja.kbs = d.sp.cbsA;
+      ja.rows = d.m;
+      ja.k = d.k;
+      ja.KT = KT;
+      ja.R = 128;
+      ja.units = ((d.m + 127) / 128) * KT;
+      ja.out = packbuf + pack_a[i];
+      PackJob jb = ja;
+      jb.x = static_cast<const float*>(d.b);
+      jb.rs = d.sp.cB;
+      jb.ks = d.sp.rB;
+      jb.kbs = d.sp.rbsB;
+      jb.rows = d.n;
+      jb.R = c.bn;
+      jb.units = (int64_t)d.tiles_n * KT;
+      jb.out = packbuf + pack_b[i];
+      pack_job_groups(ja);
+      pack_job_groups(jb);
+      for (const PackJob& j : {ja, jb}) {
+        jobs.push_back(j);
+        jpre.push_back(jpre.back() + j.groups);
+      }
+    }
   }
+  pl->njobs = (int32_t)jobs.size();
+  pl->pack_groups = jpre.back();
   auto up = [](void* dst, const void* src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
@@ -697,7 +778,9 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
       !up(pl->d_items, items.data(), sizeof(WorkItem) * items.size()) ||
       !up(pl->d_split, splitp.data(), sizeof(int32_t) * splitp.size()) ||
       !up(pl->d_split_cols, scols.data(), sizeof(int64_t) * scols.size()) ||
-      !up(base + o_tmap, maps.data(), sizeof(CUtensorMap) * maps.size()))
+      !up(base + o_tmap, maps.data(), sizeof(CUtensorMap) * maps.size()) ||
+      (pl->packed && (!up(pl->d_jobs, jobs.data(), sizeof(PackJob) * jobs.size()) ||
+                      !up(pl->d_job_prefix, jpre.data(), sizeof(int64_t) * jpre.size()))))
     return TC_ERR_CUDA;
   if (pl->checks) {
     std::vector<CheckBounds> cb(np);
@@ -825,6 +908,13 @@ int tc_plan_config(const tc_plan* plan, int32_t index, int32_t* out) {
   return TC_OK;
 }
 
+int tc_plan_form(const tc_plan* plan, int32_t* form) {
+  if (!plan || !form) return TC_ERR_ARG;
+  if (plan->mode == TC_MODE_F64) return TC_ERR_UNSUPPORTED;
+  *form = plan->packed ? TC_FORM_PACKED : TC_FORM_GATHER;
+  return TC_OK;
+}
+
 int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes) {
   if (!plan || !bytes) return TC_ERR_ARG;
   *bytes = 0;  // the plan owns its scatter vectors and partials
@@ -888,6 +978,12 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.counter = plan->d_counter;
     q.err = err_word();
     q.gate = gate;
+    if (plan->packed) {
+      q.pack_jobs = plan->d_jobs;
+      q.pack_prefix = plan->d_job_prefix;
+      q.pack_njobs = plan->njobs;
+      q.pack_groups = plan->pack_groups;
+    }
     e = launch_tc(q, s);
   }
   return e == cudaSuccess ? TC_OK : TC_ERR_CUDA;

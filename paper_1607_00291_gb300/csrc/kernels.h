@@ -142,7 +142,30 @@ struct DevProblem {
   BoxAccess boxA, boxB;       // tensor-core path: TMA boxes or gathers per operand
   const CUtensorMap* tmaps;   // batch: the two tensor maps in device memory (a single
                               // call passes them as kernel parameters instead)
+  const uint8_t* pa;          // packed form: A's units [ceil(m/128)][ceil(k/32)] and
+  const uint8_t* pb;          // B's [tiles_n][ceil(k/32)], each all pieces of 128 (bn)
+                              // rows x 32 k in the tensor core's K-major layout
 };
+
+// One operand of one problem to pack (the packed form): `units` units of R
+// rows x 32 k, row tile by row tile, k-tile by k-tile, from x through its row
+// scatter vector rs and its scatter vector along the contracted range ks
+// (kbs: its block-scatter vector, blocks of four).  The packing launch hands
+// out groups of G consecutive units (G units of R rows make at least 256
+// tasks of eight values where R allows), `groups` of them.
+struct PackJob {
+  const float* x;
+  const int64_t* rs;
+  const int64_t* ks;
+  const int64_t* kbs;
+  int64_t rows, k, KT, units, groups;
+  int32_t R, G;
+  uint8_t* out;
+};
+inline void pack_job_groups(PackJob& j) {
+  j.G = j.R * 4 >= 256 ? 1 : 256 / (j.R * 4);
+  j.groups = (j.units + j.G - 1) / j.G;
+}
 
 // One unit of work of a batch: an output tile of a problem over one k-split.
 struct WorkItem {
@@ -174,11 +197,17 @@ struct TcLaunch {
   const int32_t* gate;  // checked launch: skip all work if *gate == kDevBounds (or null)
   void* pack_ws;  // single problem, packed form: tc_pack_bytes() bytes for the packed
                   // units of A and B (null: the gather or box form)
+  const PackJob* pack_jobs;    // batch, packed form: two jobs per problem (device), or null
+  const int64_t* pack_prefix;  // their prefix sums of unit groups (device, pack_njobs + 1)
+  int32_t pack_njobs;
+  int64_t pack_groups;
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
-// Workspace of the packed form: A's units (128 rows x 32 k, all pieces) then
-// B's (bn rows x 32 k), each part 256-byte aligned.
-size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces);
+// Workspace of the packed form: A's units (128 rows x 32 k, all pieces; the
+// pair form pads them to whole 256-row tiles) then B's (bn rows x 32 k; the
+// pair form: two half-tile units of bn / 2 rows, the same bytes), each part
+// 256-byte aligned.
+size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces, bool pair);
 
 // K6 on the FP64 path (f64.cu): persistent batched mainloop + FP64 reduction
 // of split problems.

@@ -56,6 +56,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "kernels.h"
 #include "sm100_ptx.cuh"
@@ -1088,39 +1089,58 @@ __global__ void k_reduce_partials(const DevProblem single, const DevProblem* pro
 // B), and the mainloop then has no loaders and no converters; the price is
 // one write and one read of the packed operands (as many bytes as the FP32
 // operands for two pieces).  The results equal k_tc's bit for bit.
-struct PackArgs {
-  const float* x;
-  const int64_t* rs;  // the operand's row scatter vector (rows entries)
-  const int64_t* ks;  // its scatter vector along the contracted range (k entries)
-  int64_t rows, k;
-  int32_t R;          // rows of a unit: 128 for A, the tile width bn for B
-  int64_t KT;         // k-tiles of the contracted range
-  int64_t units;      // row tiles x KT
-  uint8_t* out;
+// Units of every packing job in one launch: a single contraction's A and B
+// (jobs in the parameter block), or those of every problem of a batch (jobs
+// and their prefix sums of unit groups in device memory).
+struct PackLaunch {
+  PackJob local[2];
+  int64_t local_prefix[3];
+  const PackJob* jobs;    // batch: the jobs (device), or null
+  const int64_t* prefix;  // batch: prefix sums of the jobs' unit groups (device, njobs + 1)
+  int32_t njobs;
+  int64_t total;          // unit groups of all jobs
   const int32_t* gate;
 };
 
-// One CTA per unit; task c = (row r = c % R, k-chunk q = c / R) packs eight
-// values of one row (rows past the operand and k past its range are zeros).
+// Unit group g of a job.  Task c = (row r = c % R, k-chunk q = c / R) of a
+// unit packs eight values of one row (rows past the operand and k past its
+// range are zeros); eight elements that the block-scatter vector shows at
+// unit stride, from a 16-byte boundary, take two 16-byte loads.
 template <int NS>
-__global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
-  if (p.gate && *p.gate == kDevBounds) return;
-  const int R = p.R;
-  const int unit_bytes = NS * R * BK * 2;
-  for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
-  const int64_t tr = u / p.KT, kt = u % p.KT;
-  uint8_t* out = p.out + u * (int64_t)unit_bytes;
-  const int64_t k0 = kt * BK;
-  for (int c = threadIdx.x; c < R * (BK / 8); c += blockDim.x) {
+__device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
+  const int R = p.R, per_unit = R * (BK / 8);
+  const int64_t u0 = g * p.G;
+  const int nt = p.G * per_unit;
+  for (int tt = threadIdx.x; tt < nt; tt += blockDim.x) {
+    const int64_t u = u0 + tt / per_unit;
+    if (u >= p.units) break;
+    const int c = tt % per_unit;
     const int r = c % R, q = c / R;
+    const int64_t tr = u / p.KT, kt = u % p.KT;
+    uint8_t* out = p.out + u * (int64_t)(NS * R * BK * 2);
     const int64_t row = tr * R + r;
+    const int64_t kk0 = kt * BK + 8 * q;
     float v[8];
     if (row < p.rows) {
       const float* xr = p.x + __ldg(p.rs + row);
+      bool vec = false;
+      if (kk0 + 7 < p.k) {
+        const int64_t o = __ldg(p.ks + kk0);
+        if (__ldg(p.kbs + (kk0 >> 2)) == 1 && __ldg(p.kbs + (kk0 >> 2) + 1) == 1 &&
+            __ldg(p.ks + kk0 + 4) == o + 4 && (reinterpret_cast<uintptr_t>(xr + o) & 15) == 0) {
+          const float4 x0 = __ldg(reinterpret_cast<const float4*>(xr + o));
+          const float4 x1 = __ldg(reinterpret_cast<const float4*>(xr + o + 4));
+          v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+          v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+          vec = true;
+        }
+      }
+      if (!vec) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t kk = k0 + 8 * q + j;
-        v[j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
+        for (int j = 0; j < 8; ++j) {
+          const int64_t kk = kk0 + j;
+          v[j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
+        }
       }
     } else {
 #pragma unroll
@@ -1129,67 +1149,100 @@ __global__ void __launch_bounds__(256) k_pack(const PackArgs p) {
     split8_store<NS>(v, out, R * BK * 2,
                      (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16));
   }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackLaunch p) {
+  if (p.gate && *p.gate == kDevBounds) return;
+  for (int64_t g = blockIdx.x; g < p.total; g += gridDim.x) {
+    if (p.jobs) {
+      int lo = 0, hi = p.njobs;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(p.prefix + mid) <= g) lo = mid; else hi = mid;
+      }
+      const PackJob job = p.jobs[lo];
+      pack_group<NS>(job, g - __ldg(p.prefix + lo));
+    } else {
+      const int j = g < p.local_prefix[1] ? 0 : 1;
+      pack_group<NS>(p.local[j], g - p.local_prefix[j]);
+    }
   }
 }
 
 struct PackedArgs {
-  DevProblem single;
-  const uint8_t* pa;  // packed A units [tiles_m][KT][piece][128 x 32 bf16]
-  const uint8_t* pb;  // packed B units [tiles_n][KT][piece][bn x 32 bf16]
-  int64_t KT;         // k-tiles of the whole contracted range
+  DevProblem single;           // the problem of a single call (probs == null)
+  const DevProblem* probs;     // batch descriptors (device), or null
+  const WorkItem* items;       // batch work list (device), or null
   int64_t nitems, tiles_single;
   int32_t* err;
   const int32_t* gate;
-  int dbuf;  // every work item is one chunk: alternate two accumulators
   int fault;  // 1: injected timeout (see TcLaunch::fault)
 };
 
-constexpr int PK_THREADS = 192;  // producer warp, MMA warp, four epilogue warps
-constexpr int PK_EPI_W0 = 2;
+// Warps: producer, MMA, four epilogue warps; in the pair form also a relay
+// warp that tells the pair's MMA issuer when its CTA's stage has landed.
+constexpr int pk_threads(bool pair) { return pair ? 224 : 192; }
+constexpr int PK_EPI_W0 = 2, PK_RELAY_WARP = 6;
 
-template <int NS>
+// PAIR: CTA pairs (cta_group::2) on 256-row tiles; each CTA stages its own
+// 128 rows of A and half of the tile's B rows (B is packed in half-tile
+// units for it), which cuts every SM's operand bytes per k-tile by a quarter.
+// A stage holds U consecutive k-tiles (units) of both operands: with two
+// pieces, two k-tiles, so that each wait and commit of the MMA thread covers
+// twelve MMAs; the tensor core takes a new MMA only about as fast as it
+// finishes one, so the thread's fixed costs per stage (the barrier test, the
+// commit, the loop) otherwise leave it idle for a third of the time.
+template <int NS, bool PAIR = false>
 struct PLay {
-  static constexpr int A_BYTES = NS * BM * BK * 2;
-  static constexpr int B_BYTES = NS * BNMAX * BK * 2;  // room for the widest tile
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int NSTG = NS == 3 ? 4 : 6;
+  static constexpr int U = NS == 2 ? 2 : 1;
+  static constexpr int A_BYTES = NS * BM * BK * 2;  // one unit of A
+  static constexpr int B_BYTES = NS * (PAIR ? BNMAX / 2 : BNMAX) * BK * 2;  // the widest unit of B
+  static constexpr int STAGE = U * (A_BYTES + B_BYTES);  // U units of A, then U of B
+  static constexpr int NSTG = PAIR ? (NS == 3 ? 5 : 4) : (NS == 3 ? 4 : 3);
   static constexpr int SCAT = NSTG * STAGE;  // int64 rC[BM] cC[BNMAX]
   static constexpr int PROB = SCAT + (BM + BNMAX) * 8;
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
-  static constexpr int NBARS = 2 * NSTG + 5;
+  static constexpr int NBARS = 3 * NSTG + 5;
   static constexpr int MISC = BARS + NBARS * 8;
   static constexpr int END = MISC + 16;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
 };
 
-template <int NS>
-__global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ PackedArgs a) {
-  using Ly = PLay<NS>;
-  constexpr int NSTG = Ly::NSTG;
+template <int NS, bool PAIR>
+__global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_constant__ PackedArgs a) {
+  using Ly = PLay<NS, PAIR>;
+  constexpr int NSTG = Ly::NSTG, U = Ly::U;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   int64_t* sRC = reinterpret_cast<int64_t*>(smem + Ly::SCAT);
   int64_t* sCC = sRC + BM;
   DevProblem* sProb = reinterpret_cast<DevProblem*>(smem + Ly::PROB);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Ly::BARS);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Ly::BARS);  // this CTA's stage landed
   uint64_t* empty = full + NSTG;
-  uint64_t* acc_full = empty + NSTG;  // [2]
+  uint64_t* pfull = empty + NSTG;  // pair form, even CTA: both CTAs' stages landed
+  uint64_t* acc_full = pfull + NSTG;  // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
-  constexpr uint32_t PK_COLS = 2 * BNMAX;  // accumulator + running sum (or the second accumulator)
+  // Tensor Memory: two accumulators that chunks alternate between, so that
+  // the MMAs of a chunk run while the epilogue folds the previous one, and
+  // the running sum of a multi-chunk tile
+  constexpr uint32_t PK_COLS = 4 * BNMAX, PK_SUM = 2 * BNMAX;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < NSTG; ++s) {
       mbar_init(&full[s], 1);   // the producer's arrival, with the transaction count
-      mbar_init(&empty[s], 1);  // tcgen05.commit
+      mbar_init(&empty[s], 1);  // tcgen05.commit (pair form: multicast to both CTAs)
+      mbar_init(&pfull[s], 2);  // pair form: one relay arrival from each CTA
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], NEPI);
+      // pair form: the even CTA's also counts the odd CTA's epilogue threads
+      mbar_init(&acc_empty[b], (PAIR ? 2 : 1) * NEPI);
     }
     mbar_init(drain, 1);
     *abort = (a.gate && *a.gate == kDevBounds) ? 2 : 0;
@@ -1197,43 +1250,68 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, PK_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc2(tmem_slot, PK_COLS);
+      tmem_relinquish2();
+    } else {
+      tmem_alloc(tmem_slot, PK_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers exist before any remote arrival
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const DevProblem* d = sProb;
-  const int64_t nitems = a.nitems, w0 = blockIdx.x, dw = gridDim.x;
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+  // the pair form takes work items per pair: both CTAs the same ones
+  const int64_t nitems = a.nitems;
+  const int64_t w0 = PAIR ? blockIdx.x / 2 : blockIdx.x, dw = PAIR ? gridDim.x / 2 : gridDim.x;
   const uint32_t a_bytes = (uint32_t)Ly::A_BYTES;
-  const uint32_t b_bytes = (uint32_t)(NS * d->bn * BK * 2);
+  // work item w: a tile of the single problem, or entry w of the batch's list
+  // (longest first; the CTAs take them round robin)
   auto item = [&](int64_t w) {
-    return item_of_tile<false>(d, w % a.tiles_single, (int)(w / a.tiles_single));
+    if (a.probs) {
+      const WorkItem wi = a.items[w];
+      return item_of_tile<PAIR>(a.probs + wi.prob, wi.tile, wi.split, crank);
+    }
+    return item_of_tile<PAIR>(sProb, w % a.tiles_single, (int)(w / a.tiles_single), crank);
   };
 
   if (warp == 0) {
     // ---- producer: one lane streams the units of every work item ----
     if (lane == 0) {
       int64_t g = 0, g_iss = -1;
+      uint32_t st_i = 0, ph = 0;  // stage and phase parity of k-tile g
       bool failed = false;
       for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
         const Item it = item(w);
-        const uint8_t* ua = a.pa + ((it.m0 / BM) * a.KT + it.kbeg / BK) * (int64_t)a_bytes;
-        const uint8_t* ub = a.pb + ((it.n0 / d->bn) * a.KT + it.kbeg / BK) * (int64_t)b_bytes;
-        for (int64_t kt = 0; kt < it.KT; ++kt, ++g) {
-          const int s = (int)(g % NSTG);
-          if (!mbar_wait(&empty[s], (uint32_t)(((g / NSTG) & 1) ^ 1), abort)) {
+        const DevProblem* d = it.d;
+        const int64_t KT = (d->k + BK - 1) / BK;
+        // pair form: B in half-tile units, this CTA's half
+        const int rb = PAIR ? d->bn / 2 : d->bn;
+        const uint32_t b_bytes = (uint32_t)(NS * rb * BK * 2);
+        const int64_t ubi = PAIR ? (it.n0 / d->bn) * 2 + crank : it.n0 / d->bn;
+        const uint8_t* ua = d->pa + ((it.m0 / BM) * KT + it.kbeg / BK) * (int64_t)a_bytes;
+        const uint8_t* ub = d->pb + (ubi * KT + it.kbeg / BK) * (int64_t)b_bytes;
+        for (int64_t kt = 0; kt < it.KT; kt += U, ++g) {
+          const int s = (int)st_i;
+          const uint32_t nu = (uint32_t)(it.KT - kt < U ? it.KT - kt : U);  // units in this stage
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort)) {
             record_timeout(abort, a.err);
             failed = true;
             break;
           }
           const uint32_t st = smem_u32(smem + s * Ly::STAGE);
-          mbar_expect_tx(&full[s], a_bytes + b_bytes);
-          bulk_load(st, ua + kt * (int64_t)a_bytes, a_bytes, &full[s]);
-          bulk_load(st + Ly::A_BYTES, ub + kt * (int64_t)b_bytes, b_bytes, &full[s]);
+          mbar_expect_tx(&full[s], nu * (a_bytes + b_bytes));
+          bulk_load(st, ua + kt * (int64_t)a_bytes, nu * a_bytes, &full[s]);
+          bulk_load(st + U * Ly::A_BYTES, ub + kt * (int64_t)b_bytes, nu * b_bytes, &full[s]);
           mbar_arrive(&full[s]);
           g_iss = g;
+          if (++st_i == (uint32_t)NSTG) {
+            st_i = 0;
+            ph ^= 1u;
+          }
         }
       }
       // no copy may outlive the CTA (matters only after an abort): only the
@@ -1248,11 +1326,19 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
       }
     }
   } else if (warp == 1) {
-    // ---- MMA issue: the same products, in the same order, as k_tc ----
+    // ---- MMA issue: the same products, in the same order, as k_tc (pair
+    // form: the even CTA issues for both; the odd one only waits, before
+    // releasing Tensor Memory, for the MMAs writing it) ----
     if (lane == 0) {
-      int64_t g = 0, gc = 0;
+      int64_t gc = 0;
+      uint32_t st_i = 0, ph = 0;  // stage and phase parity of the next k-tile
       bool failed = false;
-      if (a.fault == 1) {
+      const bool issuer = !PAIR || crank == 0;
+      // matrix descriptors of stage 0; a stage's, piece's or k-slice's own
+      // descriptor adds its byte offset / 16 to the start-address field
+      // (shared-memory addresses stay below 256 KB: no carry out of it)
+      const uint64_t descA0 = smem_desc(smem_u32(smem), (BM / 8) * 128, 128);
+      if (issuer && a.fault == 1) {
         // injected failure: a bounded wait (about 10 ms) on a barrier nothing
         // arrives on yet; it expires, and the CTA unwinds through the abort path
         if (!mbar_wait(drain, 0, abort, 20000000LL)) {
@@ -1260,63 +1346,116 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
           failed = true;
         }
       }
-      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
+      for (int64_t w = w0; issuer && w < nitems && !*abort && !failed; w += dw) {
         const Item it = item(w);
-        const int bn = d->bn;
-        const uint32_t idesc = idesc_bf16_f32(BM, (uint32_t)bn);
+        const int bn = it.d->bn;
+        const int rb = PAIR ? bn / 2 : bn;  // B rows in each CTA's stage
+        const uint32_t idesc = idesc_bf16_f32(PAIR ? 2 * BM : BM, (uint32_t)bn);
+        const uint32_t b_bytes = (uint32_t)(NS * rb * BK * 2);  // one unit of B
+        const uint64_t descB0 =
+            smem_desc(smem_u32(smem) + U * Ly::A_BYTES, (uint32_t)(rb / 8) * 128, 128);
         for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
-          const int buf = a.dbuf ? (int)(gc & 1) : 0;
-          const int64_t use = a.dbuf ? gc >> 1 : gc;
-          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
+          const int buf = (int)(gc & 1);
+          const int64_t use = gc >> 1;  // earlier uses of this accumulator
+          if (use > 0 &&
+              !mbar_wait<PAIR>(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
             record_timeout(abort, a.err);
             failed = true;
             break;
           }
           tc_fence_after();
-          const uint32_t acc = tmem + (buf ? TM_SUM : TM_ACC);
+          const uint32_t acc = tmem + (uint32_t)buf * BNMAX;
           const int64_t kt0 = (int64_t)ch * CHUNK_KT;
           const int64_t kt1 = kt0 + CHUNK_KT < it.KT ? kt0 + CHUNK_KT : it.KT;
-          for (int64_t kt = kt0; kt < kt1; ++kt, ++g) {
-            const int s = (int)(g % NSTG);
-            if (!mbar_wait(&full[s], (uint32_t)((g / NSTG) & 1), abort)) {
+          for (int64_t kt = kt0; kt < kt1; kt += U) {
+            const int s = (int)st_i;
+            const int nu = (int)(kt1 - kt < U ? kt1 - kt : U);
+            if (!mbar_wait<PAIR>(PAIR ? &pfull[s] : &full[s], ph, abort)) {
               record_timeout(abort, a.err);
               failed = true;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * Ly::STAGE);
-            const uint32_t sb = sa + Ly::A_BYTES;
+            const uint64_t so = (uint64_t)((s * Ly::STAGE) >> 4);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              if (u >= nu) break;
 #pragma unroll
             for (int ksl = 0; ksl < BK / 16; ++ksl) {
               uint64_t dA[NS], dB[NS];
 #pragma unroll
               for (int i = 0; i < NS; ++i) {
-                dA[i] = smem_desc(sa + i * BM * BK * 2 + ksl * 2 * (BM / 8) * 128,
-                                  (BM / 8) * 128, 128);
-                dB[i] = smem_desc(sb + i * bn * BK * 2 + ksl * 2 * (bn / 8) * 128,
-                                  (uint32_t)(bn / 8) * 128, 128);
+                dA[i] = descA0 + so +
+                        (uint64_t)((u * Ly::A_BYTES + i * BM * BK * 2 + ksl * 2 * (BM / 8) * 128) >> 4);
+                dB[i] = descB0 + so +
+                        (uint64_t)((u * b_bytes + i * rb * BK * 2 + ksl * 2 * (rb / 8) * 128) >> 4);
               }
-              mma_bf16_ss(acc, dA[0], dB[0], idesc, (kt > kt0 || ksl > 0) ? 1u : 0u);
+              auto mma = [&](uint64_t da, uint64_t db, uint32_t accum) {
+                if constexpr (PAIR) mma_bf16_ss2(acc, da, db, idesc, accum);
+                else mma_bf16_ss(acc, da, db, idesc, accum);
+              };
+              mma(dA[0], dB[0], (kt + u > kt0 || ksl > 0) ? 1u : 0u);
 #pragma unroll
               for (int ts = 1; ts < NS; ++ts)
 #pragma unroll
-                for (int i = 0; i <= ts; ++i) mma_bf16_ss(acc, dA[i], dB[ts - i], idesc, 1u);
+                for (int i = 0; i <= ts; ++i) mma(dA[i], dB[ts - i], 1u);
             }
-            mma_commit(&empty[s]);
+            }
+            if constexpr (PAIR) mma_commit2(&empty[s], 0x3);  // both CTAs' stages
+            else mma_commit(&empty[s]);
+            if (++st_i == (uint32_t)NSTG) {
+              st_i = 0;
+              ph ^= 1u;
+            }
           }
           if (failed) break;
-          if (kt1 > kt0) mma_commit(&acc_full[buf]);
-          else mbar_arrive(&acc_full[buf]);
+          if (kt1 > kt0) {
+            if constexpr (PAIR) mma_commit2(&acc_full[buf], 0x3);
+            else mma_commit(&acc_full[buf]);
+          } else if constexpr (PAIR) {  // nothing to accumulate: hand over at once
+            mbar_arrive_cluster(&acc_full[buf], 0);
+            mbar_arrive_cluster(&acc_full[buf], 1);
+          } else {
+            mbar_arrive(&acc_full[buf]);
+          }
         }
       }
-      mma_commit(drain);
+      // every MMA the issuer issued has completed once this commit arrives
+      // (in the pair form on both CTAs' drain barriers)
+      if (issuer) {
+        if constexpr (PAIR) mma_commit2(drain, 0x3);
+        else mma_commit(drain);
+      }
       if (!mbar_wait(drain, 0, abort)) {
         const long long t0 = clock64();
         while (!mbar_try_wait(drain, 0) && clock64() - t0 < 4000000000LL) {
         }
       }
     }
-  } else {
+  } else if (PAIR && warp == PK_RELAY_WARP) {
+    // ---- relay (pair form): once this CTA's stage has landed, one arrival
+    // on the even CTA's pfull for it ----
+    if (lane == 0) {
+      uint32_t st_i = 0, ph = 0;
+      bool failed = false;
+      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
+        const Item it = item(w);
+        for (int64_t kt = 0; kt < it.KT; kt += U) {
+          const int s = (int)st_i;
+          if (!mbar_wait(&full[s], ph, abort)) {
+            record_timeout(abort, a.err);
+            failed = true;
+            break;
+          }
+          mbar_arrive_cluster(&pfull[s], 0);
+          if (++st_i == (uint32_t)NSTG) {
+            st_i = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp < PK_EPI_W0 + 4) {
     // ---- epilogue: one thread per accumulator row (as in k_tc) ----
     const int t = tid - PK_EPI_W0 * 32;
     const int wq = warp & 3;
@@ -1325,11 +1464,11 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
     constexpr int NB = BNMAX / NEPI;
     int64_t pre_r = 0, pre_c[NB];
     auto fetch_rows = [&](const Item& it) {
-      pre_r = t < it.rows_a ? __ldg(d->sp.rC + it.m0 + t) : 0;
+      pre_r = t < it.rows_a ? __ldg(it.d->sp.rC + it.m0 + t) : 0;
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
         const int c = t + i * NEPI;
-        pre_c[i] = c < it.rows_b ? __ldg(d->sp.cC + it.n0 + c) : 0;
+        pre_c[i] = c < it.rows_b ? __ldg(it.d->sp.cC + it.n0 + c) : 0;
       }
     };
     int64_t w = w0;
@@ -1338,6 +1477,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
     for (;;) {
       if (bar_or(BAR_EPI, NEPI, *abort || w >= nitems)) break;
       const Item it = item(w);
+      const DevProblem* d = it.d;
       sRC[t] = pre_r;
 #pragma unroll
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
@@ -1378,16 +1518,18 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
       };
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
-        const int buf = a.dbuf ? (int)(gc & 1) : 0;
-        const uint32_t use = (uint32_t)(a.dbuf ? gc >> 1 : gc);
+        const int buf = (int)(gc & 1);
+        const uint32_t use = (uint32_t)(gc >> 1);
         if (have && !*abort) {
-          if (!mbar_wait(&acc_full[buf], use & 1u, abort)) record_timeout(abort, a.err);
+          if (!mbar_wait<PAIR>(&acc_full[buf], use & 1u, abort)) record_timeout(abort, a.err);
         }
         tc_fence_after();
         ok = __all_sync(0xffffffffu, !*abort);
-        const bool direct_out = a.dbuf || (first && last && it.KT <= 4);
+        // a one-chunk tile is written straight from its accumulator; longer
+        // ones are folded into the running sum chunk by chunk
+        const bool direct_out = first && last;
+        const uint32_t accc = (uint32_t)buf * BNMAX;
         if (ok && direct_out) {
-          const uint32_t accc = buf ? TM_SUM : TM_ACC;
           float z[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) z[q] = 0.f;
@@ -1411,7 +1553,7 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
           for (int cb = 0; cb < bn; cb += 8) {
             float v[8], sum[8];
             if (have) {
-              tmem_ld8(lane_base + TM_ACC + (uint32_t)cb, v);
+              tmem_ld8(lane_base + accc + (uint32_t)cb, v);
             } else {
 #pragma unroll
               for (int q = 0; q < 8; ++q) v[q] = 0.f;
@@ -1420,23 +1562,24 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
 #pragma unroll
               for (int q = 0; q < 8; ++q) sum[q] = v[q];
             } else {
-              tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
+              tmem_ld8(lane_base + PK_SUM + (uint32_t)cb, sum);
 #pragma unroll
               for (int q = 0; q < 8; ++q) sum[q] = __fadd_rn(sum[q], v[q]);
             }
-            tmem_st8(lane_base + TM_SUM + (uint32_t)cb, sum);
+            tmem_st8(lane_base + PK_SUM + (uint32_t)cb, sum);
           }
           tmem_st_wait();
         }
         tc_fence_before();
-        mbar_arrive(&acc_empty[buf]);
+        if constexpr (PAIR) mbar_arrive_cluster(&acc_empty[buf], 0);
+        else mbar_arrive(&acc_empty[buf]);
         if (!ok) break;
         if (!last || direct_out) continue;
         for (int cb = 0; cb < bn; cb += 8) {
           float sum[8], z[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) z[q] = 0.f;
-          tmem_ld8(lane_base + TM_SUM + (uint32_t)cb, sum);
+          tmem_ld8(lane_base + PK_SUM + (uint32_t)cb, sum);
           out8(cb, sum, z);
         }
       }
@@ -1445,9 +1588,11 @@ __global__ void __launch_bounds__(PK_THREADS, 1) k_tcp(const __grid_constant__ P
 
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs are done with both Tensor Memories
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, PK_COLS);
+    if constexpr (PAIR) tmem_dealloc2(tmem, PK_COLS);
+    else tmem_dealloc(tmem, PK_COLS);
   }
 }
 
@@ -1542,65 +1687,106 @@ cudaError_t launch_reduce(const TcLaunch& q, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t pack_a_bytes(int64_t m, int64_t k, int pieces) {
-  return align_up((size_t)((m + BM - 1) / BM) * (size_t)((k + BK - 1) / BK) * pieces * BM * BK * 2,
+// A's row units: 128 rows each; the pair form pads them to whole 256-row tiles.
+int64_t pack_a_units(int64_t m, bool pair) { return pair ? 2 * ((m + 2 * BM - 1) / (2 * BM)) : (m + BM - 1) / BM; }
+
+size_t pack_a_bytes(int64_t m, int64_t k, int pieces, bool pair) {
+  return align_up((size_t)pack_a_units(m, pair) * (size_t)((k + BK - 1) / BK) * pieces * BM * BK * 2,
                   256);
 }
 
-template <int NS>
+template <int NS, bool PAIR>
 cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_tcp<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         PLay<NS>::ALLOC);
+    cudaError_t e = cudaFuncSetAttribute(k_tcp<NS, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PLay<NS, PAIR>::ALLOC);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const DevProblem& d = q.single;
-  const int64_t KT = (d.k + BK - 1) / BK;
-  const int64_t tm = (d.m + BM - 1) / BM, tn = d.tiles_n;
-  if (KT == 0 || tm == 0 || tn == 0) return cudaSuccess;
-  uint8_t* pa = static_cast<uint8_t*>(q.pack_ws);
-  uint8_t* pb = pa + pack_a_bytes(d.m, d.k, NS);
-  mainloop_event_before(s);
-  const int64_t pack_grid_max = (int64_t)q.ctas * 8;
-  PackArgs pk;
-  pk.x = static_cast<const float*>(d.a);
-  pk.rs = d.sp.rA;
-  pk.ks = d.sp.cA;
-  pk.rows = d.m;
-  pk.k = d.k;
-  pk.R = BM;
-  pk.KT = KT;
-  pk.units = tm * KT;
-  pk.out = pa;
+  PackLaunch pk;
+  std::memset(&pk, 0, sizeof pk);
   pk.gate = q.gate;
-  k_pack<NS><<<(unsigned)std::min(pk.units, pack_grid_max), 256, 0, s>>>(pk);
-  note_launch();
-  pk.x = static_cast<const float*>(d.b);
-  pk.rs = d.sp.cB;
-  pk.ks = d.sp.rB;
-  pk.rows = d.n;
-  pk.R = d.bn;
-  pk.units = tn * KT;
-  pk.out = pb;
-  k_pack<NS><<<(unsigned)std::min(pk.units, pack_grid_max), 256, 0, s>>>(pk);
-  note_launch();
   PackedArgs a;
-  a.single = d;
-  a.pa = pa;
-  a.pb = pb;
-  a.KT = KT;
-  a.tiles_single = tm * tn;
-  a.nitems = a.tiles_single * d.splits;
+  std::memset(&a, 0, sizeof a);
+  a.single = q.single;
+  if (q.probs) {
+    pk.jobs = q.pack_jobs;
+    pk.prefix = q.pack_prefix;
+    pk.njobs = q.pack_njobs;
+    pk.total = q.pack_groups;
+    a.probs = q.probs;
+    a.items = q.items;
+    a.nitems = q.nitems;
+    a.tiles_single = 1;
+  } else {
+    DevProblem& d = a.single;
+    const int64_t KT = (d.k + BK - 1) / BK;
+    const int64_t tm = pack_a_units(d.m, PAIR), tn = d.tiles_n;
+    if (KT == 0 || tm == 0 || tn == 0) return cudaSuccess;
+    d.pa = static_cast<const uint8_t*>(q.pack_ws);
+    d.pb = d.pa + pack_a_bytes(d.m, d.k, NS, PAIR);
+    PackJob& ja = pk.local[0];
+    ja.x = static_cast<const float*>(d.a);
+    ja.rs = d.sp.rA;
+    ja.ks = d.sp.cA;
+    ja.kbs = d.sp.cbsA;
+    ja.rows = d.m;
+    ja.k = d.k;
+    ja.R = BM;
+    ja.KT = KT;
+    ja.units = tm * KT;
+    ja.out = const_cast<uint8_t*>(d.pa);
+    PackJob& jb = pk.local[1];
+    jb = ja;
+    jb.x = static_cast<const float*>(d.b);
+    jb.rs = d.sp.cB;
+    jb.ks = d.sp.rB;
+    jb.kbs = d.sp.rbsB;
+    jb.rows = d.n;
+    jb.R = PAIR ? d.bn / 2 : d.bn;  // pair form: half-tile units, one per CTA
+    jb.units = (PAIR ? 2 : 1) * tn * KT;
+    jb.out = const_cast<uint8_t*>(d.pb);
+    pack_job_groups(ja);
+    pack_job_groups(jb);
+    pk.local_prefix[1] = ja.groups;
+    pk.local_prefix[2] = pk.total = ja.groups + jb.groups;
+    a.tiles_single = (PAIR ? tm / 2 : tm) * tn;
+    a.nitems = a.tiles_single * d.splits;
+  }
+  if (a.nitems == 0) return cudaSuccess;
   a.err = q.err;
   a.gate = q.gate;
-  a.dbuf = d.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0;
   a.fault = q.fault;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
-  k_tcp<NS><<<(unsigned)grid, PK_THREADS, PLay<NS>::ALLOC, s>>>(a);
+  mainloop_event_before(s);
+  if (pk.total > 0) {
+    k_pack<NS><<<(unsigned)std::min<int64_t>(pk.total, (int64_t)q.ctas * 8), 256, 0, s>>>(pk);
+    note_launch();
+  }
+  if constexpr (PAIR) {
+    // clusters of two CTAs, one pair per work item at a time
+    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(q.ctas / 2, a.nitems));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+    cfg.blockDim = dim3(pk_threads(true), 1, 1);
+    cfg.dynamicSmemBytes = PLay<NS, true>::ALLOC;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tcp<NS, true>, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(q.ctas, a.nitems));
+    k_tcp<NS, false><<<(unsigned)grid, pk_threads(false), PLay<NS, false>::ALLOC, s>>>(a);
+  }
   note_launch();
   const cudaError_t e = launch_reduce(q, s);
   mainloop_event_after(s);
@@ -1610,10 +1796,10 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
 }  // namespace
 
 int tc_bn_max() { return BNMAX; }
-size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces) {
+size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces, bool pair) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
   const size_t b = (size_t)((n + bn - 1) / bn) * (size_t)((k + BK - 1) / BK) * pieces * bn * BK * 2;
-  return pack_a_bytes(m, k, pieces) + align_up(b, 256);
+  return pack_a_bytes(m, k, pieces, pair) + align_up(b, 256);
 }
 int tc_max_item_ktiles() { return MAX_CHUNKS * CHUNK_KT; }
 
@@ -1621,8 +1807,11 @@ cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s) {
   // boxes only when every work item has both operands as boxes (the planner
   // sets both or neither; batch plans set neither); the pair form only with
   // boxes planned for it (B boxes half the tile wide)
-  if (!q.probs && q.pack_ws)
-    return q.pieces == 3 ? launch_packed<3>(q, s) : launch_packed<2>(q, s);
+  if (q.probs ? q.pack_jobs != nullptr : q.pack_ws != nullptr) {
+    const bool pp = !q.probs && q.single.pair;  // batches: single CTAs
+    if (q.pieces == 3) return pp ? launch_packed<3, true>(q, s) : launch_packed<3, false>(q, s);
+    return pp ? launch_packed<2, true>(q, s) : launch_packed<2, false>(q, s);
+  }
   const bool box = !q.probs && q.single.boxA.rank > 0 && q.single.boxB.rank > 0;
   const bool pair = box && q.single.pair;
   if (q.pieces == 3)

@@ -144,9 +144,10 @@ def test_forms_full_size_spiky():
 
 
 def test_batched_plans_under_every_access_setting():
-    # batch plans gather every operand whatever the setting (their box form is
-    # disabled); a plan created under each setting, executed and replayed from
-    # a CUDA graph, gives the same bits and matches the oracle
+    # batch plans gather every operand under the box, block and scatter
+    # settings (their box form is disabled) and pack them under "packed"; a
+    # plan created under each setting, executed and replayed from a CUDA
+    # graph, gives the same bits and matches the oracle
     g = torch.Generator().manual_seed(10)
     probs = []
     for name in sorted(CASES):
@@ -155,7 +156,7 @@ def test_batched_plans_under_every_access_setting():
         C0 = colmajor_rand(lC, ext, g)
         probs.append((A, lA, B, lB, C0, lC))
     outs = {}
-    for acc in FORMS:
+    for acc in FORMS + ("packed",):
         with tc.access(acc):
             dev = [(to_device(A, torch.float32), lA, to_device(B, torch.float32), lB,
                     to_device(C0, torch.float32), lC, 0.5, 1.0) for A, lA, B, lB, C0, lC in probs]
@@ -182,5 +183,6 @@ def test_batched_plans_under_every_access_setting():
     for i, (A, lA, B, lB, C0, lC) in enumerate(probs):
         a = outs["box"][i]
         assert torch.equal(a, outs["block"][i]) and torch.equal(a, outs["scatter"][i]), lA
+        assert torch.equal(a, outs["packed"][i]), lA
         ref, mag = oracle_ref(0.5, A, lA, B, lB, 1.0, C0, lC)
         assert norm_err(a.cpu().double().numpy(), ref, mag) <= TOLS["bf16x3"]

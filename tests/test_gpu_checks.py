@@ -103,8 +103,15 @@ def test_short_range_fires_on_the_scale_only_path(monkeypatch):
     assert torch.equal(dC.cpu(), C0 * 0.5)
 
 
-@pytest.mark.parametrize("mode,dt", [("f64", torch.float64), ("bf16x3", torch.float32)])
-def test_checked_batch_plan(monkeypatch, mode, dt):
+@pytest.mark.parametrize("mode,dt,acc", [("f64", torch.float64, "auto"),
+                                         ("bf16x3", torch.float32, "auto"),
+                                         ("bf16x3", torch.float32, "packed")])
+def test_checked_batch_plan(monkeypatch, mode, dt, acc):
+    with tc.access(acc):
+        _checked_batch_plan(monkeypatch, mode, dt)
+
+
+def _checked_batch_plan(monkeypatch, mode, dt):
     rng = np.random.default_rng(12)
     probs = [W.random_problem(rng, ext=(3, 24)) for _ in range(12)]
     host = [W.make_random_inputs(p, seed=300 + i, dtype=dt) for i, p in enumerate(probs)]
@@ -219,8 +226,10 @@ def test_writes_stay_inside_C(mode, dt, access, shape_seed):
     assert norm_err(dC.cpu().double().numpy(), ref, mag) <= tol
 
 
-@pytest.mark.parametrize("mode,dt", [("f64", torch.float64), ("bf16x3", torch.float32)])
-def test_batch_writes_stay_inside_C(mode, dt):
+@pytest.mark.parametrize("mode,dt,acc", [("f64", torch.float64, "auto"),
+                                         ("bf16x3", torch.float32, "auto"),
+                                         ("bf16x3", torch.float32, "packed")])
+def test_batch_writes_stay_inside_C(mode, dt, acc):
     rng = np.random.default_rng(61)
     probs = [W.random_problem(rng, ext=(3, 30), max_elems=1 << 16) for _ in range(10)]
     calls, guards = [], []
@@ -229,7 +238,8 @@ def test_batch_writes_stay_inside_C(mode, dt):
         buf, dC, mask = _guarded_c(tuple(p.ext[x] for x in p.labC), dt, pad=2)
         guards.append((buf, mask, _nan_bits(buf)[~mask].clone(), h))
         calls.append((to_device(h["A"], dt), p.labA, to_device(h["B"], dt), p.labB, dC, p.labC, 1.0, 0.0))
-    pl = tc.Plan(calls, mode=mode)
+    with tc.access(acc):
+        pl = tc.Plan(calls, mode=mode)
     pl.execute()
     torch.cuda.synchronize()
     assert tc.device_error() == 0

@@ -10,7 +10,8 @@ bound.  Covered: every layout of the box-form cases (row- and k-contiguous
 operands, tails in m, n and k, multi-dim row tiles), both modes with alpha and
 beta, NaN in C with beta = 0, k-splits, narrow tiles (B units of 16 and 64
 rows), the benchmark strings at reduced extents, device-side checks, and the
-full-size 4096^3 contraction."""
+full-size 4096^3 contraction; and the form on CTA pairs against the
+single-CTA form, bit for bit."""
 import zlib
 
 import numpy as np
@@ -148,3 +149,31 @@ def test_packed_full_size_spiky():
             assert tc.device_error() == 0
             res[acc] = dC
     assert torch.equal(res["box"], res["packed"])
+
+
+from test_gpu_pair import CASES as PAIR_CASES  # noqa: E402
+
+
+@pytest.mark.parametrize("mode", sorted(TOLS))
+@pytest.mark.parametrize("name", sorted(PAIR_CASES))
+def test_packed_pair_matches_single_cta(monkeypatch, name, mode):
+    # the packed form on CTA pairs (TC_PAIR=1: 256-row tiles, each CTA its
+    # 128 rows of A and a half-tile unit of B) against the single-CTA packed
+    # form: the same sums in the same order, bit for bit; and the oracle
+    lA, lB, lC, ext = PAIR_CASES[name]
+    g = torch.Generator().manual_seed(zlib.crc32(name.encode()) % 1000 + 3)
+    A, B = colmajor_rand(lA, ext, g), colmajor_rand(lB, ext, g)
+    C0 = colmajor_rand(lC, ext, g)
+    dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
+    out = {}
+    with tc.access("packed"):
+        for pair in ("1", "0"):
+            monkeypatch.setenv("TC_PAIR", pair)
+            dC = to_device(C0, torch.float32)
+            tc.contract(dA, lA, dB, lB, dC, lC, alpha=0.5, beta=-1.5, mode=mode)
+            torch.cuda.synchronize()
+            assert tc.device_error() == 0
+            out[pair] = dC.cpu().double().numpy()
+    assert np.array_equal(out["1"], out["0"])
+    ref, mag = oracle_ref(0.5, A, lA, B, lB, -1.5, C0, lC)
+    assert norm_err(out["1"], ref, mag) <= TOLS[mode]
