@@ -175,9 +175,13 @@ TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, cons
  * 2, 4, 8 and 16; the timed runs write scratch copies of the outputs (the
  * caller's C is not touched) and their results are kept for the process and
  * in the cache file.  Untuned: least-padding FP64 tiles, tensor-core tiles
- * covering n, D = 4.  tc_plan_execute only enqueues work -- kernels and
- * the memset of the work counters -- with no host synchronisation and no
- * allocation, so it can be captured in a CUDA graph. */
+ * covering n, D = 4.  The plan's scatter vectors (K1) depend on the layouts
+ * alone: tc_plan_create builds them on the device, on the legacy default
+ * stream, and returns once they are built.  tc_plan_execute only enqueues
+ * work -- the device-side checks if they were on at creation, the packing,
+ * mainloop and reduction kernels and the memset of the work counters -- with
+ * no host synchronisation and no allocation, so it can be captured in a CUDA
+ * graph. */
 TC_API int tc_plan_create(tc_dtype dtype, tc_mode mode, int32_t count, const tc_problem* probs,
                    tc_plan** out);
 TC_API int tc_plan_workspace_size(const tc_plan* plan, size_t* bytes);

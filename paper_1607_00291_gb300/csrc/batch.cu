@@ -787,6 +787,13 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     for (int i = 0; i < np; ++i) cb[i] = check_bounds(lay[i]);
     if (!up(pl->d_bounds, cb.data(), sizeof(CheckBounds) * np)) return TC_ERR_CUDA;
   }
+  // K1 once per plan: the scatter vectors depend on the layouts alone, so
+  // every execution reads the ones built here (the call returns once they
+  // are built)
+  if (np > 0 && (launch_build_scatter_batched(pl->d_layouts, pl->d_offs, np, pl->total_scatter,
+                                               kBsBlock, pl->d_scat, 0) != cudaSuccess ||
+                 cudaStreamSynchronize(0) != cudaSuccess))
+    return TC_ERR_CUDA;
   return TC_OK;
 }
 
@@ -929,9 +936,6 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
   const int np = (int)plan->planned.size();
   if (np == 0) return TC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (launch_build_scatter_batched(plan->d_layouts, plan->d_offs, np, plan->total_scatter,
-                                   kBsBlock, plan->d_scat, s) != cudaSuccess)
-    return TC_ERR_CUDA;
   const int32_t* gate = nullptr;
   if (plan->checks) {
     int32_t* ew = err_word();
