@@ -1205,9 +1205,15 @@ struct PLay {
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
   static constexpr int NBARS = 3 * NSTG + 5;
   static constexpr int MISC = BARS + NBARS * 8;
-  static constexpr int END = MISC + 16;
+  // decoded work items: the producer decodes each item once (for a batch,
+  // from the work list and the problem's descriptor in device memory) and
+  // hands it to the other roles through a ring in shared memory
+  static constexpr int QRP = 16;
+  static constexpr int RING = MISC + 16;  // Item[QRP], then QRP full and QRP empty barriers
+  static constexpr int END = RING + QRP * (int)sizeof(Item) + 2 * QRP * 8;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
+  static_assert(sizeof(Item) % 8 == 0 && (QRP & (QRP - 1)) == 0, "item ring layout");
 };
 
 template <int NS, bool PAIR>
@@ -1227,6 +1233,10 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Ly::MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + Ly::MISC + 4);
+  constexpr int QRP = Ly::QRP;
+  Item* ring = reinterpret_cast<Item*>(smem + Ly::RING);
+  uint64_t* ring_full = reinterpret_cast<uint64_t*>(smem + Ly::RING + QRP * sizeof(Item));
+  uint64_t* ring_empty = ring_full + QRP;
   // Tensor Memory: two accumulators that chunks alternate between, so that
   // the MMAs of a chunk run while the epilogue folds the previous one, and
   // the running sum of a multi-chunk tile
@@ -1245,6 +1255,11 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       mbar_init(&acc_empty[b], (PAIR ? 2 : 1) * NEPI);
     }
     mbar_init(drain, 1);
+    for (int q = 0; q < QRP; ++q) {
+      mbar_init(&ring_full[q], 1);
+      // read by the MMA thread, the four epilogue warps and (pair form) the relay
+      mbar_init(&ring_empty[q], 5 + (PAIR ? 1 : 0));
+    }
     *abort = (a.gate && *a.gate == kDevBounds) ? 2 : 0;
     *sProb = a.single;
     fence_mbar_init();
@@ -1277,6 +1292,18 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
     }
     return item_of_tile<PAIR>(sProb, w % a.tiles_single, (int)(w / a.tiles_single), crank);
   };
+  // this CTA's j-th item from the ring (false at the end of its items, or on
+  // a timeout); the caller releases the entry with ring_release once read
+  auto ring_get = [&](int64_t j, Item& out) -> bool {
+    const int q = (int)(j & (QRP - 1));
+    if (!mbar_wait(&ring_full[q], (uint32_t)((j / QRP) & 1), abort)) {
+      record_timeout(abort, a.err);
+      return false;
+    }
+    out = ring[q];
+    return out.d != nullptr;
+  };
+  auto ring_release = [&](int64_t j) { mbar_arrive(&ring_empty[j & (QRP - 1)]); };
 
   if (warp == 0) {
     // ---- producer: one lane streams the units of every work item ----
@@ -1284,8 +1311,36 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       int64_t g = 0, g_iss = -1;
       uint32_t st_i = 0, ph = 0;  // stage and phase parity of k-tile g
       bool failed = false;
-      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
-        const Item it = item(w);
+      // Item j + 1 is published before item j's stages are streamed: the
+      // epilogue reads one item ahead (to fetch its rows and columns), and
+      // item j's stages reach it only through the epilogue's release of
+      // earlier accumulators.  An entry with d == null ends the sequence.
+      auto decode = [&](int64_t w) {
+        Item x;
+        if (w < nitems) {
+          x = item(w);
+        } else {
+          std::memset(&x, 0, sizeof x);
+        }
+        return x;
+      };
+      auto publish = [&](int64_t j, const Item& x) {
+        const int q = (int)(j & (QRP - 1));
+        if (!mbar_wait(&ring_empty[q], (uint32_t)(((j / QRP) & 1) ^ 1), abort)) {
+          record_timeout(abort, a.err);
+          return false;
+        }
+        ring[q] = x;
+        mbar_arrive(&ring_full[q]);
+        return true;
+      };
+      Item nx = decode(w0);
+      bool pub = publish(0, nx);
+      for (int64_t j = 0; pub && !*abort && !failed; ++j) {
+        const Item it = nx;
+        if (it.d == nullptr) break;
+        nx = decode(w0 + (j + 1) * dw);
+        if (!(pub = publish(j + 1, nx))) break;
         const DevProblem* d = it.d;
         const int64_t KT = (d->k + BK - 1) / BK;
         // pair form: B in half-tile units, this CTA's half
@@ -1346,8 +1401,12 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           failed = true;
         }
       }
-      for (int64_t w = w0; issuer && w < nitems && !*abort && !failed; w += dw) {
-        const Item it = item(w);
+      for (int64_t j = 0; !*abort && !failed; ++j) {
+        Item it;
+        const bool got = ring_get(j, it);
+        ring_release(j);
+        if (!got) break;
+        if (!issuer) continue;  // pair form, odd CTA: only keeps the ring moving
         const int bn = it.d->bn;
         const int rb = PAIR ? bn / 2 : bn;  // B rows in each CTA's stage
         const uint32_t idesc = idesc_bf16_f32(PAIR ? 2 * BM : BM, (uint32_t)bn);
@@ -1438,8 +1497,11 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
     if (lane == 0) {
       uint32_t st_i = 0, ph = 0;
       bool failed = false;
-      for (int64_t w = w0; w < nitems && !*abort && !failed; w += dw) {
-        const Item it = item(w);
+      for (int64_t j = 0; !*abort && !failed; ++j) {
+        Item it;
+        const bool got = ring_get(j, it);
+        ring_release(j);
+        if (!got) break;
         for (int64_t kt = 0; kt < it.KT; kt += U) {
           const int s = (int)st_i;
           if (!mbar_wait(&full[s], ph, abort)) {
@@ -1471,18 +1533,27 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
         pre_c[i] = c < it.rows_b ? __ldg(it.d->sp.cC + it.n0 + c) : 0;
       }
     };
-    int64_t w = w0;
-    if (w < nitems) fetch_rows(item(w));
+    // item j from the ring, read by every lane, released once per warp
+    auto get = [&](int64_t j, Item& out) {
+      const bool got = ring_get(j, out);
+      __syncwarp();
+      if (lane == 0) ring_release(j);
+      return got;
+    };
+    Item cur, nxt;
+    bool got_cur = get(0, cur);
+    if (got_cur) fetch_rows(cur);
     int64_t gc = 0;
-    for (;;) {
-      if (bar_or(BAR_EPI, NEPI, *abort || w >= nitems)) break;
-      const Item it = item(w);
+    for (int64_t j = 0;; ++j) {
+      if (bar_or(BAR_EPI, NEPI, !got_cur || *abort)) break;  // uniform exit
+      const Item it = cur;
       const DevProblem* d = it.d;
       sRC[t] = pre_r;
 #pragma unroll
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
-      w += dw;
-      if (w < nitems) fetch_rows(item(w));
+      // the next item's row and column entries are fetched one item ahead
+      const bool have_next = get(j + 1, nxt);
+      if (have_next) fetch_rows(nxt);
       bar_sync(BAR_EPI, NEPI);
       const bool have = it.KT > 0;
       const int bn = d->bn;
@@ -1583,6 +1654,8 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           out8(cb, sum, z);
         }
       }
+      cur = nxt;
+      got_cur = have_next;
     }
   }
 
