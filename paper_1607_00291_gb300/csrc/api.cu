@@ -130,6 +130,8 @@ struct WsLayout {
   bool pack_pair;               // packed form on CTA pairs
   size_t total;
   TcChoice tcc;
+  Layout L;       // the layout the kernels run on: the planned one, or its
+  bool blocked;   // blocked row bundle (packed form, block_row_bundle)
 };
 
 // The packed form on CTA pairs only under TC_PAIR=1: the pairs cut each SM's
@@ -186,10 +188,8 @@ bool packed_form(const Planned& p, const TcChoice& c) {
 
 WsLayout ws_layout(const Planned& p, tc_mode mode) {
   WsLayout w;
-  const ScatterOffsets o = scatter_offsets(p.L, kBsBlock);
-  w.scatter_off = 0;
-  w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
-  w.partial_off = w.scatter_bytes;
+  w.L = p.L;
+  w.blocked = false;
   w.partial_bytes = 0;
   w.pack_bytes = 0;
   w.pack_pair = false;
@@ -202,15 +202,28 @@ WsLayout ws_layout(const Planned& p, tc_mode mode) {
       const int v = std::atoi(e);
       if (v >= 16 && v % 16 == 0 && v <= tc_bn_max()) force = v;
     }
-    w.tcc = choose_tc(p.L, mode == TC_MODE_BF16X6 ? 3 : 2, sm_count(), force);
-    if (w.tcc.splits > 1)
-      w.partial_bytes = align_up((size_t)w.tcc.splits * p.L.m * p.L.n * sizeof(float), 256);
+    const int pieces = mode == TC_MODE_BF16X6 ? 3 : 2;
+    w.tcc = choose_tc(p.L, pieces, sm_count(), force);
     if (packed_form(p, w.tcc)) {
       w.pack_pair = packed_pair(p.L, w.tcc, sm_count());
-      w.pack_bytes = tc_pack_bytes(p.L.m, p.L.n, p.L.k, w.tcc.bn, mode == TC_MODE_BF16X6 ? 3 : 2,
-                                   w.pack_pair);
+      // single-CTA packed tiles: rows blocked 16 x 8 where A's and C's
+      // unit strides lie in different row dims (the packing then reads A in
+      // runs of eight, the epilogue writes C in runs of sixteen)
+      Layout lb;
+      if (!w.pack_pair && block_row_bundle(p.L, p.info.a_k_contig != 0, &lb)) {
+        w.L = lb;
+        w.blocked = true;
+        w.tcc = choose_tc(w.L, pieces, sm_count(), force);
+      }
+      w.pack_bytes = tc_pack_bytes(w.L.m, w.L.n, w.L.k, w.tcc.bn, pieces, w.pack_pair);
     }
+    if (w.tcc.splits > 1)
+      w.partial_bytes = align_up((size_t)w.tcc.splits * w.L.m * w.L.n * sizeof(float), 256);
   }
+  const ScatterOffsets o = scatter_offsets(w.L, kBsBlock);
+  w.scatter_off = 0;
+  w.scatter_bytes = align_up((size_t)o.total * sizeof(int64_t), 256);
+  w.partial_off = w.scatter_bytes;
   if (mode == TC_MODE_F64 && p.L.k > 0) {
     const int sms = sm_count();
     if (f64_grid(p.L.m, p.L.n, p.L.k, sms, true) != f64_grid(p.L.m, p.L.n, p.L.k, 0, false))
@@ -231,9 +244,9 @@ int plan_checked(tc_dtype dt, const tc_tensor* A, const tc_tensor* B, const tc_t
 
 int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Planned& p,
                 void* ws, size_t ws_bytes, cudaStream_t s) {
-  const Layout& L = p.L;
-  if (L.m == 0 || L.n == 0) return TC_OK;
+  if (p.L.m == 0 || p.L.n == 0) return TC_OK;
   const WsLayout w = ws_layout(p, mode);
+  const Layout& L = w.L;  // the planned layout, or its blocked row bundle
   if (ws_bytes < w.total || (w.total > 0 && ws == nullptr) ||
       (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
     return TC_ERR_WORKSPACE;
@@ -245,7 +258,9 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
   const int32_t* gate = nullptr;
   if (checks_on()) {
     int32_t* e = err_word();
-    if (!e || launch_check_scatter(L, kBsBlock, scat, check_bounds(L), e, s) != cudaSuccess)
+    // the ranges come from the planned layout (a blocked bundle's dims reach
+    // past the operand only at its holes)
+    if (!e || launch_check_scatter(L, kBsBlock, scat, check_bounds(p.L), e, s) != cudaSuccess)
       return TC_ERR_CUDA;
     gate = e;
   }
@@ -277,18 +292,20 @@ int run_planned(tc_dtype dt, tc_mode mode, double alpha, double beta, const Plan
     q.reduce_f64 = split_reduction_f64() ? 1 : 0;
     q.pack_ws = w.pack_bytes > 0 ? static_cast<char*>(ws) + w.pack_off : nullptr;
     if (q.pack_ws) d.pair = w.pack_pair ? 1 : 0;
+    d.rows_blocked = w.blocked ? 1 : 0;
     q.ctas = sm_count();
     q.err = err_word();
     q.gate = gate;
     if (log_enabled())
       std::fprintf(stderr,
                    "[libtc] contract: %s data, %s, m=%lld n=%lld k=%lld, tile %dx%d, %d k-split(s), "
-                   "access %s%s%s\n",
+                   "access %s%s%s%s\n",
                    dt == TC_F64 ? "f64" : "f32", mode == TC_MODE_BF16X6 ? "bf16x6" : "bf16x3",
                    (long long)L.m, (long long)L.n, (long long)L.k, d.pair ? 256 : 128, d.bn,
                    d.splits, q.pack_ws ? "packed units" : d.boxA.rank > 0 ? "TMA boxes"
                                         : d.elem_gather ? "element gathers" : "block gathers",
-                   d.pair ? " on CTA pairs" : "", gate ? ", checked" : "");
+                   d.pair ? " on CTA pairs" : "", w.blocked ? ", rows blocked 16 x 8" : "",
+                   gate ? ", checked" : "");
     // TC_FAULT=timeout: test hook that makes the kernel's first wait expire
     if (const char* f = std::getenv("TC_FAULT")) q.fault = std::strcmp(f, "timeout") == 0 ? 1 : 0;
     return launch_tc(q, s) == cudaSuccess ? TC_OK : TC_ERR_CUDA;

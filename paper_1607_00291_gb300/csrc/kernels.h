@@ -139,6 +139,9 @@ struct DevProblem {
                     // each CTA of the pair loading its 128 rows of A and half of B's
                     // columns (boxB then covers bn / 2 columns)
   int64_t kps;      // contracted indices per split (a multiple of the k-tile)
+  int32_t rows_blocked;  // packed form: the row bundle is blocked 16 x 8 (block_row_bundle);
+                         // its scatter entries may be kHole
+  int32_t pad_;
   BoxAccess boxA, boxB;       // tensor-core path: TMA boxes or gathers per operand
   const CUtensorMap* tmaps;   // batch: the two tensor maps in device memory (a single
                               // call passes them as kernel parameters instead)
@@ -155,11 +158,14 @@ struct DevProblem {
 // tasks of eight values where R allows), `groups` of them.
 struct PackJob {
   const float* x;
-  const int64_t* rs;
+  const int64_t* rs;  // may hold kHole entries (a blocked row bundle): zeros
   const int64_t* ks;
   const int64_t* kbs;
   int64_t rows, k, KT, units, groups;
   int32_t R, G;
+  int32_t swz;  // blocked rows (R = 128 = 16 x 8): walk each unit's rows with
+                // the eight of one 16-row column consecutive (0: in order)
+  int32_t pad;
   uint8_t* out;
 };
 inline void pack_job_groups(PackJob& j) {

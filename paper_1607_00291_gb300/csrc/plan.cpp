@@ -314,3 +314,48 @@ int aliases(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, size_t e
 }
 
 }  // namespace tc
+
+namespace tc {
+
+bool block_row_bundle(const Layout& L, bool a_k_contig, Layout* out) {
+  const Bundle& I = L.I;
+  constexpr int64_t B0 = 16, B1 = 8;
+  if (a_k_contig || I.nd < 2 || I.nd + 2 > kMaxRank || L.n <= 0 || L.k <= 0) return false;
+  // C's unit stride leads the row bundle, A's is the second row dim
+  if (std::llabs(I.s1[0]) != 1 || std::llabs(I.s0[1]) != 1 || std::llabs(I.s0[0]) == 1)
+    return false;
+  const int64_t e0 = I.len[0], e1 = I.len[1];
+  if (e0 < B0 || e1 < B1) return false;
+  const int64_t h0 = (e0 + B0 - 1) / B0, h1 = (e1 + B1 - 1) / B1;
+  int64_t rest = 1;
+  for (int d = 2; d < I.nd; ++d) rest *= I.len[d];
+  const int64_t mb = B0 * B1 * h0 * h1 * rest;
+  // the holes may not cost more than a quarter of the rows
+  if ((double)mb > 1.25 * (double)L.m) return false;
+  *out = L;
+  Bundle& b = out->I;
+  auto set = [&](int d, int64_t len, int64_t s0, int64_t s1) {
+    b.len[d] = len;
+    b.s0[d] = s0;
+    b.s1[d] = s1;
+  };
+  set(0, B0, I.s0[0], I.s1[0]);
+  set(1, B1, I.s0[1], I.s1[1]);
+  set(2, h0, B0 * I.s0[0], B0 * I.s1[0]);
+  set(3, h1, B1 * I.s0[1], B1 * I.s1[1]);
+  for (int d = 2; d < I.nd; ++d) set(d + 2, I.len[d], I.s0[d], I.s1[d]);
+  b.nd = I.nd + 2;
+  b.nblk = 2;
+  b.blk_lo[0] = 0;
+  b.blk_hi[0] = 2;
+  b.blk_b[0] = B0;
+  b.blk_lim[0] = e0;
+  b.blk_lo[1] = 1;
+  b.blk_hi[1] = 3;
+  b.blk_b[1] = B1;
+  b.blk_lim[1] = e1;
+  out->m = mb;
+  return true;
+}
+
+}  // namespace tc

@@ -18,33 +18,44 @@
 namespace tc {
 namespace {
 
-__device__ __forceinline__ int64_t scat_at(const int64_t* len, const int64_t* s, int nd,
-                                           int64_t x) {
-  int64_t v = 0;
-  for (int d = 0; d < nd; ++d) {
-    int64_t q = x / len[d];
-    v += (x - q * len[d]) * s[d];
+// Entry x of a bundle's scatter vector over its s0 (first) or s1 strides;
+// kHole where the digits of x fall past an original extent of a blocked
+// bundle.
+__device__ __forceinline__ int64_t scat_at(const Bundle& B, bool first, int64_t x) {
+  const int64_t* s = first ? B.s0 : B.s1;
+  int64_t v = 0, lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+  for (int d = 0; d < B.nd; ++d) {
+    const int64_t q = x / B.len[d];
+    const int64_t u = x - q * B.len[d];
+    v += u * s[d];
+    if (B.nblk > 0) {
+      if (d == B.blk_lo[0]) lo0 = u;
+      if (d == B.blk_hi[0]) hi0 = u;
+      if (d == B.blk_lo[1]) lo1 = u;
+      if (d == B.blk_hi[1]) hi1 = u;
+    }
     x = q;
   }
+  if (B.nblk > 0 && lo0 + B.blk_b[0] * hi0 >= B.blk_lim[0]) return kHole;
+  if (B.nblk > 1 && lo1 + B.blk_b[1] * hi1 >= B.blk_lim[1]) return kHole;
   return v;
 }
 
 struct Section {
-  const int64_t* len;
-  const int64_t* s;
-  int nd;
+  const Bundle* B;
+  bool first;
   int64_t l;
 };
 
 __device__ __forceinline__ Section section(const Layout& L, int which) {
   // 0 rA: I/A   1 cA: P/A   2 rB: P/B   3 cB: J/B   4 rC: I/C   5 cC: J/C
   switch (which) {
-    case 0: return {L.I.len, L.I.s0, L.I.nd, L.m};
-    case 1: return {L.P.len, L.P.s0, L.P.nd, L.k};
-    case 2: return {L.P.len, L.P.s1, L.P.nd, L.k};
-    case 3: return {L.J.len, L.J.s0, L.J.nd, L.n};
-    case 4: return {L.I.len, L.I.s1, L.I.nd, L.m};
-    default: return {L.J.len, L.J.s1, L.J.nd, L.n};
+    case 0: return {&L.I, true, L.m};
+    case 1: return {&L.P, true, L.k};
+    case 2: return {&L.P, false, L.k};
+    case 3: return {&L.J, true, L.n};
+    case 4: return {&L.I, false, L.m};
+    default: return {&L.J, false, L.n};
   }
 }
 
@@ -58,20 +69,22 @@ __device__ __forceinline__ int64_t scatter_entry(const Layout& L, const ScatterO
   const int64_t x = t - starts[sec];
   if (sec < 6) {
     Section S = section(L, sec);
-    return scat_at(S.len, S.s, S.nd, x);
+    return scat_at(*S.B, S.first, x);
   }
   Section S = section(L, sec - 6);
   const int64_t lo = x * b;
   const int64_t hi = lo + b < S.l ? lo + b : S.l;
+  int64_t prev = scat_at(*S.B, S.first, lo);
+  if (prev == kHole) return 0;  // a block with a hole makes no claim
   if (hi - lo <= 1) return 1;
-  int64_t prev = scat_at(S.len, S.s, S.nd, lo);
-  int64_t cur = scat_at(S.len, S.s, S.nd, lo + 1);
+  int64_t cur = scat_at(*S.B, S.first, lo + 1);
+  if (cur == kHole) return 0;
   const int64_t st = cur - prev;
   bool ok = st > 0;
   for (int64_t j = lo + 2; j < hi && ok; ++j) {
     prev = cur;
-    cur = scat_at(S.len, S.s, S.nd, j);
-    ok = (cur - prev) == st;
+    cur = scat_at(*S.B, S.first, j);
+    ok = cur != kHole && (cur - prev) == st;
   }
   return ok ? st : 0;
 }
@@ -108,7 +121,9 @@ __device__ __forceinline__ bool entry_ok(const Layout& L, const ScatterOffsets& 
                               o.cbsA, o.rbsB, o.cbsB, o.rbsC, o.cbsC, o.total};
   int sec = 0;
   while (sec < 11 && t >= starts[sec + 1]) ++sec;
-  if (sec < 6) return v[t] >= cb.lo[sec] && v[t] <= cb.hi[sec];
+  // a hole of a blocked row bundle (rA, rC) names no element
+  if (sec < 6) return (v[t] >= cb.lo[sec] && v[t] <= cb.hi[sec]) ||
+                      (v[t] == kHole && (sec == 0 || sec == 4) && L.I.nblk > 0);
   const int vs = sec - 6;  // the scatter vector this block-scatter vector describes
   const int64_t len = starts[vs + 1] - starts[vs];
   const int64_t lo = (t - starts[sec]) * b, hi = lo + b < len ? lo + b : len;
@@ -156,7 +171,9 @@ __global__ void k_scale_c(T* __restrict__ c, const int64_t* __restrict__ rC,
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t % m, j = t / m;
-    T* p = c + rC[i] + cC[j];
+    const int64_t r = rC[i];
+    if (r == kHole) continue;  // a hole of a blocked row bundle
+    T* p = c + r + cC[j];
     *p = beta == 0.0 ? T(0) : T(beta * (double)*p);
   }
 }

@@ -19,7 +19,19 @@ struct Bundle {
   int64_t len[kMaxRank];
   int64_t s0[kMaxRank];
   int64_t s1[kMaxRank];
+  // Blocked row bundle (the packed form's two-dimensional row tiles, built by
+  // block_row_bundle): for each of the nblk pairs p, dims blk_lo[p] and
+  // blk_hi[p] split one original dim of extent blk_lim[p] into blk_b[p] and
+  // ceil(blk_lim[p] / blk_b[p]); a linear index whose digits give
+  // u_lo + blk_b[p] u_hi >= blk_lim[p] is a hole, whose scatter entry is kHole.
+  int32_t nblk;
+  int32_t blk_lo[2], blk_hi[2];
+  int64_t blk_b[2], blk_lim[2];
 };
+
+// The scatter entry of a hole of a blocked bundle: no element; every kernel
+// that reads a blocked bundle's entries skips it.
+constexpr int64_t kHole = INT64_MIN / 4;
 
 // The matrix view of one contraction: C_{IJ} (m x n) = A_{IP} (m x k) B_{PJ} (k x n).
 struct Layout {
@@ -41,6 +53,15 @@ struct Planned {
 
 // Validation + Section 7.3 normalisation.  Returns TC_OK or an error code.
 int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Planned* out);
+
+// The packed form's blocked row order: when A is read along its rows and its
+// unit-stride dim is the second row dim, behind C's (GPU step 7's interleave),
+// out = L with those two dims split into 16 x ceil(E0 / 16) and 8 x ceil(E1 / 8)
+// and ordered (lo0, lo1, hi0, hi1, rest): every 128-row tile is one 16 x 8
+// block, over which C's unit-stride runs are 16 long and A's 8 long.  Rows
+// past an original extent are holes (kHole entries).  Returns false (out
+// untouched) when the layout does not qualify.
+bool block_row_bundle(const Layout& L, bool a_k_contig, Layout* out);
 
 // Scatter-vector section offsets inside a workspace (int64 entries).
 struct ScatterOffsets {

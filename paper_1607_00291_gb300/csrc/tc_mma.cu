@@ -1021,10 +1021,12 @@ __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int6
     const float* pn = part + n * M;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t rm = __ldg(d.sp.rC + m);
+      if (rm == kHole) continue;  // a hole of a blocked row bundle
       if constexpr (F64) {
         double sum = 0.0;
         for (int ks = 0; ks < S; ++ks) sum += (double)__ldg(pn + ks * plane + m);
-        float* cp = c + __ldg(d.sp.rC + m) + cn;
+        float* cp = c + rm + cn;
         double r = d.alpha * sum;
         if (d.beta != 0.0) r += d.beta * (double)*cp;
         *cp = (float)r;
@@ -1036,7 +1038,7 @@ __device__ __forceinline__ void reduce_one(const DevProblem& d, int64_t n0, int6
         two_sum(hi, __ldg(pn + ks * plane + m), hi, e);
         lo = __fadd_rn(lo, e);
       }
-      float* cp = c + __ldg(d.sp.rC + m) + cn;
+      float* cp = c + rm + cn;
       // alpha * (hi + lo) [+ beta * C], the small term folded in first; C is
       // only read when beta != 0
       const float r = __fmaf_rn(alpha, hi, alpha * lo);
@@ -1115,14 +1117,17 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
     const int64_t u = u0 + tt / per_unit;
     if (u >= p.units) break;
     const int c = tt % per_unit;
-    const int r = c % R, q = c / R;
+    // a blocked unit's row r = lo0 + 16 lo1: consecutive threads take
+    // consecutive lo1, the operand's unit-stride dim
+    const int r = p.swz ? (c % R) / 8 + 16 * ((c % R) % 8) : c % R, q = c / R;
     const int64_t tr = u / p.KT, kt = u % p.KT;
     uint8_t* out = p.out + u * (int64_t)(NS * R * BK * 2);
     const int64_t row = tr * R + r;
     const int64_t kk0 = kt * BK + 8 * q;
     float v[8];
-    if (row < p.rows) {
-      const float* xr = p.x + __ldg(p.rs + row);
+    const int64_t ro = row < p.rows ? __ldg(p.rs + row) : kHole;
+    if (ro != kHole) {
+      const float* xr = p.x + ro;
       bool vec = false;
       if (kk0 + 7 < p.k) {
         const int64_t o = __ldg(p.ks + kk0);
@@ -1564,7 +1569,8 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
                                  : static_cast<float*>(d->partial) +
                                        ((int64_t)it.split * d->n + it.n0) * d->m + it.m0 + row;
       const int64_t pm = d->m;
-      const bool mv = row < it.rows_a;
+      // rows past the operand, and holes of a blocked row bundle, write nothing
+      const bool mv = row < it.rows_a && sRC[row] != kHole;
       const int cols = it.rows_b;
       bool ok = true;
       auto out8 = [&](int cb, const float (&hi)[8], const float (&lo)[8]) {
@@ -1812,6 +1818,7 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
     ja.R = BM;
     ja.KT = KT;
     ja.units = tm * KT;
+    ja.swz = d.rows_blocked ? 16 : 0;
     ja.out = const_cast<uint8_t*>(d.pa);
     PackJob& jb = pk.local[1];
     jb = ja;
@@ -1820,6 +1827,7 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
     jb.ks = d.sp.rB;
     jb.kbs = d.sp.rbsB;
     jb.rows = d.n;
+    jb.swz = 0;
     jb.R = PAIR ? d.bn / 2 : d.bn;  // pair form: half-tile units, one per CTA
     jb.units = (PAIR ? 2 : 1) * tn * KT;
     jb.out = const_cast<uint8_t*>(d.pb);

@@ -10,8 +10,10 @@ bound.  Covered: every layout of the box-form cases (row- and k-contiguous
 operands, tails in m, n and k, multi-dim row tiles), both modes with alpha and
 beta, NaN in C with beta = 0, k-splits, narrow tiles (B units of 16 and 64
 rows), the benchmark strings at reduced extents, device-side checks, and the
-full-size 4096^3 contraction; and the form on CTA pairs against the
-single-CTA form, bit for bit."""
+full-size 4096^3 contraction; the form on CTA pairs against the single-CTA
+form, bit for bit; and blocked row bundles (16 x 8 row tiles with holes past
+the original extents) against the gathers, the oracle, and a guard region
+around C."""
 import zlib
 
 import numpy as np
@@ -177,3 +179,74 @@ def test_packed_pair_matches_single_cta(monkeypatch, name, mode):
     assert np.array_equal(out["1"], out["0"])
     ref, mag = oracle_ref(0.5, A, lA, B, lB, -1.5, C0, lC)
     assert norm_err(out["1"], ref, mag) <= TOLS[mode]
+
+
+from test_gpu_checks import _guarded_c, _nan_bits  # noqa: E402
+
+# Blocked rows (block_row_bundle): A's unit-stride row dim second behind C's,
+# so the packed form blocks the rows 16 x 8; rows past an original extent are
+# holes that nothing reads or writes.  (labels A, B, C, extents, alpha, beta)
+BLOCKED = {
+    # the first benchmark string's structure, 45 x 45 with holes in both dims
+    "string1_45": ("efbad", "cf", "abcde", dict(a=45, b=2, c=8, d=2, e=45, f=16), 1.0, 0.0),
+    # exact 16 x 8 blocks (no holes), beta != 0
+    "exact_64x24": ("efbad", "cf", "abcde", dict(a=64, b=3, c=24, d=1, e=24, f=40), 0.5, -1.25),
+    # the third benchmark string's structure: holes in one dim only, n = 40
+    "string3_47x24": ("dbea", "ec", "abcd", dict(a=47, b=3, c=40, d=24, e=50), 1.0, 0.5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BLOCKED))
+def test_blocked_rows_equal_gathers_and_oracle(monkeypatch, capfd, name):
+    lA, lB, lC, ext, alpha, beta = BLOCKED[name]
+    g = torch.Generator().manual_seed(zlib.crc32(name.encode()) % 1000 + 5)
+    A, B = colmajor_rand(lA, ext, g), colmajor_rand(lB, ext, g)
+    C0 = colmajor_rand(lC, ext, g)
+    monkeypatch.setenv("TC_LOG", "1")
+    got = run_packed(A, lA, B, lB, C0, lC, alpha=alpha, beta=beta)
+    assert "rows blocked 16 x 8" in capfd.readouterr().err
+    ref, mag = oracle_ref(alpha, A, lA, B, lB, beta, C0, lC)
+    assert norm_err(got, ref, mag) <= TOLS["bf16x3"]
+
+
+def test_blocked_rows_write_only_c():
+    # beta = 0 over a C that is NaN inside a padded buffer: every element of
+    # C is written once, nothing around it is touched, A and B are unchanged
+    lA, lB, lC, ext, _, _ = BLOCKED["string1_45"]
+    g = torch.Generator().manual_seed(77)
+    A, B = colmajor_rand(lA, ext, g), colmajor_rand(lB, ext, g)
+    dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
+    A0, B0 = dA.clone(), dB.clone()
+    buf, dC, mask = _guarded_c(tuple(ext[x] for x in lC), torch.float32, pad=2)
+    outside = _nan_bits(buf)[~mask].clone()
+    with tc.access("packed"):
+        tc.contract(dA, lA, dB, lB, dC, lC, mode="bf16x3")
+        torch.cuda.synchronize()
+    assert tc.device_error() == 0
+    assert torch.equal(_nan_bits(buf)[~mask], outside)
+    assert bool(torch.isfinite(dC).all())
+    assert torch.equal(dA, A0) and torch.equal(dB, B0)
+    ref, mag = oracle_ref(1.0, A, lA, B, lB, 0.0, torch.zeros(dC.shape, dtype=torch.float64), lC)
+    assert norm_err(dC.cpu().double().numpy(), ref, mag) <= TOLS["bf16x3"]
+
+
+def test_blocked_rows_checked_and_alpha_zero():
+    # device-side checks accept the holes (and still catch a short range);
+    # alpha = 0 scales C through the blocked vectors, skipping the holes
+    lA, lB, lC, ext, _, _ = BLOCKED["string1_45"]
+    g = torch.Generator().manual_seed(78)
+    A, B = colmajor_rand(lA, ext, g), colmajor_rand(lB, ext, g)
+    C0 = colmajor_rand(lC, ext, g)
+    dA, dB = to_device(A, torch.float32), to_device(B, torch.float32)
+    ref = run_packed(A, lA, B, lB, C0, lC, beta=0.5)
+    with tc.access("packed"), tc.checks(True):
+        dC = to_device(C0, torch.float32)
+        tc.contract(dA, lA, dB, lB, dC, lC, beta=0.5, mode="bf16x3")
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
+        assert np.array_equal(dC.cpu().double().numpy(), ref)
+        dC = to_device(C0, torch.float32)
+        tc.contract(dA, lA, dB, lB, dC, lC, alpha=0.0, beta=0.5, mode="bf16x3")
+        torch.cuda.synchronize()
+        assert tc.device_error() == 0
+        assert torch.equal(dC.cpu(), (C0 * 0.5).float())
