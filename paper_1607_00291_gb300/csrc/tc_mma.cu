@@ -1183,12 +1183,15 @@ struct PackedArgs {
   int32_t* err;
   const int32_t* gate;
   int fault;  // 1: injected timeout (see TcLaunch::fault)
+  int dual;   // every work item is one accumulation chunk: two epilogue groups
 };
 
-// Warps: producer, MMA, four epilogue warps; in the pair form also a relay
-// warp that tells the pair's MMA issuer when its CTA's stage has landed.
-constexpr int pk_threads(bool pair) { return pair ? 224 : 192; }
-constexpr int PK_EPI_W0 = 2, PK_RELAY_WARP = 6;
+// Warps: producer, MMA, two groups of four epilogue warps (the second works
+// only when every item is one accumulation chunk: the groups then take the
+// items in turn, each with its own accumulator); in the pair form also a
+// relay warp that tells the pair's MMA issuer when its CTA's stage has landed.
+constexpr int pk_threads(bool pair) { return pair ? 352 : 320; }
+constexpr int PK_EPI_W0 = 2, PK_RELAY_WARP = 10;
 
 // PAIR: CTA pairs (cta_group::2) on 256-row tiles; each CTA stages its own
 // 128 rows of A and half of the tile's B rows (B is packed in half-tile
@@ -1205,8 +1208,8 @@ struct PLay {
   static constexpr int B_BYTES = NS * (PAIR ? BNMAX / 2 : BNMAX) * BK * 2;  // the widest unit of B
   static constexpr int STAGE = U * (A_BYTES + B_BYTES);  // U units of A, then U of B
   static constexpr int NSTG = PAIR ? (NS == 3 ? 5 : 4) : (NS == 3 ? 4 : 3);
-  static constexpr int SCAT = NSTG * STAGE;  // int64 rC[BM] cC[BNMAX]
-  static constexpr int PROB = SCAT + (BM + BNMAX) * 8;
+  static constexpr int SCAT = NSTG * STAGE;  // per epilogue group int64 rC[BM] cC[BNMAX]
+  static constexpr int PROB = SCAT + 2 * (BM + BNMAX) * 8;
   static constexpr int BARS = PROB + (int)((sizeof(DevProblem) + 15) / 16 * 16);
   static constexpr int NBARS = 3 * NSTG + 5;
   static constexpr int MISC = BARS + NBARS * 8;
@@ -1227,8 +1230,6 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
   constexpr int NSTG = Ly::NSTG, U = Ly::U;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  int64_t* sRC = reinterpret_cast<int64_t*>(smem + Ly::SCAT);
-  int64_t* sCC = sRC + BM;
   DevProblem* sProb = reinterpret_cast<DevProblem*>(smem + Ly::PROB);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Ly::BARS);  // this CTA's stage landed
   uint64_t* empty = full + NSTG;
@@ -1343,7 +1344,12 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       bool pub = publish(0, nx);
       for (int64_t j = 0; pub && !*abort && !failed; ++j) {
         const Item it = nx;
-        if (it.d == nullptr) break;
+        if (it.d == nullptr) {
+          // a second end entry: with two epilogue groups each reads every
+          // other entry, so each must meet an end
+          publish(j + 1, nx);
+          break;
+        }
         nx = decode(w0 + (j + 1) * dw);
         if (!(pub = publish(j + 1, nx))) break;
         const DevProblem* d = it.d;
@@ -1522,9 +1528,15 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
         }
       }
     }
-  } else if (warp < PK_EPI_W0 + 4) {
-    // ---- epilogue: one thread per accumulator row (as in k_tc) ----
-    const int t = tid - PK_EPI_W0 * 32;
+  } else if (warp < PK_EPI_W0 + 8 && (warp - PK_EPI_W0) / 4 < (a.dual ? 2 : 1)) {
+    // ---- epilogue: one thread per accumulator row (as in k_tc); with two
+    // groups, group g takes items g, g + 2, ... (each item one chunk, in
+    // accumulator g) ----
+    const int grp = (warp - PK_EPI_W0) >> 2, EG = a.dual ? 2 : 1;
+    const int ebar = BAR_EPI + grp;
+    int64_t* sRC = reinterpret_cast<int64_t*>(smem + Ly::SCAT) + grp * (BM + BNMAX);
+    int64_t* sCC = sRC + BM;
+    const int t = tid - (PK_EPI_W0 + 4 * grp) * 32;
     const int wq = warp & 3;
     const int row = 32 * wq + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
@@ -1546,20 +1558,21 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       return got;
     };
     Item cur, nxt;
-    bool got_cur = get(0, cur);
+    bool got_cur = get(grp, cur);
     if (got_cur) fetch_rows(cur);
-    int64_t gc = 0;
-    for (int64_t j = 0;; ++j) {
-      if (bar_or(BAR_EPI, NEPI, !got_cur || *abort)) break;  // uniform exit
+    int64_t gc = 0;  // chunks before this one in the CTA's sequence
+    for (int64_t j = grp;; j += EG) {
+      if (bar_or(ebar, NEPI, !got_cur || *abort)) break;  // uniform exit
       const Item it = cur;
       const DevProblem* d = it.d;
       sRC[t] = pre_r;
 #pragma unroll
       for (int i = 0; i < NB; ++i) sCC[t + i * NEPI] = pre_c[i];
       // the next item's row and column entries are fetched one item ahead
-      const bool have_next = get(j + 1, nxt);
+      const bool have_next = get(j + EG, nxt);
       if (have_next) fetch_rows(nxt);
-      bar_sync(BAR_EPI, NEPI);
+      bar_sync(ebar, NEPI);
+      if (a.dual) gc = j;  // one chunk per item
       const bool have = it.KT > 0;
       const int bn = d->bn;
       const bool direct = d->splits == 1;
@@ -1842,6 +1855,8 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   a.err = q.err;
   a.gate = q.gate;
   a.fault = q.fault;
+  // every item one chunk: the two epilogue groups take the items in turn
+  a.dual = q.probs ? q.pack_dual : (q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0);
   mainloop_event_before(s);
   if (pk.total > 0) {
     k_pack<NS><<<(unsigned)std::min<int64_t>(pk.total, (int64_t)q.ctas * 8), 256, 0, s>>>(pk);
