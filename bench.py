@@ -1070,7 +1070,7 @@ def run_ours(args, ws, rank, local):
                 "roofline": {"bound": "tensor", "kernel": kname, "achieved": round(ach, 5),
                              "peak": round(peak_v, 5), "unit": "TFLOP/s", "frac": round(ach / peak_v, 4),
                              "peak_source": src, "kernel_ms": round(kms_max, 4),
-                             "traffic": traffic_for(kname, spec.name) if spec.mode != "f64" else None,
+                             "traffic": traffic_for(kname, f"{spec.name}_{spec.mode}") if spec.mode != "f64" else None,
                              "algorithmic": f"{flops:.4g} flops per launch"
                                             + (f" (x{prods} bf16 products)" if spec.mode != "f64" else "")}}
         if spec.mode != "f64":
@@ -1153,7 +1153,7 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": bound, "kernel": kname, "achieved": round(ach, 5), "peak": round(peak_v, 5),
                      "unit": unit, "frac": round(ach / peak_v, 4), "peak_source": peak_src,
                      "kernel_ms": round(kms_max, 4),
-                     "traffic": traffic_for(kname, spec.name),
+                     "traffic": traffic_for(kname, spec.name if spec.mode == "f64" else f"{spec.name}_{spec.mode}"),
                      "algorithmic": f"{flops:.4g} flops per launch"
                                     + (f" (x{prods} bf16 products)" if spec.mode != "f64" else "")},
         "device_error": err_code,
