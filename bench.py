@@ -810,6 +810,8 @@ def run_calls(args, ws, rank, local, *, calls, inputs, outputs, flops, mode, des
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": int(launches), "roofline": roof, "device_error": err_code,
     }
+    if forms:
+        line["forms"] = forms
     if not args.no_ttgt:
         for c, c0 in zip(calls, C0):
             c[4].copy_(c0)
