@@ -463,6 +463,35 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     alpha.push_back(pr.alpha);
     beta.push_back(pr.beta);
   }
+  // The packed form for tensor-core batches: always under TC_ACCESS_PACKED,
+  // under TC_ACCESS_AUTO when the batch holds at least 2^26 multiply-adds
+  // (as for single contractions).  Every operand of a batch is gathered
+  // otherwise, so packing pays here even for operands read by one tile: the
+  // packing launch, many small CTAs per SM, gathers them faster than the
+  // mainloop's loader warps.
+  if (!f64) {
+    double work = 0;
+    for (size_t i = 0; i < pl->planned.size(); ++i) {
+      const Layout& L = pl->planned[i].L;
+      work += (double)L.m * (double)L.n * (double)L.k;
+    }
+    const int acc = access_setting();
+    pl->packed = acc == TC_ACCESS_PACKED || (acc == TC_ACCESS_AUTO && work >= 67108864.0);
+  }
+  // Packed batches exchange A's and B's roles for problems whose 128-row
+  // tiles would pad the rows far more than the columns' tiles (16..128 wide)
+  // would pad them the other way round: the packed operands and the MMA work
+  // shrink with the padding; the epilogue then writes C along its columns.
+  if (pl->packed) {
+    auto padded = [](int64_t m, int64_t n) {
+      const int64_t bn = std::min<int64_t>(128, std::max<int64_t>(16, (n + 15) / 16 * 16));
+      return (double)((m + 127) / 128 * 128) * (double)((n + bn - 1) / bn * bn);
+    };
+    for (Planned& p : pl->planned) {
+      const Layout& L = p.L;
+      if (L.k > 0 && L.m < 128 && padded(L.n, L.m) < 0.75 * padded(L.m, L.n)) swap_roles(&p);
+    }
+  }
   // the autotuner's tile records (see K7), timed here for classes without one
   const bool tune = autotune_enabled();
   auto tuned_tile = [&](int i) -> int {
@@ -572,21 +601,6 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
     }
   }
 
-  // The packed form for tensor-core batches: always under TC_ACCESS_PACKED,
-  // under TC_ACCESS_AUTO when the batch holds at least 2^26 multiply-adds
-  // (as for single contractions).  Every operand of a batch is gathered
-  // otherwise, so packing pays here even for operands read by one tile: the
-  // packing launch, many small CTAs per SM, gathers them faster than the
-  // mainloop's loader warps.
-  if (!f64) {
-    double work = 0;
-    for (int i = 0; i < np; ++i) {
-      const Layout& L = pl->planned[i].L;
-      work += (double)L.m * (double)L.n * (double)L.k;
-    }
-    const int acc = access_setting();
-    pl->packed = acc == TC_ACCESS_PACKED || (acc == TC_ACCESS_AUTO && work >= 67108864.0);
-  }
   std::vector<size_t> pack_a(np, 0), pack_b(np, 0);
   size_t pack_total = 0;
   if (pl->packed) {

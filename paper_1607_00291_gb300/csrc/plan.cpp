@@ -359,3 +359,20 @@ bool block_row_bundle(const Layout& L, bool a_k_contig, Layout* out) {
 }
 
 }  // namespace tc
+
+namespace tc {
+
+void swap_roles(Planned* p) {
+  Layout& L = p->L;
+  std::swap(L.I, L.J);
+  std::swap(L.m, L.n);
+  for (int i = 0; i < L.P.nd; ++i) std::swap(L.P.s0[i], L.P.s1[i]);
+  std::swap(p->a, p->b);
+  tc_plan_info& f = p->info;
+  f.swapped = !f.swapped;
+  std::swap(f.a_k_contig, f.b_k_contig);
+  std::swap(f.m, f.n);
+}
+
+}  // namespace tc
+

@@ -63,6 +63,12 @@ int plan_problem(const tc_tensor* A, const tc_tensor* B, const tc_tensor* C, Pla
 // untouched) when the layout does not qualify.
 bool block_row_bundle(const Layout& L, bool a_k_contig, Layout* out);
 
+// Exchange the matrix roles of A and B (C^T = B^T A^T: I and J swap, P's two
+// stride sets swap, and the operands and their access flags with them), as
+// Section 7.3's step 4 does.  Used by packed batch plans for problems whose
+// rows pad far more than their columns would.
+void swap_roles(Planned* p);
+
 // Scatter-vector section offsets inside a workspace (int64 entries).
 struct ScatterOffsets {
   int64_t rA, cA, rB, cB, rC, cC;        // scatter vectors
