@@ -435,7 +435,6 @@ struct tc_plan {
   int64_t* d_job_prefix = nullptr;
   int32_t njobs = 0;
   int64_t pack_groups = 0;
-  int pack_dual = 0;  // every work item one accumulation chunk (1024 terms)
 };
 
 namespace {
@@ -784,9 +783,6 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   }
   pl->njobs = (int32_t)jobs.size();
   pl->pack_groups = jpre.back();
-  pl->pack_dual = 1;
-  for (int i = 0; i < np; ++i)
-    if (pl->cfg[i].kps > 1024 && pl->planned[i].L.k > 0) pl->pack_dual = 0;
   auto up = [](void* dst, const void* src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
@@ -1005,7 +1001,6 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
       q.pack_prefix = plan->d_job_prefix;
       q.pack_njobs = plan->njobs;
       q.pack_groups = plan->pack_groups;
-      q.pack_dual = plan->pack_dual;
     }
     e = launch_tc(q, s);
   }

@@ -207,7 +207,6 @@ struct TcLaunch {
   const int64_t* pack_prefix;  // their prefix sums of unit groups (device, pack_njobs + 1)
   int32_t pack_njobs;
   int64_t pack_groups;
-  int pack_dual;  // batch, packed form: every work item is one accumulation chunk
 };
 cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
 // Workspace of the packed form: A's units (128 rows x 32 k, all pieces; the

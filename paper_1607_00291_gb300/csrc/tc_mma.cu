@@ -1183,7 +1183,7 @@ struct PackedArgs {
   int32_t* err;
   const int32_t* gate;
   int fault;  // 1: injected timeout (see TcLaunch::fault)
-  int dual;   // every work item is one accumulation chunk: two epilogue groups
+  int dual;   // two epilogue groups taking the work items in turn (see the epilogue)
 };
 
 // Warps: producer, MMA, two groups of four epilogue warps (the second works
@@ -1243,9 +1243,11 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
   Item* ring = reinterpret_cast<Item*>(smem + Ly::RING);
   uint64_t* ring_full = reinterpret_cast<uint64_t*>(smem + Ly::RING + QRP * sizeof(Item));
   uint64_t* ring_empty = ring_full + QRP;
-  // Tensor Memory: two accumulators that chunks alternate between, so that
-  // the MMAs of a chunk run while the epilogue folds the previous one, and
-  // the running sum of a multi-chunk tile
+  // Tensor Memory: two accumulators and the running sums of multi-chunk
+  // tiles.  One epilogue group: chunks alternate between the accumulators, so
+  // that the MMAs of a chunk run while the epilogue folds the previous one,
+  // and one running sum.  Two groups: each its own accumulator (all chunks of
+  // its items) and its own running sum.
   constexpr uint32_t PK_COLS = 4 * BNMAX, PK_SUM = 2 * BNMAX;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1317,10 +1319,13 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       int64_t g = 0, g_iss = -1;
       uint32_t st_i = 0, ph = 0;  // stage and phase parity of k-tile g
       bool failed = false;
-      // Item j + 1 is published before item j's stages are streamed: the
-      // epilogue reads one item ahead (to fetch its rows and columns), and
-      // item j's stages reach it only through the epilogue's release of
-      // earlier accumulators.  An entry with d == null ends the sequence.
+      // Items up to j + 2 are published before item j's stages are streamed:
+      // an epilogue group reads one of its items ahead (to fetch its rows'
+      // and columns' scatter entries) -- item j + 1 with one group, j + 2 with
+      // two -- and item j's later stages reach the producer only through that
+      // group's release of accumulators.  An entry with d == null ends the
+      // sequence; a second one follows it, since with two groups each reads
+      // every other entry.
       auto decode = [&](int64_t w) {
         Item x;
         if (w < nitems) {
@@ -1340,18 +1345,26 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
         mbar_arrive(&ring_full[q]);
         return true;
       };
-      Item nx = decode(w0);
-      bool pub = publish(0, nx);
-      for (int64_t j = 0; pub && !*abort && !failed; ++j) {
-        const Item it = nx;
-        if (it.d == nullptr) {
-          // a second end entry: with two epilogue groups each reads every
-          // other entry, so each must meet an end
-          publish(j + 1, nx);
-          break;
+      int64_t npub = 0;    // entries published
+      bool ended = false;  // both end entries published
+      auto publish_upto = [&](int64_t last) {
+        while (!ended && npub <= last) {
+          const Item x = decode(w0 + npub * dw);
+          if (!publish(npub, x)) return false;
+          ++npub;
+          if (x.d == nullptr) {
+            if (!publish(npub, x)) return false;
+            ++npub;
+            ended = true;
+          }
         }
-        nx = decode(w0 + (j + 1) * dw);
-        if (!(pub = publish(j + 1, nx))) break;
+        return true;
+      };
+      for (int64_t j = 0; !*abort && !failed; ++j) {
+        if (!publish_upto(j + 2)) break;
+        // item j as published (its slot is not rewritten before item j + 14)
+        const Item it = ring[j & (QRP - 1)];
+        if (it.d == nullptr) break;
         const DevProblem* d = it.d;
         const int64_t KT = (d->k + BK - 1) / BK;
         // pair form: B in half-tile units, this CTA's half
@@ -1412,6 +1425,7 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           failed = true;
         }
       }
+      int64_t uses[2] = {0, 0};  // two groups: chunks issued into each accumulator so far
       for (int64_t j = 0; !*abort && !failed; ++j) {
         Item it;
         const bool got = ring_get(j, it);
@@ -1425,8 +1439,10 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
         const uint64_t descB0 =
             smem_desc(smem_u32(smem) + U * Ly::A_BYTES, (uint32_t)(rb / 8) * 128, 128);
         for (int ch = 0; ch < it.nchunks && !failed; ++ch, ++gc) {
-          const int buf = (int)(gc & 1);
-          const int64_t use = gc >> 1;  // earlier uses of this accumulator
+          // one group: chunks alternate between the accumulators; two groups:
+          // item j's chunks all go to accumulator j % 2, the one its group reads
+          const int buf = a.dual ? (int)(j & 1) : (int)(gc & 1);
+          const int64_t use = a.dual ? uses[buf]++ : gc >> 1;  // earlier uses of this accumulator
           if (use > 0 &&
               !mbar_wait<PAIR>(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
             record_timeout(abort, a.err);
@@ -1533,6 +1549,8 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
     // groups, group g takes items g, g + 2, ... (each item one chunk, in
     // accumulator g) ----
     const int grp = (warp - PK_EPI_W0) >> 2, EG = a.dual ? 2 : 1;
+    // the running sum of a multi-chunk tile: one region, or one per group
+    const uint32_t psum = PK_SUM + (uint32_t)(a.dual ? grp : 0) * BNMAX;
     const int ebar = BAR_EPI + grp;
     int64_t* sRC = reinterpret_cast<int64_t*>(smem + Ly::SCAT) + grp * (BM + BNMAX);
     int64_t* sCC = sRC + BM;
@@ -1572,7 +1590,7 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       const bool have_next = get(j + EG, nxt);
       if (have_next) fetch_rows(nxt);
       bar_sync(ebar, NEPI);
-      if (a.dual) gc = j;  // one chunk per item
+
       const bool have = it.KT > 0;
       const int bn = d->bn;
       const bool direct = d->splits == 1;
@@ -1608,8 +1626,10 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       };
       for (int ch = 0; ch < it.nchunks; ++ch, ++gc) {
         const bool first = ch == 0, last = ch + 1 == it.nchunks;
-        const int buf = (int)(gc & 1);
-        const uint32_t use = (uint32_t)(gc >> 1);
+        // one group: chunk gc of the CTA in accumulator gc % 2; two groups:
+        // this group's gc-th chunk in accumulator grp (its own running sum too)
+        const int buf = a.dual ? grp : (int)(gc & 1);
+        const uint32_t use = (uint32_t)(a.dual ? gc : gc >> 1);
         if (have && !*abort) {
           if (!mbar_wait<PAIR>(&acc_full[buf], use & 1u, abort)) record_timeout(abort, a.err);
         }
@@ -1652,11 +1672,11 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
 #pragma unroll
               for (int q = 0; q < 8; ++q) sum[q] = v[q];
             } else {
-              tmem_ld8(lane_base + PK_SUM + (uint32_t)cb, sum);
+              tmem_ld8(lane_base + psum + (uint32_t)cb, sum);
 #pragma unroll
               for (int q = 0; q < 8; ++q) sum[q] = __fadd_rn(sum[q], v[q]);
             }
-            tmem_st8(lane_base + PK_SUM + (uint32_t)cb, sum);
+            tmem_st8(lane_base + psum + (uint32_t)cb, sum);
           }
           tmem_st_wait();
         }
@@ -1669,7 +1689,7 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           float sum[8], z[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) z[q] = 0.f;
-          tmem_ld8(lane_base + PK_SUM + (uint32_t)cb, sum);
+          tmem_ld8(lane_base + psum + (uint32_t)cb, sum);
           out8(cb, sum, z);
         }
       }
@@ -1855,8 +1875,12 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   a.err = q.err;
   a.gate = q.gate;
   a.fault = q.fault;
-  // every item one chunk: the two epilogue groups take the items in turn
-  a.dual = q.probs ? q.pack_dual : (q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0);
+  // two epilogue groups that take the items in turn: for a batch (short
+  // items, most of them one chunk), and for a single problem whose items are
+  // one chunk each; a single problem of long items keeps one group, whose
+  // chunks alternate between the accumulators (the MMAs of a chunk then run
+  // while the previous chunk is folded)
+  a.dual = q.probs ? 1 : (q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0);
   mainloop_event_before(s);
   if (pk.total > 0) {
     k_pack<NS><<<(unsigned)std::min<int64_t>(pk.total, (int64_t)q.ctas * 8), 256, 0, s>>>(pk);
