@@ -1425,7 +1425,7 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           failed = true;
         }
       }
-      int64_t uses[2] = {0, 0};  // two groups: chunks issued into each accumulator so far
+      int64_t uses0 = 0, uses1 = 0;  // two groups: chunks issued into each accumulator so far
       for (int64_t j = 0; !*abort && !failed; ++j) {
         Item it;
         const bool got = ring_get(j, it);
@@ -1442,7 +1442,8 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
           // one group: chunks alternate between the accumulators; two groups:
           // item j's chunks all go to accumulator j % 2, the one its group reads
           const int buf = a.dual ? (int)(j & 1) : (int)(gc & 1);
-          const int64_t use = a.dual ? uses[buf]++ : gc >> 1;  // earlier uses of this accumulator
+          // earlier uses of this accumulator (scalars, not an array: no local memory)
+          const int64_t use = a.dual ? (buf ? uses1++ : uses0++) : gc >> 1;
           if (use > 0 &&
               !mbar_wait<PAIR>(&acc_empty[buf], (uint32_t)((use - 1) & 1), abort)) {
             record_timeout(abort, a.err);
