@@ -1105,9 +1105,9 @@ struct PackLaunch {
 };
 
 // Unit group g of a job.  Task c = (row r = c % R, k-chunk q = c / R) of a
-// unit packs eight values of one row (rows past the operand and k past its
-// range are zeros); eight elements that the block-scatter vector shows at
-// unit stride, from a 16-byte boundary, take two 16-byte loads.
+// unit packs eight values of one row (k past the range as zeros; rows past
+// the operand are skipped); eight elements that the block-scatter vector
+// shows at unit stride, from a 16-byte boundary, take two 16-byte loads.
 template <int NS>
 __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
   const int R = p.R, per_unit = R * (BK / 8);
@@ -1126,7 +1126,10 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
     const int64_t kk0 = kt * BK + 8 * q;
     float v[8];
     const int64_t ro = row < p.rows ? __ldg(p.rs + row) : kHole;
-    if (ro != kHole) {
+    // a row past the operand or a hole of a blocked bundle is not written: it
+    // reaches only its own accumulator row (column), which is never stored
+    if (ro == kHole) continue;
+    {
       const float* xr = p.x + ro;
       bool vec = false;
       if (kk0 + 7 < p.k) {
@@ -1147,9 +1150,6 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
           v[j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
         }
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = 0.f;
     }
     split8_store<NS>(v, out, R * BK * 2,
                      (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16));
