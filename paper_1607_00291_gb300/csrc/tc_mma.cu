@@ -1156,22 +1156,37 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
   }
 }
 
+// A single contraction's two jobs: the CTAs take the unit groups round robin
+// (neighbouring units, which share sectors of the operand, are packed side by
+// side).  A batch: each CTA packs one contiguous range of unit groups, so that
+// its job -- a binary search over the prefix sums -- is looked up only when the
+// range crosses into another job (one search per group cost the batch 5 %).
 template <int NS>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackLaunch p) {
   if (p.gate && *p.gate == kDevBounds) return;
-  for (int64_t g = blockIdx.x; g < p.total; g += gridDim.x) {
-    if (p.jobs) {
+  if (!p.jobs) {
+    for (int64_t g = blockIdx.x; g < p.total; g += gridDim.x) {
+      const int j = g < p.local_prefix[1] ? 0 : 1;
+      pack_group<NS>(p.local[j], g - p.local_prefix[j]);
+    }
+    return;
+  }
+  const int64_t per = (p.total + gridDim.x - 1) / gridDim.x;
+  const int64_t g0 = blockIdx.x * per, g1 = g0 + per < p.total ? g0 + per : p.total;
+  int64_t jlo = 0, jhi = 0;  // the current job's groups [jlo, jhi)
+  PackJob J;
+  for (int64_t g = g0; g < g1; ++g) {
+    if (g >= jhi) {
       int lo = 0, hi = p.njobs;
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (__ldg(p.prefix + mid) <= g) lo = mid; else hi = mid;
       }
-      const PackJob job = p.jobs[lo];
-      pack_group<NS>(job, g - __ldg(p.prefix + lo));
-    } else {
-      const int j = g < p.local_prefix[1] ? 0 : 1;
-      pack_group<NS>(p.local[j], g - p.local_prefix[j]);
+      J = p.jobs[lo];
+      jlo = __ldg(p.prefix + lo);
+      jhi = __ldg(p.prefix + lo + 1);
     }
+    pack_group<NS>(J, g - jlo);
   }
 }
 
@@ -1187,9 +1202,10 @@ struct PackedArgs {
 };
 
 // Warps: producer, MMA, two groups of four epilogue warps (the second works
-// only when every item is one accumulation chunk: the groups then take the
-// items in turn, each with its own accumulator); in the pair form also a
-// relay warp that tells the pair's MMA issuer when its CTA's stage has landed.
+// for batches and for single contractions whose items are one accumulation
+// chunk each: the groups then take the items in turn, each with its own
+// accumulator); in the pair form also a relay warp that tells the pair's MMA
+// issuer when its CTA's stage has landed.
 constexpr int pk_threads(bool pair) { return pair ? 352 : 320; }
 constexpr int PK_EPI_W0 = 2, PK_RELAY_WARP = 10;
 
