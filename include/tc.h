@@ -211,7 +211,8 @@ TC_API void tc_plan_destroy(tc_plan* plan);
  * of at least 2^26 multiply-adds (m n k) unless both operands are boxes and
  * one of them is read by a single row or column of output tiles (packing
  * would add a write and a read of it and save nothing: a box reads it at
- * full speed); otherwise as TC_ACCESS_BOX.  tc_operand_form reports the
+ * full speed), and for batch plans of at least 2^26 multiply-adds in all;
+ * otherwise as TC_ACCESS_BOX.  tc_operand_form and tc_plan_form report the
  * choice.
  * TC_ACCESS_BOX: when, for both A and B, the tile rows and a k-tile
  * form one box in the operand's own dims -- its unit-stride dim leads the row
@@ -234,8 +235,8 @@ TC_API void tc_plan_destroy(tc_plan* plan);
  * reads them (the packing of BLIS that Sections 5-6 build on: every element
  * gathered once instead of once per output tile across from it); the
  * mainloop then streams the packed units with bulk copies.  The workspace
- * grows by about the bytes of A and B (tc_workspace_size reports it).
- * Batches gather as in TC_ACCESS_BLOCK.
+ * grows by about the bytes of A and B (tc_workspace_size reports it); a
+ * batch plan packs every problem in one launch into its own buffer.
  * The FP64 mode always uses the BLOCK form.  The setting is process-wide and
  * read when a contraction is issued or a plan is created; it is not tied to
  * any thread or stream, so a host thread that changes it while another issues

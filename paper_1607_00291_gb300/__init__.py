@@ -124,8 +124,8 @@ def set_access(access: str) -> str:
     time where the block-scatter vectors allow; "scatter" gathers element by
     element (the plain scatter-matrix form); "packed" packs A and B once
     each into bf16 pieces in the tensor core's layout before the mainloop
-    (single contractions; batches gather as with "block").  Returns the
-    previous setting."""
+    (batch plans: every problem, in one launch).  Returns the previous
+    setting."""
     if access not in _ACCESS:
         raise ValueError(f"access must be one of {sorted(_ACCESS)}")
     prev = L.lib().tc_set_access(_ACCESS[access])
