@@ -171,6 +171,34 @@ def fp64_peak_tflops() -> float:
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
+def mixed_roofline(per_problem, kernel_ms, pipe_peak, pipe_src, prods, kernel, traffic):
+    """Roofline of a launch that runs several independent contractions.
+    per_problem: (algorithmic bytes, flops) of each -- A and B read once, C
+    written once; flops counted once (x `prods` products on the pipe).  Each
+    problem's floor is the larger of its bytes at the measured copy bandwidth
+    and its products at the pipe's peak; the line is bound by whichever of the
+    two sums is larger, and `floors` gives the sum of the per-problem floors
+    against the kernel time."""
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    t_hbm = [b / (hbm_peak * 1e9) * 1e3 for b, _ in per_problem]
+    t_pipe = [prods * f / (pipe_peak * 1e12) * 1e3 for _, f in per_problem]
+    nbytes = float(sum(b for b, _ in per_problem))
+    flops = float(sum(f for _, f in per_problem))
+    floor = sum(max(a, b) for a, b in zip(t_hbm, t_pipe))
+    if sum(t_hbm) >= sum(t_pipe):
+        ach, peak, unit, bound = nbytes / (kernel_ms * 1e-3) / 1e9, hbm_peak, "GB/s", "hbm"
+        src, alg = "MEASURED_PEAKS.json hbm_gbs", f"{nbytes / 1e6:.1f} MB per launch (A, B read, C written once)"
+    else:
+        ach, peak, unit, bound = prods * flops / (kernel_ms * 1e-3) / 1e12, pipe_peak, "TFLOP/s", "tensor"
+        src, alg = pipe_src, f"{flops:.4g} flops per launch (x{prods} products)"
+    return {"bound": bound, "kernel": kernel, "achieved": round(ach, 5), "peak": round(peak, 5),
+            "unit": unit, "frac": round(ach / peak, 4), "peak_source": src,
+            "kernel_ms": round(kernel_ms, 4), "traffic": traffic, "algorithmic": alg,
+            "floors": {"sum_floor_ms": round(floor, 4), "frac": round(floor / kernel_ms, 4),
+                       "hbm_floor_ms": round(sum(t_hbm), 4), "pipe_floor_ms": round(sum(t_pipe), 4),
+                       "note": "per problem the larger of its HBM floor and its pipe floor"}}
+
+
 def profiled_step(args, fn):
     """--profile: one untimed step inside a profiler range, after the timed region."""
     if not args.profile:
@@ -441,6 +469,20 @@ def oracle_err(alpha, hA, labA, hB, labB, beta, hC0, labC, got, windows):
 
 # ---- our arm ---------------------------------------------------------------------------------
 
+def batch_roofline(probs, dt, mode, kms, kernel, traffic):
+    """The batch's roofline: most of its 512 problems have a short side, so
+    their bytes, not their products, bound them (mixed_roofline)."""
+    if mode == "f64":
+        peak, src, prods = fp64_peak_tflops(), "cuBLAS DGEMM 4096^3 measured in this run", 1
+    else:
+        peak = measured_peaks().get("bf16_tflops", 1900.0)
+        src, prods = "MEASURED_PEAKS.json bf16_tflops (burst)", (3 if mode == "bf16x3" else 6)
+    es = torch.tensor([], dtype=dt).element_size()
+    per = [(es * sum(int(np.prod([p.ext[x] for x in lab])) for lab in (p.labA, p.labB, p.labC)), p.flops())
+           for p in probs]
+    return mixed_roofline(per, kms, peak, src, prods, kernel, traffic)
+
+
 def run_batch(args, ws, rank, local):
     """512 independent contractions (ranks 2-6, extents 8..64, random layouts)
     as one planned batch, replayed from a CUDA graph: scatter builder +
@@ -532,19 +574,7 @@ def run_batch(args, ws, rank, local):
         line = {"ms_per_step": round(ms, 4), "value": round(ws * flops / (ms * 1e-3) / 1e12, 5),
                 "unit": "TFLOP/s", "steps": K, "warmup": warm, "total_flops": flops,
                 "gpu_launches_per_step": int(per_step), "device_error": err_code, "autotune": tuned}
-        if mode == "f64":
-            peak, src, prods = fp64_peak_tflops(), "cuBLAS DGEMM 4096^3 measured in this run", 1
-        else:
-            mp = measured_peaks()
-            peak, src = mp.get("bf16_tflops", 1900.0), "MEASURED_PEAKS.json bf16_tflops (burst)"
-            prods = 3 if mode == "bf16x3" else 6
-        ach = prods * flops / (kms * 1e-3) / 1e12
-        line["roofline"] = {"bound": "tensor", "kernel": bkernel,
-                            "achieved": round(ach, 5), "peak": round(peak, 5), "unit": "TFLOP/s",
-                            "frac": round(ach / peak, 4), "peak_source": src, "kernel_ms": round(kms, 4),
-                            "traffic": traffic_for(bkernel,
-                                                   f"batch512_{mode}"),
-                            "algorithmic": f"{flops:.4g} flops per launch (x{prods} products)"}
+        line["roofline"] = batch_roofline(probs, dt, mode, kms, bkernel, traffic_for(bkernel, f"batch512_{mode}"))
         if check:
             line["oracle_check"] = check
         return line
@@ -574,13 +604,6 @@ def run_batch(args, ws, rank, local):
     f1.record()
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / max(1, K // 2), ws)
-    if mode == "f64":
-        peak, src, prods = fp64_peak_tflops(), "cuBLAS DGEMM 4096^3 measured in this run", 1
-    else:
-        mp = measured_peaks()
-        peak, src = mp.get("bf16_tflops", 1900.0), "MEASURED_PEAKS.json bf16_tflops (burst)"
-        prods = 3 if mode == "bf16x3" else 6
-    ach = prods * flops / (kms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": round(ws * flops / (ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
         "n_gpus": ws, "steps": K, "warmup": warm, "ms_per_step": round(ms, 4), "higher_is_better": True,
@@ -595,10 +618,7 @@ def run_batch(args, ws, rank, local):
         "e2e": {"value": round(ws * flops / (e2e_ms * 1e-3) / 1e12, 5), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
         "gpu_launches": int(per_step * K),
-        "roofline": {"bound": "tensor", "kernel": bkernel,
-                     "achieved": round(ach, 5), "peak": round(peak, 5), "unit": "TFLOP/s",
-                     "frac": round(ach / peak, 4), "peak_source": src, "kernel_ms": round(kms, 4),
-                     "traffic": None, "algorithmic": f"{flops:.4g} flops per launch (x{prods} products)"},
+        "roofline": batch_roofline(probs, dt, mode, kms, bkernel, traffic_for(bkernel, f"batch512_{mode}")),
         "device_error": err_code,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -927,13 +947,12 @@ def run_tccg(args, ws, rank, local):
         pipe_peak, prods = fp64_peak_tflops(), 1
     else:
         pipe_peak, prods = mp.get("bf16_tflops", 1900.0), (3 if mode == "bf16x3" else 6)
-    rows, floor_sum = [], 0.0
+    rows = []
     for i, (s_, p) in enumerate(zip(W.TCCG_STRINGS, probs)):
         nbytes = es * sum(int(np.prod([p.ext[x] for x in lab])) for lab in (p.labA, p.labB, p.labC))
         t_hbm = nbytes / (hbm_peak * 1e9) * 1e3
         t_pipe = prods * p.flops() / (pipe_peak * 1e12) * 1e3
         floor = max(t_hbm, t_pipe)
-        floor_sum += floor
         r = {"string": s_, "extent": p.ext[p.labC[0]], "ms": call_ms[i], "kernel_ms": kms[i],
              "tflops": round(p.flops() / (call_ms[i] * 1e-3) / 1e12, 4),
              "bound": "hbm" if t_hbm >= t_pipe else "tensor", "floor_ms": round(floor, 4),
@@ -944,11 +963,15 @@ def run_tccg(args, ws, rank, local):
             r["ttgt_time_over_ours"] = round(tt[i] / call_ms[i], 3)
         rows.append(r)
     line["per_string"] = rows
-    line["floors"] = {"sum_floor_ms": round(floor_sum, 4), "sum_kernel_ms": round(sum(kms), 4),
-                      "frac": round(floor_sum / sum(kms), 4),
-                      "note": "per string the larger of its HBM floor (MEASURED_PEAKS.json hbm_gbs) "
-                              "and its pipe floor; most strings are HBM-bound, so the line's "
-                              "tensor-pipe fraction understates them"}
+    # the line's roofline over all strings: bound by the larger of the summed
+    # HBM and pipe floors (most strings are HBM-bound)
+    r0 = line["roofline"]
+    per = [(es * sum(int(np.prod([p.ext[x] for x in lab])) for lab in (p.labA, p.labB, p.labC)), p.flops())
+           for p in probs]
+    src = r0.get("peak_source") if r0.get("unit") == "TFLOP/s" else "MEASURED_PEAKS.json bf16_tflops (burst)"
+    rr = mixed_roofline(per, sum(kms), pipe_peak, src, prods, r0.get("kernel"), r0.get("traffic"))
+    rr["kernel_ms_per_call"] = r0.get("kernel_ms_per_call")
+    line["roofline"] = rr
     return line
 
 

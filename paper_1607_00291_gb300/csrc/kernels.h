@@ -168,8 +168,13 @@ struct PackJob {
   int32_t pad;
   uint8_t* out;
 };
+// Units per group: the fewest whose tasks (R * 4 per unit, one 8-value chunk
+// each) fill the packing launch's 256 threads evenly, at least twice over.
 inline void pack_job_groups(PackJob& j) {
-  j.G = j.R * 4 >= 256 ? 1 : 256 / (j.R * 4);
+  const int t = j.R * 4;  // R is a multiple of 8: G <= 16
+  int G = 1;
+  while ((G * t) % 256 != 0 || G * t < 512) ++G;
+  j.G = G;
   j.groups = (j.units + j.G - 1) / j.G;
 }
 

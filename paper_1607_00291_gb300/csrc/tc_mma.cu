@@ -1101,35 +1101,52 @@ struct PackLaunch {
   const int64_t* prefix;  // batch: prefix sums of the jobs' unit groups (device, njobs + 1)
   int32_t njobs;
   int64_t total;          // unit groups of all jobs
+  unsigned long long* claim;  // batch: the claim counter (zero at launch)
+  int64_t chunk;              // batch: unit groups per claim
   const int32_t* gate;
 };
 
-// Unit group g of a job.  Task c = (row r = c % R, k-chunk q = c / R) of a
+// Units [u0, u1) of a job.  Task c = (row r = c % R, k-chunk q = c / R) of a
 // unit packs eight values of one row (k past the range as zeros; rows past
 // the operand are skipped); eight elements that the block-scatter vector
 // shows at unit stride, from a 16-byte boundary, take two 16-byte loads.
+// Each thread takes PK_TPT tasks at a time, a block's width apart, and
+// issues all their loads before it splits and stores any of them: the launch
+// is bound by the latency of its loads.  Two tasks per thread at five CTAs of
+// 256 threads per SM (48 registers) measured best on the 512-problem batch:
+// resident warps count for more than tasks per thread (four tasks at three
+// CTAs per SM were slower than one task at four).
+constexpr int PK_TPT = 2;
 template <int NS>
-__device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
+__device__ __forceinline__ void pack_units(const PackJob& p, int64_t u0, int64_t u1) {
   const int R = p.R, per_unit = R * (BK / 8);
-  const int64_t u0 = g * p.G;
-  const int nt = p.G * per_unit;
-  for (int tt = threadIdx.x; tt < nt; tt += blockDim.x) {
-    const int64_t u = u0 + tt / per_unit;
-    if (u >= p.units) break;
-    const int c = tt % per_unit;
-    // a blocked unit's row r = lo0 + 16 lo1: consecutive threads take
-    // consecutive lo1, the operand's unit-stride dim
-    const int r = p.swz ? (c % R) / 8 + 16 * ((c % R) % 8) : c % R, q = c / R;
-    const int64_t tr = u / p.KT, kt = u % p.KT;
-    uint8_t* out = p.out + u * (int64_t)(NS * R * BK * 2);
-    const int64_t row = tr * R + r;
-    const int64_t kk0 = kt * BK + 8 * q;
-    float v[8];
-    const int64_t ro = row < p.rows ? __ldg(p.rs + row) : kHole;
-    // a row past the operand or a hole of a blocked bundle is not written: it
-    // reaches only its own accumulator row (column), which is never stored
-    if (ro == kHole) continue;
-    {
+  const int nt = (int)((u1 - u0) * per_unit);  // a launch's share: far below 2^31
+  const int unit_bytes = NS * R * BK * 2;
+  for (int base = threadIdx.x; base < nt; base += PK_TPT * blockDim.x) {
+    float v[PK_TPT][8];
+    int uls[PK_TPT];  // the task's unit (from u0), or -1: nothing to store
+    uint32_t off[PK_TPT];
+#pragma unroll
+    for (int i = 0; i < PK_TPT; ++i) {
+      const int tt = base + i * (int)blockDim.x;
+      uls[i] = -1;
+      off[i] = 0;
+      if (tt >= nt) continue;
+      const int ul = tt / per_unit, c = tt - ul * per_unit;
+      // a job's units number far below 2^32 (each is 2 KB or more)
+      const uint32_t u = (uint32_t)u0 + (uint32_t)ul, KT = (uint32_t)p.KT;
+      // a blocked unit's row r = lo0 + 16 lo1: consecutive threads take
+      // consecutive lo1, the operand's unit-stride dim
+      const int r = p.swz ? (c % R) / 8 + 16 * ((c % R) % 8) : c % R, q = c / R;
+      const uint32_t tr = u / KT, kt = u - tr * KT;
+      const int64_t row = (int64_t)tr * R + r;
+      const int64_t kk0 = (int64_t)kt * BK + 8 * q;
+      const int64_t ro = row < p.rows ? __ldg(p.rs + row) : kHole;
+      // a row past the operand or a hole of a blocked bundle is not written: it
+      // reaches only its own accumulator row (column), which is never stored
+      if (ro == kHole) continue;
+      uls[i] = ul;
+      off[i] = (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16);
       const float* xr = p.x + ro;
       bool vec = false;
       if (kk0 + 7 < p.k) {
@@ -1138,8 +1155,8 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
             __ldg(p.ks + kk0 + 4) == o + 4 && (reinterpret_cast<uintptr_t>(xr + o) & 15) == 0) {
           const float4 x0 = __ldg(reinterpret_cast<const float4*>(xr + o));
           const float4 x1 = __ldg(reinterpret_cast<const float4*>(xr + o + 4));
-          v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-          v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+          v[i][0] = x0.x; v[i][1] = x0.y; v[i][2] = x0.z; v[i][3] = x0.w;
+          v[i][4] = x1.x; v[i][5] = x1.y; v[i][6] = x1.z; v[i][7] = x1.w;
           vec = true;
         }
       }
@@ -1147,46 +1164,65 @@ __device__ __forceinline__ void pack_group(const PackJob& p, int64_t g) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int64_t kk = kk0 + j;
-          v[j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
+          v[i][j] = kk < p.k ? __ldg(xr + __ldg(p.ks + kk)) : 0.f;
         }
       }
     }
-    split8_store<NS>(v, out, R * BK * 2,
-                     (uint32_t)((q * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16));
+#pragma unroll
+    for (int i = 0; i < PK_TPT; ++i)
+      if (uls[i] >= 0) split8_store<NS>(v[i], p.out + (u0 + uls[i]) * (int64_t)unit_bytes, R * BK * 2, off[i]);
   }
 }
 
 // A single contraction's two jobs: the CTAs take the unit groups round robin
 // (neighbouring units, which share sectors of the operand, are packed side by
-// side).  A batch: each CTA packs one contiguous range of unit groups, so that
-// its job -- a binary search over the prefix sums -- is looked up only when the
-// range crosses into another job (one search per group cost the batch 5 %).
+// side).  A batch: the CTAs claim runs of `chunk` consecutive unit groups from
+// a counter, so that the cost of a group, which varies with its operand's
+// layout by several times, evens out over the CTAs (fixed contiguous ranges
+// per CTA left the launch waiting on its slowest ranges); a run's job -- a
+// binary search over the prefix sums -- is looked up only when it crosses
+// into another job, and each job's part of a run is packed in one pass.
 template <int NS>
-__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackLaunch p) {
+__global__ void __launch_bounds__(256, 5) k_pack(const __grid_constant__ PackLaunch p) {
   if (p.gate && *p.gate == kDevBounds) return;
   if (!p.jobs) {
     for (int64_t g = blockIdx.x; g < p.total; g += gridDim.x) {
       const int j = g < p.local_prefix[1] ? 0 : 1;
-      pack_group<NS>(p.local[j], g - p.local_prefix[j]);
+      const PackJob& J = p.local[j];
+      const int64_t u0 = (g - p.local_prefix[j]) * J.G;
+      pack_units<NS>(J, u0, u0 + J.G < J.units ? u0 + J.G : J.units);
     }
     return;
   }
-  const int64_t per = (p.total + gridDim.x - 1) / gridDim.x;
-  const int64_t g0 = blockIdx.x * per, g1 = g0 + per < p.total ? g0 + per : p.total;
-  int64_t jlo = 0, jhi = 0;  // the current job's groups [jlo, jhi)
-  PackJob J;
-  for (int64_t g = g0; g < g1; ++g) {
-    if (g >= jhi) {
-      int lo = 0, hi = p.njobs;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(p.prefix + mid) <= g) lo = mid; else hi = mid;
+  // the claim and the current job live in shared memory (the job's fields,
+  // held in registers, would cost the launch resident CTAs)
+  __shared__ PackJob sJ;
+  __shared__ int64_t s_claim, s_jlo, s_jhi;
+  for (;;) {
+    if (threadIdx.x == 0) s_claim = (int64_t)atomicAdd(p.claim, (unsigned long long)p.chunk);
+    __syncthreads();
+    const int64_t g0 = s_claim;
+    if (g0 >= p.total) break;
+    const int64_t g1 = g0 + p.chunk < p.total ? g0 + p.chunk : p.total;
+    for (int64_t g = g0; g < g1;) {
+      if (threadIdx.x == 0) {
+        int lo = 0, hi = p.njobs;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(p.prefix + mid) <= g) lo = mid; else hi = mid;
+        }
+        sJ = p.jobs[lo];
+        s_jlo = __ldg(p.prefix + lo);
+        s_jhi = __ldg(p.prefix + lo + 1);
       }
-      J = p.jobs[lo];
-      jlo = __ldg(p.prefix + lo);
-      jhi = __ldg(p.prefix + lo + 1);
+      __syncthreads();
+      const int64_t jlo = s_jlo, jhi = s_jhi;
+      const int64_t ge = jhi < g1 ? jhi : g1;  // this job's groups in the run: [g, ge)
+      const int64_t ue = (ge - jlo) * sJ.G;
+      pack_units<NS>(sJ, (g - jlo) * sJ.G, ue < sJ.units ? ue : sJ.units);
+      __syncthreads();  // every thread is done with the job (and the claim) before they change
+      g = ge;
     }
-    pack_group<NS>(J, g - jlo);
   }
 }
 
@@ -1199,6 +1235,7 @@ struct PackedArgs {
   const int32_t* gate;
   int fault;  // 1: injected timeout (see TcLaunch::fault)
   int dual;   // two epilogue groups taking the work items in turn (see the epilogue)
+  unsigned long long* counter;  // batch (single CTAs): the item claim counter (zero at launch), or null
 };
 
 // Warps: producer, MMA, two groups of four epilogue warps (the second works
@@ -1365,7 +1402,11 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       bool ended = false;  // both end entries published
       auto publish_upto = [&](int64_t last) {
         while (!ended && npub <= last) {
-          const Item x = decode(w0 + npub * dw);
+          // a batch's CTAs claim their items after the first from a counter
+          // (items cost unevenly: their epilogues' stores differ with C's layout)
+          const int64_t w = !a.counter ? w0 + npub * dw
+                            : npub == 0 ? w0 : dw + (int64_t)atomicAdd(a.counter, 1ull);
+          const Item x = decode(w);
           if (!publish(npub, x)) return false;
           ++npub;
           if (x.d == nullptr) {
@@ -1847,6 +1888,7 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
     pk.prefix = q.pack_prefix;
     pk.njobs = q.pack_njobs;
     pk.total = q.pack_groups;
+    pk.claim = q.counter;
     a.probs = q.probs;
     a.items = q.items;
     a.nitems = q.nitems;
@@ -1898,9 +1940,32 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   // chunks alternate between the accumulators (the MMAs of a chunk then run
   // while the previous chunk is folded)
   a.dual = q.probs ? 1 : (q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0);
+  a.counter = q.probs && !PAIR ? q.counter + 1 : nullptr;
   mainloop_event_before(s);
+  if (q.probs) {
+    // the claim counters of the packing launch and of the mainloop
+    if (!q.counter) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemsetAsync(q.counter, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
   if (pk.total > 0) {
-    k_pack<NS><<<(unsigned)std::min<int64_t>(pk.total, (int64_t)q.ctas * 8), 256, 0, s>>>(pk);
+    // a batch: one wave, as many CTAs as the SMs hold at once, claiming
+    // about 16 runs each; a single contraction: eight CTAs per SM
+    static int resident = 0;
+    if (resident == 0) {
+      int r = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_pack<NS>, 256, 0) != cudaSuccess || r <= 0) {
+        cudaGetLastError();
+        r = 4;
+      }
+      resident = r;
+    }
+    int64_t grid = std::min<int64_t>(pk.total, (int64_t)q.ctas * 8);
+    if (q.probs) {
+      grid = std::min<int64_t>(pk.total, (int64_t)q.ctas * resident);
+      pk.chunk = std::max<int64_t>(1, pk.total / (grid * 16));
+    }
+    k_pack<NS><<<(unsigned)grid, 256, 0, s>>>(pk);
     note_launch();
   }
   if constexpr (PAIR) {
