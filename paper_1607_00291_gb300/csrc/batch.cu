@@ -433,6 +433,7 @@ struct tc_plan {
   bool packed = false;
   PackJob* d_jobs = nullptr;
   int64_t* d_job_prefix = nullptr;
+  void* d_pitems = nullptr;  // packed: the work items decoded at creation (launch_decode_items)
   int32_t njobs = 0;
   int64_t pack_groups = 0;
 };
@@ -689,6 +690,7 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
   const size_t o_jobs = take(pl->packed ? sizeof(PackJob) * 2 * std::max(np, 1) : 0);
   const size_t o_jpre = take(pl->packed ? sizeof(int64_t) * (2 * np + 1) : 0);
   const size_t o_pack = take(pack_total);
+  const size_t o_pit = take(pl->packed ? tc_item_bytes() * (size_t)std::max<int64_t>(1, pl->nitems) : 0);
   if (cudaMalloc(&pl->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     pl->dmem = nullptr;
@@ -808,6 +810,13 @@ int build_plan(tc_plan* pl, const std::vector<tc_problem>& probs, int balance) {
                                                kBsBlock, pl->d_scat, 0) != cudaSuccess ||
                  cudaStreamSynchronize(0) != cudaSuccess))
     return TC_ERR_CUDA;
+  // packed: the work items decoded once, here
+  if (pl->packed) {
+    pl->d_pitems = base + o_pit;
+    if (launch_decode_items(pl->d_probs, pl->d_items, pl->nitems, pl->d_pitems, 0) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess)
+      return TC_ERR_CUDA;
+  }
   return TC_OK;
 }
 
@@ -997,6 +1006,7 @@ int tc_plan_execute(tc_plan* plan, void* workspace, size_t ws_bytes, void* strea
     q.err = err_word();
     q.gate = gate;
     if (plan->packed) {
+      q.pack_items = plan->d_pitems;
       q.pack_jobs = plan->d_jobs;
       q.pack_prefix = plan->d_job_prefix;
       q.pack_njobs = plan->njobs;

@@ -208,6 +208,7 @@ struct TcLaunch {
   const int32_t* gate;  // checked launch: skip all work if *gate == kDevBounds (or null)
   void* pack_ws;  // single problem, packed form: tc_pack_bytes() bytes for the packed
                   // units of A and B (null: the gather or box form)
+  const void* pack_items;      // batch, packed form: the work items decoded (launch_decode_items)
   const PackJob* pack_jobs;    // batch, packed form: two jobs per problem (device), or null
   const int64_t* pack_prefix;  // their prefix sums of unit groups (device, pack_njobs + 1)
   int32_t pack_njobs;
@@ -219,6 +220,11 @@ cudaError_t launch_tc(const TcLaunch& q, cudaStream_t s);
 // pair form: two half-tile units of bn / 2 rows, the same bytes), each part
 // 256-byte aligned.
 size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces, bool pair);
+// Packed batches: every work item decoded once, at plan creation, into the
+// form the mainloop's roles read (tc_item_bytes() bytes each, 16-byte aligned).
+size_t tc_item_bytes();
+cudaError_t launch_decode_items(const DevProblem* probs, const WorkItem* items, int64_t n, void* out,
+                                cudaStream_t s);
 
 // K6 on the FP64 path (f64.cu): persistent batched mainloop + FP64 reduction
 // of split problems.

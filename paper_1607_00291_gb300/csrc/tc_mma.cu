@@ -174,7 +174,7 @@ __device__ __forceinline__ void record_timeout(volatile int* abort, int32_t* err
   if (err) atomicCAS(err, 0, kDevTimeout);
 }
 
-struct Item {
+struct __align__(16) Item {
   const DevProblem* d;
   int64_t m0, n0, kbeg, kend, KT;
   int split;
@@ -1236,6 +1236,7 @@ struct PackedArgs {
   int fault;  // 1: injected timeout (see TcLaunch::fault)
   int dual;   // two epilogue groups taking the work items in turn (see the epilogue)
   unsigned long long* counter;  // batch (single CTAs): the item claim counter (zero at launch), or null
+  const Item* pitems;           // batch (single CTAs): the work items decoded at plan creation, or null
 };
 
 // Warps: producer, MMA, two groups of four epilogue warps (the second works
@@ -1270,11 +1271,13 @@ struct PLay {
   // from the work list and the problem's descriptor in device memory) and
   // hands it to the other roles through a ring in shared memory
   static constexpr int QRP = 16;
-  static constexpr int RING = MISC + 16;  // Item[QRP], then QRP full and QRP empty barriers
+  // Item[QRP] (16-byte aligned: items are copied 16 bytes at a time), then
+  // QRP full and QRP empty barriers
+  static constexpr int RING = (MISC + 16 + 15) / 16 * 16;
   static constexpr int END = RING + QRP * (int)sizeof(Item) + 2 * QRP * 8;
   static constexpr int ALLOC = END + 1024;
   static_assert(ALLOC <= 227 * 1024, "shared memory plan exceeds the per-CTA limit");
-  static_assert(sizeof(Item) % 8 == 0 && (QRP & (QRP - 1)) == 0, "item ring layout");
+  static_assert(sizeof(Item) % 16 == 0 && RING % 16 == 0 && (QRP & (QRP - 1)) == 0, "item ring layout");
 };
 
 template <int NS, bool PAIR>
@@ -1382,11 +1385,22 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       auto decode = [&](int64_t w) {
         Item x;
         if (w < nitems) {
-          x = item(w);
+          x = a.pitems ? a.pitems[w] : item(w);
         } else {
           std::memset(&x, 0, sizeof x);
         }
         return x;
+      };
+      // a batch's CTAs claim their items after the first from a counter
+      // (items cost unevenly: their epilogues' stores differ with C's layout),
+      // each claim issued one entry ahead of its use, so that its round trip
+      // overlaps the streaming of the item before
+      int64_t claimed = w0;
+      auto next_index = [&](int64_t n) -> int64_t {
+        if (!a.counter) return w0 + n * dw;
+        const int64_t w = claimed;
+        if (w < nitems) claimed = dw + (int64_t)atomicAdd(a.counter, 1ull);
+        return w;
       };
       auto publish = [&](int64_t j, const Item& x) {
         const int q = (int)(j & (QRP - 1));
@@ -1402,11 +1416,7 @@ __global__ void __launch_bounds__(pk_threads(PAIR), 1) k_tcp(const __grid_consta
       bool ended = false;  // both end entries published
       auto publish_upto = [&](int64_t last) {
         while (!ended && npub <= last) {
-          // a batch's CTAs claim their items after the first from a counter
-          // (items cost unevenly: their epilogues' stores differ with C's layout)
-          const int64_t w = !a.counter ? w0 + npub * dw
-                            : npub == 0 ? w0 : dw + (int64_t)atomicAdd(a.counter, 1ull);
-          const Item x = decode(w);
+          const Item x = decode(next_index(npub));
           if (!publish(npub, x)) return false;
           ++npub;
           if (x.d == nullptr) {
@@ -1941,6 +1951,7 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   // while the previous chunk is folded)
   a.dual = q.probs ? 1 : (q.single.kps <= (int64_t)CHUNK_KT * BK ? 1 : 0);
   a.counter = q.probs && !PAIR ? q.counter + 1 : nullptr;
+  a.pitems = q.probs && !PAIR ? static_cast<const Item*>(q.pack_items) : nullptr;
   mainloop_event_before(s);
   if (q.probs) {
     // the claim counters of the packing launch and of the mainloop
@@ -1995,9 +2006,29 @@ cudaError_t launch_packed(const TcLaunch& q, cudaStream_t s) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Packed batches: each work item decoded once, at plan creation (the
+// producer of k_tcp then loads it instead of decoding it from the work list
+// and the problem's descriptor, two dependent round trips per item).
+__global__ void k_decode_items(const DevProblem* probs, const WorkItem* items, int64_t n, Item* out) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const WorkItem wi = items[w];
+    out[w] = item_of_tile<false>(probs + wi.prob, wi.tile, wi.split);
+  }
+}
+
 }  // namespace
 
 int tc_bn_max() { return BNMAX; }
+size_t tc_item_bytes() { return sizeof(Item); }
+cudaError_t launch_decode_items(const DevProblem* probs, const WorkItem* items, int64_t n, void* out,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, 1024);
+  k_decode_items<<<(unsigned)grid, 256, 0, s>>>(probs, items, n, static_cast<Item*>(out));
+  note_launch();
+  return cudaGetLastError();
+}
 size_t tc_pack_bytes(int64_t m, int64_t n, int64_t k, int bn, int pieces, bool pair) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
   const size_t b = (size_t)((n + bn - 1) / bn) * (size_t)((k + BK - 1) / BK) * pieces * bn * BK * 2;
