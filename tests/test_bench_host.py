@@ -46,3 +46,24 @@ def test_oracle_err_is_zero_on_the_oracle_and_sees_a_planted_error():
     e, _ = bench.oracle_err(s.alpha, h["A"].numpy(), s.labA, h["B"].numpy(), s.labB, s.beta,
                             h["C"].numpy(), s.labC, bad, wins)
     assert e > 1e-9
+
+
+def test_mixed_roofline_takes_the_larger_summed_floor(monkeypatch):
+    # a copy-bound problem (bytes dominate) and a pipe-bound one (products
+    # dominate): each floor is the larger of the two, the bound the larger sum
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 1000.0})
+    per = [(2e9, 1e9), (1e6, 3e12)]  # (bytes, flops)
+    r = bench.mixed_roofline(per, kernel_ms=10.0, pipe_peak=1000.0, pipe_src="test", prods=3,
+                             kernel="k", traffic=None)
+    t_hbm = [2e9 / 1e12 * 1e3, 1e6 / 1e12 * 1e3]            # ms at 1000 GB/s
+    t_pipe = [3 * 1e9 / 1e15 * 1e3, 3 * 3e12 / 1e15 * 1e3]  # ms at 1000 TFLOP/s
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"  # 9.003 ms of products > 2.001 ms of bytes
+    assert np.isclose(r["achieved"], 3 * (1e9 + 3e12) / 1e-2 / 1e12, rtol=1e-4)
+    assert np.isclose(r["floors"]["sum_floor_ms"], max(t_hbm[0], t_pipe[0]) + max(t_hbm[1], t_pipe[1]),
+                      rtol=1e-3)
+    assert np.isclose(r["floors"]["frac"], r["floors"]["sum_floor_ms"] / 10.0, rtol=1e-3)
+    # bytes alone: HBM-bound, achieved in GB/s
+    r = bench.mixed_roofline([(5e9, 1e6)], kernel_ms=10.0, pipe_peak=1000.0, pipe_src="test",
+                             prods=3, kernel="k", traffic=7)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 7
+    assert np.isclose(r["achieved"], 500.0) and np.isclose(r["frac"], 0.5)
