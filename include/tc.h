@@ -177,7 +177,8 @@ TC_API int tc_contract_batched(tc_dtype dtype, tc_mode mode, int32_t count, cons
  * in the cache file.  Untuned: least-padding FP64 tiles, tensor-core tiles
  * covering n, D = 4.  The plan's scatter vectors (K1) depend on the layouts
  * alone: tc_plan_create builds them on the device, on the legacy default
- * stream, and returns once they are built.  tc_plan_execute only enqueues
+ * stream (a packed plan also decodes its work items there, once), and
+ * returns once they are built.  tc_plan_execute only enqueues
  * work -- the device-side checks if they were on at creation, the packing,
  * mainloop and reduction kernels and the memset of the work counters -- with
  * no host synchronisation and no allocation, so it can be captured in a CUDA
