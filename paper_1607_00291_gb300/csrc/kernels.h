@@ -154,8 +154,8 @@ struct DevProblem {
 // rows x 32 k, row tile by row tile, k-tile by k-tile, from x through its row
 // scatter vector rs and its scatter vector along the contracted range ks
 // (kbs: its block-scatter vector, blocks of four).  The packing launch hands
-// out groups of G consecutive units (G units of R rows make at least 256
-// tasks of eight values where R allows), `groups` of them.
+// out groups of G consecutive units (G units of R rows make a multiple of 256
+// tasks of eight values, at least 512: pack_job_groups), `groups` of them.
 struct PackJob {
   const float* x;
   const int64_t* rs;  // may hold kHole entries (a blocked row bundle): zeros
